@@ -1,0 +1,232 @@
+"""ctypes wrapper of the FP64 CPU oracle (spl_oracle.c).
+
+TEST INFRASTRUCTURE: imported only by tests/, by __graft_entry__.smoke() and by the CPU-baseline leg of
+bench.py. It never touches the CUDA library and the CUDA library never touches it.
+
+All arrays are numpy; inputs are converted to float64 (counts and IRF taps are exact in float64).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spl_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over pixels). Returns the path of the shared library."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-D_GNU_SOURCE",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ct.Structure):
+    _fields_ = [("T", ct.c_int), ("L", ct.c_int), ("peak", ct.c_int), ("dmin", ct.c_int), ("dmax", ct.c_int),
+                ("beta", ct.c_double), ("sigma_rw2", ct.c_double), ("nu", ct.c_double * 9)]
+
+
+def params(T, L, peak, dmin=None, dmax=None, beta=0.5, sigma_rw2=3.0, nu=None) -> Params:
+    """Oracle parameters; dmin/dmax default to the full-support range [peak, T - L + peak]."""
+    q = Params()
+    q.T, q.L, q.peak = int(T), int(L), int(peak)
+    q.dmin = int(peak if dmin is None else dmin)
+    q.dmax = int(T - L + peak if dmax is None else dmax)
+    q.beta = float(beta)
+    q.sigma_rw2 = float(sigma_rw2)
+    w = np.zeros(9) if nu is None else np.asarray(nu, np.float64).reshape(9)
+    if nu is None:
+        w[4] = 1.0
+    for k in range(9):
+        q.nu[k] = float(w[k])
+    return q
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ct.CDLL(build())
+            d = ct.POINTER(ct.c_double)
+            u8 = ct.POINTER(ct.c_uint8)
+            i32 = ct.POINTER(ct.c_int32)
+            P = ct.POINTER(Params)
+            L.orc_set_threads.argtypes = [ct.c_int]
+            L.orc_set_threads.restype = ct.c_int
+            L.orc_check_domain.argtypes = [P]
+            L.orc_check_domain.restype = ct.c_int
+            L.orc_template_power_sum.argtypes = [P, d, ct.c_int, ct.c_double]
+            L.orc_template_power_sum.restype = ct.c_double
+            L.orc_cost.argtypes = [P, d, d, ct.c_long, d]
+            L.orc_cost_toa.argtypes = [P, d, i32, ct.c_int, d]
+            L.orc_posterior.argtypes = [ct.c_int, ct.c_int, d, i32, d, d]
+            L.orc_log_mixture.argtypes = [ct.c_int, d, d, d, ct.c_double]
+            L.orc_log_mixture.restype = ct.c_double
+            L.orc_estimate.argtypes = [P, d, d, ct.c_long, d, d, i32, d, d, d]
+            L.orc_filter_step.argtypes = [P, ct.c_int, ct.c_int, d, d, u8, d, d, u8, i32, d, d, d]
+            L.orc_intensity_mle.argtypes = [P, d, d, ct.c_int, d, d]
+            L.orc_intensity.argtypes = [P, d, d, ct.c_long, d, i32, u8, u8, d, d]
+            L.orc_pi_propagate.argtypes = [ct.c_int, ct.c_int, d, d, u8, d]
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _u8(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(ct.POINTER(ctype))
+
+
+def set_threads(n: int) -> int:
+    return lib().orc_set_threads(int(n))
+
+
+def check_domain(q: Params) -> int:
+    return lib().orc_check_domain(ct.byref(q))
+
+
+def template_power_sum(q: Params, h, d: int, expo: float) -> float:
+    h = _d(h)
+    return lib().orc_template_power_sum(ct.byref(q), _ptr(h, ct.c_double), int(d), float(expo))
+
+
+def cost(q: Params, h, z) -> np.ndarray:
+    """C[p, k] = C(dmin + k) for histograms z[..., T]."""
+    assert check_domain(q) == 0
+    h, z = _d(h), _d(z)
+    P = z.size // q.T
+    D = q.dmax - q.dmin + 1
+    C = np.empty((P, D))
+    lib().orc_cost(ct.byref(q), _ptr(h, ct.c_double), _ptr(z, ct.c_double), P, _ptr(C, ct.c_double))
+    return C.reshape(*z.shape[:-1], D)
+
+
+def cost_toa(q: Params, h, bins) -> np.ndarray:
+    assert check_domain(q) == 0
+    h = _d(h)
+    y = np.ascontiguousarray(bins, dtype=np.int32)
+    D = q.dmax - q.dmin + 1
+    C = np.empty(D)
+    lib().orc_cost_toa(ct.byref(q), _ptr(h, ct.c_double), _ptr(y, ct.c_int32), int(y.size), _ptr(C, ct.c_double))
+    return C
+
+
+def posterior(ell, dmin: int):
+    ell = _d(ell)
+    a = np.zeros(1, np.int32)
+    mu = np.zeros(1)
+    var = np.zeros(1)
+    lib().orc_posterior(int(ell.size), int(dmin), _ptr(ell, ct.c_double), _ptr(a, ct.c_int32),
+                        _ptr(mu, ct.c_double), _ptr(var, ct.c_double))
+    return int(a[0]), float(mu[0]), float(var[0])
+
+
+def log_mixture(nu, m, s2, d: float) -> float:
+    nu, m, s2 = _d(nu), _d(m), _d(s2)
+    return lib().orc_log_mixture(int(nu.size), _ptr(nu, ct.c_double), _ptr(m, ct.c_double),
+                                 _ptr(s2, ct.c_double), float(d))
+
+
+def estimate(q: Params, h, z, prior_mu=None, prior_var=None, want_ell=False):
+    """Single-frame estimate; returns dict(argmax, mu, var[, ell]) shaped like z[..., :]."""
+    assert check_domain(q) == 0
+    h, z = _d(h), _d(z)
+    shape = z.shape[:-1]
+    P = z.size // q.T
+    D = q.dmax - q.dmin + 1
+    a = np.empty(P, np.int32)
+    mu = np.empty(P)
+    var = np.empty(P)
+    ell = np.empty((P, D)) if want_ell else None
+    pm, pv = _d(prior_mu), _d(prior_var)
+    lib().orc_estimate(ct.byref(q), _ptr(h, ct.c_double), _ptr(z, ct.c_double), P, _ptr(pm, ct.c_double),
+                       _ptr(pv, ct.c_double), _ptr(a, ct.c_int32), _ptr(mu, ct.c_double),
+                       _ptr(var, ct.c_double), _ptr(ell, ct.c_double))
+    out = dict(argmax=a.reshape(shape), mu=mu.reshape(shape), var=var.reshape(shape))
+    if want_ell:
+        out["ell"] = ell.reshape(*shape, D)
+    return out
+
+
+def filter_step(q: Params, h, z, mu_in, var_in, present_in=None, faulty=None, want_ell=False):
+    """One frame of the online filter on an [H, W, T] histogram cube; returns dict(argmax, mu, var[, ell])."""
+    assert check_domain(q) == 0
+    h, z = _d(h), _d(z)
+    H, W, T = z.shape
+    assert T == q.T
+    P = H * W
+    D = q.dmax - q.dmin + 1
+    a = np.empty(P, np.int32)
+    mu = np.empty(P)
+    var = np.empty(P)
+    ell = np.empty((P, D)) if want_ell else None
+    mi, vi = _d(mu_in), _d(var_in)
+    pr, fa = _u8(present_in), _u8(faulty)
+    lib().orc_filter_step(ct.byref(q), H, W, _ptr(h, ct.c_double), _ptr(z, ct.c_double), _ptr(fa, ct.c_uint8),
+                          _ptr(mi, ct.c_double), _ptr(vi, ct.c_double), _ptr(pr, ct.c_uint8),
+                          _ptr(a, ct.c_int32), _ptr(mu, ct.c_double), _ptr(var, ct.c_double),
+                          _ptr(ell, ct.c_double))
+    out = dict(argmax=a.reshape(H, W), mu=mu.reshape(H, W), var=var.reshape(H, W))
+    if want_ell:
+        out["ell"] = ell.reshape(H, W, D)
+    return out
+
+
+def intensity_mle(q: Params, h, z, dr: int):
+    h, z = _d(h), _d(z)
+    r = np.zeros(1)
+    b = np.zeros(1)
+    lib().orc_intensity_mle(ct.byref(q), _ptr(h, ct.c_double), _ptr(z, ct.c_double), int(dr),
+                            _ptr(r, ct.c_double), _ptr(b, ct.c_double))
+    return float(r[0]), float(b[0])
+
+
+def intensity(q: Params, h, z, mu, present=None, faulty=None, dr=None):
+    """(refl, bg) per pixel, shaped like mu."""
+    h, z = _d(h), _d(z)
+    shape = np.shape(mu)
+    P = z.size // q.T
+    m = _d(mu).reshape(-1)
+    drr = None if dr is None else np.ascontiguousarray(dr, dtype=np.int32).reshape(-1)
+    pr, fa = _u8(present), _u8(faulty)
+    r = np.empty(P)
+    b = np.empty(P)
+    lib().orc_intensity(ct.byref(q), _ptr(h, ct.c_double), _ptr(z, ct.c_double), P, _ptr(m, ct.c_double),
+                        _ptr(drr, ct.c_int32), _ptr(pr, ct.c_uint8), _ptr(fa, ct.c_uint8),
+                        _ptr(r, ct.c_double), _ptr(b, ct.c_double))
+    return r.reshape(shape), b.reshape(shape)
+
+
+def pi_propagate(nu, pi_in, faulty=None):
+    pi = _d(pi_in)
+    H, W = pi.shape
+    nu = _d(nu).reshape(9)
+    fa = _u8(faulty)
+    out = np.empty((H, W))
+    lib().orc_pi_propagate(H, W, _ptr(nu, ct.c_double), _ptr(pi, ct.c_double), _ptr(fa, ct.c_uint8),
+                           _ptr(out, ct.c_double))
+    return out
+
+
+def state_init(q: Params, H: int, W: int):
+    """Initial Gaussians of Algorithm 1 (n = 0): the weakly informative flat Gaussian everywhere."""
+    mu = np.full((H, W), 0.5 * (q.dmin + q.dmax))
+    var = np.full((H, W), (q.dmax - q.dmin) ** 2 / 12.0)
+    return mu, var

@@ -1,0 +1,382 @@
+/*
+ * FP64 CPU oracle for the robust depth estimate and the online spatio-temporal filter of
+ * "Robust 3D reconstruction of dynamic scenes from single-photon lidar using Beta-divergences"
+ * (Legros et al., arXiv 2004.09211).
+ *
+ * TEST INFRASTRUCTURE. This file is the plain, slow, obviously correct statement of what the CUDA library
+ * computes. It is loaded only by the tests, by the package's smoke check and by the benchmark's CPU-baseline
+ * leg; the library itself never calls it. It shares no code, header, table or constant with the CUDA
+ * sources. Every function works in double precision on host arrays and follows the paper's definitions in
+ * the paper's order, with no blocking, pruning or reordering.
+ *
+ * Conventions (readings of the paper, each one stated where it is used):
+ *   - Time and depth are measured in histogram bins; 2d/c is never formed (Sec. IV gives sigma_RW in bins).
+ *   - h[0..L) is the tabulated IRF and `peak` = j_p the index of its maximum. A surface at depth d puts tap j
+ *     in bin t = d - peak + j, i.e. the template is s_d[t] = h[t - d + peak], zero outside [0, L).
+ *   - The candidate depths are the integers d in [dmin, dmax], inside the full-support range
+ *     [peak, T - L + peak]. On that range every template lies inside the histogram, which is what makes the
+ *     integral of f0^(1+beta) independent of d (the condition stated after Eq. beta_div2).
+ *   - 0^beta = 0 (an IRF tap of zero contributes nothing).
+ *
+ * Parity pins (all in tests/test_oracle_pins.py): beta = 1 against numpy.correlate (matched filter,
+ * Sec. II-B); the photon-list form of Eq. beta_div2 against the histogram form; strict argmax recovery on
+ * noiseless templates (Hoelder); invariance of sum s_d^(1+beta) over the domain; a one-photon box-IRF
+ * closed form of the posterior moments; posterior = prior on an empty histogram (Gaussian moments);
+ * translation equivariance and the dependency cone of the filter; the box-IRF closed form of the intensity
+ * MLE and its KKT conditions checked by scipy; the fixed points of Eq. prior_detect.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int T;            /* histogram bins N_T                                   */
+    int L;            /* IRF taps                                             */
+    int peak;         /* index j_p of the IRF maximum                         */
+    int dmin, dmax;   /* candidate depth range, inclusive, in bins            */
+    double beta;      /* divergence parameter beta > 0                        */
+    double sigma_rw2; /* random-walk variance sigma_RW^2 (s^2 in Algorithm 1)  */
+    double nu[9];     /* 3x3 mixture weights, row-major, centre nu[4]         */
+} orc_params;
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Set-up                                                                                                */
+/* ---------------------------------------------------------------------------------------------------- */
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* 0 when the candidate range lies inside the full-support range [peak, T - L + peak] (the reading of the
+ * "shape never changes" condition of Sec. II-B and Sec. III-A); nonzero otherwise. */
+int orc_check_domain(const orc_params* q) {
+    if (q->T < 1 || q->L < 1 || q->L > q->T) return 1;
+    if (q->peak < 0 || q->peak >= q->L) return 2;
+    if (q->dmin > q->dmax) return 3;
+    if (q->dmin < q->peak || q->dmax > q->T - q->L + q->peak) return 4;
+    if (!(q->beta > 0.0)) return 5;
+    return 0;
+}
+
+/* powered IRF value h^beta with 0^beta = 0 */
+static double powb(double h, double beta) { return h > 0.0 ? pow(h, beta) : 0.0; }
+
+/* template value s_d[t] = h[t - d + peak] (zero outside the taps) -- Eq. lik_ideal_poisson */
+static double tmpl(const orc_params* q, const double* h, int d, int t) {
+    int j = t - d + q->peak;
+    return (j >= 0 && j < q->L) ? h[j] : 0.0;
+}
+
+/* sum_t s_d[t]^expo over the whole histogram: the integral of f0^(1+beta) that Eq. beta_div2 drops as a
+ * constant. Used by the shift-invariance pin. */
+double orc_template_power_sum(const orc_params* q, const double* h, int d, double expo) {
+    double s = 0.0;
+    for (int t = 0; t < q->T; ++t) s += powb(tmpl(q, h, d, t), expo);
+    return s;
+}
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Robust data term: C(d) = z^T s_d^beta (histogram form of Eq. beta_div2, Sec. II-B)                   */
+/* ---------------------------------------------------------------------------------------------------- */
+
+static void cost_one(const orc_params* q, const double* h, const double* z, double* C) {
+    const int D = q->dmax - q->dmin + 1;
+    for (int k = 0; k < D; ++k) {
+        const int d = q->dmin + k;
+        double c = 0.0;
+        for (int t = d - q->peak; t < d - q->peak + q->L; ++t)   /* support of s_d */
+            c += z[t] * powb(tmpl(q, h, d, t), q->beta);
+        C[k] = c;
+    }
+}
+
+/* C[p][k] = C(dmin + k) for each of the P histograms z[p][0..T). */
+void orc_cost(const orc_params* q, const double* h, const double* z, long P, double* C) {
+    const int D = q->dmax - q->dmin + 1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long p = 0; p < P; ++p) cost_one(q, h, z + p * (long)q->T, C + p * (long)D);
+}
+
+/* Photon-list form of Eq. beta_div2 without the 1/K: sum over photons k of f0(y_k | d)^beta, the ToA bins
+ * y[0..K). */
+void orc_cost_toa(const orc_params* q, const double* h, const int32_t* y, int K, double* C) {
+    const int D = q->dmax - q->dmin + 1;
+    for (int k = 0; k < D; ++k) {
+        const int d = q->dmin + k;
+        double c = 0.0;
+        for (int i = 0; i < K; ++i) c += powb(tmpl(q, h, d, y[i]), q->beta);
+        C[k] = c;
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Pseudo-posterior (Eq. approx_post) and its moments (numerical integration on the grid, Sec. II-C)     */
+/* ---------------------------------------------------------------------------------------------------- */
+
+/* ell[k] = log pseudo-posterior (up to a constant) at d = dmin + k. Writes the smallest maximiser, the mean
+ * and the variance of the normalised weights exp(ell - max). Variance is taken in two passes. */
+void orc_posterior(int D, int dmin, const double* ell, int* argmax, double* mu, double* var) {
+    int a = 0;
+    for (int k = 1; k < D; ++k)
+        if (ell[k] > ell[a]) a = k;
+    const double m = ell[a];
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = 0; k < D; ++k) {
+        const double w = exp(ell[k] - m);
+        s0 += w;
+        s1 += w * (double)(dmin + k);
+    }
+    const double mean = s1 / s0;
+    double s2 = 0.0;
+    for (int k = 0; k < D; ++k) {
+        const double w = exp(ell[k] - m);
+        const double e = (double)(dmin + k) - mean;
+        s2 += w * e * e;
+    }
+    *argmax = dmin + a;
+    *mu = mean;
+    *var = s2 / s0;
+}
+
+/* log of the Gaussian mixture sum_c nu_c N(d; m_c, s2_c), by log-sum-exp. */
+double orc_log_mixture(int n, const double* nu, const double* m, const double* s2, double d) {
+    double lt[9];
+    double mx = -INFINITY;
+    for (int c = 0; c < n; ++c) {
+        const double e = d - m[c];
+        lt[c] = log(nu[c]) - 0.5 * log(2.0 * M_PI * s2[c]) - e * e / (2.0 * s2[c]);
+        if (lt[c] > mx) mx = lt[c];
+    }
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += exp(lt[c] - mx);
+    return mx + log(s);
+}
+
+/* lambda = (beta + 1) / beta: the factor in K * CE_beta(d) = -lambda * C(d) (Eq. beta_CE). */
+static double lambda_of(double beta) { return (beta + 1.0) / beta; }
+
+/* Single-frame estimate. With prior_mu == NULL the prior is uniform on [dmin, dmax], so the argmax is the
+ * minimum-divergence estimator of Sec. II-B; otherwise the prior is N(prior_mu[p], prior_var[p]).
+ * ell_out (nullable) receives ell[p][k]. */
+void orc_estimate(const orc_params* q, const double* h, const double* z, long P, const double* prior_mu,
+                  const double* prior_var, int* argmax, double* mu, double* var, double* ell_out) {
+    const int D = q->dmax - q->dmin + 1;
+    const double lam = lambda_of(q->beta);
+#pragma omp parallel
+    {
+        double* C = (double*)malloc(sizeof(double) * D);
+        double* ell = (double*)malloc(sizeof(double) * D);
+#pragma omp for schedule(dynamic, 16)
+        for (long p = 0; p < P; ++p) {
+            cost_one(q, h, z + p * (long)q->T, C);
+            for (int k = 0; k < D; ++k) {
+                double lp = 0.0;
+                if (prior_mu) {
+                    const double one = 1.0, m = prior_mu[p], s2 = prior_var[p];
+                    lp = orc_log_mixture(1, &one, &m, &s2, (double)(q->dmin + k));
+                }
+                ell[k] = lam * C[k] + lp;
+            }
+            orc_posterior(D, q->dmin, ell, argmax + p, mu + p, var + p);
+            if (ell_out) memcpy(ell_out + p * (long)D, ell, sizeof(double) * D);
+        }
+        free(C);
+        free(ell);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Spatio-temporal prior (Eq. predict with the ADF Gaussians of Eq. KL_div) and one filter step           */
+/* ---------------------------------------------------------------------------------------------------- */
+
+/* Components of the prior of pixel (y, x): one per stencil entry with nu > 0. A neighbour that is inside
+ * the image, present (its detection at the previous frame) and not faulty contributes N(mu, var + s^2):
+ * its Gaussian q convolved with the random walk. Any other entry contributes the weakly informative
+ * N((dmin+dmax)/2, (dmax-dmin)^2/12 + s^2) (Sec. III-A: absent pixels and pixels outside the field of
+ * view; the random walk is applied to it as to every q). Weights are used as given. Returns the count. */
+static int prior_components(const orc_params* q, int H, int W, int y, int x, const double* mu_in,
+                            const double* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                            double* nu, double* m, double* s2) {
+    const double flat_m = 0.5 * (q->dmin + q->dmax);
+    const double flat_v = (double)(q->dmax - q->dmin) * (double)(q->dmax - q->dmin) / 12.0;
+    int n = 0;
+    for (int k = 0; k < 9; ++k) {
+        if (!(q->nu[k] > 0.0)) continue;
+        const int yy = y + k / 3 - 1, xx = x + k % 3 - 1;
+        int informative = 0;
+        long i = 0;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            i = (long)yy * W + xx;
+            informative = (present_in ? present_in[i] != 0 : 1) && !(faulty && faulty[i]);
+        }
+        nu[n] = q->nu[k];
+        m[n] = informative ? mu_in[i] : flat_m;
+        s2[n] = (informative ? var_in[i] : flat_v) + q->sigma_rw2;
+        ++n;
+    }
+    return n;
+}
+
+/* One outer iteration of Algorithm 1 for the whole frame: prior from the previous frame's Gaussians,
+ * pseudo-posterior with this frame's histograms, moment matching. A faulty pixel has no data: its
+ * pseudo-posterior is its prior (Sec. III-B). present_in / faulty may be NULL (all present / none faulty).
+ * ell_out (nullable) receives ell[p][k]. */
+void orc_filter_step(const orc_params* q, int H, int W, const double* h, const double* z,
+                     const uint8_t* faulty, const double* mu_in, const double* var_in,
+                     const uint8_t* present_in, int* argmax, double* mu_out, double* var_out,
+                     double* ell_out) {
+    const int D = q->dmax - q->dmin + 1;
+    const double lam = lambda_of(q->beta);
+    const long P = (long)H * W;
+#pragma omp parallel
+    {
+        double* C = (double*)malloc(sizeof(double) * D);
+        double* ell = (double*)malloc(sizeof(double) * D);
+#pragma omp for schedule(dynamic, 16)
+        for (long p = 0; p < P; ++p) {
+            const int y = (int)(p / W), x = (int)(p % W);
+            double nu[9], m[9], s2[9];
+            const int nc = prior_components(q, H, W, y, x, mu_in, var_in, present_in, faulty, nu, m, s2);
+            const int has_data = !(faulty && faulty[p]);
+            if (has_data) cost_one(q, h, z + p * (long)q->T, C);
+            for (int k = 0; k < D; ++k)
+                ell[k] = (has_data ? lam * C[k] : 0.0) +
+                         orc_log_mixture(nc, nu, m, s2, (double)(q->dmin + k));
+            orc_posterior(D, q->dmin, ell, argmax + p, mu_out + p, var_out + p);
+            if (ell_out) memcpy(ell_out + p * (long)D, ell, sizeof(double) * D);
+        }
+        free(C);
+        free(ell);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Background and reflectivity (Sec. II-E)                                                              */
+/* ---------------------------------------------------------------------------------------------------- */
+
+/* Maximum-likelihood (r, b) of Eq. lik_bg_poisson, z_t ~ P(r h[t - dr + peak] + b), with the template at
+ * the integer position dr. The log-likelihood is concave in (r, b) and its maximiser satisfies
+ * r * sum(h) + b * T = K (sum of the two stationarity conditions, and also true on the boundaries r = 0,
+ * b = 0), so the MLE is the maximiser of the concave restriction phi(r) on r in [0, K / sum(h)]. phi' is
+ * decreasing; the root is found by bisection to full double precision. */
+void orc_intensity_mle(const orc_params* q, const double* h, const double* z, int dr, double* r_out,
+                       double* b_out) {
+    const int T = q->T, L = q->L, t0 = dr - q->peak;
+    if (t0 < 0 || t0 > T - L) {          /* template must lie inside the histogram */
+        *r_out = NAN;
+        *b_out = NAN;
+        return;
+    }
+    double K = 0.0, Kin = 0.0, Hs = 0.0;
+    for (int t = 0; t < T; ++t) K += z[t];
+    for (int j = 0; j < L; ++j) {
+        Kin += z[t0 + j];
+        Hs += h[j];
+    }
+    const double Kout = K - Kin;
+    if (K <= 0.0 || Hs <= 0.0) {
+        *r_out = 0.0;
+        *b_out = K / T;
+        return;
+    }
+    const double rmax = K / Hs;
+    /* phi'(r) = sum_W z_t (h_t - Hs/T) / (r h_t + b) - (Hs/T) Kout / b, b = (K - r Hs) / T; valid for
+     * r < rmax where b > 0. */
+#define DPHI(r, out)                                                         \
+    do {                                                                     \
+        const double b_ = (K - (r) * Hs) / T;                                \
+        double g_ = -(Hs / T) * Kout / b_;                                   \
+        for (int j = 0; j < L; ++j)                                          \
+            if (z[t0 + j] != 0.0) g_ += z[t0 + j] * (h[j] - Hs / T) / ((r) * h[j] + b_); \
+        (out) = g_;                                                          \
+    } while (0)
+    double g0;
+    DPHI(0.0, g0);
+    double r;
+    if (g0 <= 0.0) {
+        r = 0.0;
+    } else {
+        double lo = 0.0, hi = rmax;
+        for (int it = 0; it < 400 && hi - lo > 1e-16 * rmax; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (!(mid < rmax)) break;
+            double g;
+            DPHI(mid, g);
+            if (g > 0.0) lo = mid; else hi = mid;
+        }
+        r = 0.5 * (lo + hi);
+    }
+#undef DPHI
+    double b = (K - r * Hs) / T;
+    if (b < 0.0) b = 0.0;
+    *r_out = r;
+    *b_out = b;
+}
+
+/* Per pixel: absent -> b = K / T, r = 0; present -> the MLE above with the template at round(mu) (round half
+ * to even, the depth point estimate being the posterior mean). dr (nullable) overrides the template
+ * position per pixel. Faulty pixels have no data: r = b = 0. */
+void orc_intensity(const orc_params* q, const double* h, const double* z, long P, const double* mu,
+                   const int32_t* dr, const uint8_t* present, const uint8_t* faulty, double* refl,
+                   double* bg) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long p = 0; p < P; ++p) {
+        const double* zp = z + p * (long)q->T;
+        if (faulty && faulty[p]) {
+            refl[p] = 0.0;
+            bg[p] = 0.0;
+            continue;
+        }
+        if (present && !present[p]) {
+            double K = 0.0;
+            for (int t = 0; t < q->T; ++t) K += zp[t];
+            refl[p] = 0.0;
+            bg[p] = K / q->T;
+            continue;
+        }
+        const int d = dr ? dr[p] : (int)rint(mu[p]);
+        orc_intensity_mle(q, h, zp, d, refl + p, bg + p);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Prior probability of presence (Eq. prior_detect)                                                     */
+/* ---------------------------------------------------------------------------------------------------- */
+
+/* pi0[p] = sigmoid(sum_k nu_k logit(pi[p + k])). Readings: a neighbour outside the image enters with
+ * pi = 0.5 (logit 0, no information); a faulty pixel has pi = 0.5 (Sec. III-B), both as input and as
+ * output; pi is clamped to [1e-7, 1 - 1e-7] before the logit. */
+void orc_pi_propagate(int H, int W, const double* nu, const double* pi_in, const uint8_t* faulty,
+                      double* pi_out) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const long p = (long)y * W + x;
+            if (faulty && faulty[p]) {
+                pi_out[p] = 0.5;
+                continue;
+            }
+            double a = 0.0;
+            for (int k = 0; k < 9; ++k) {
+                const int yy = y + k / 3 - 1, xx = x + k % 3 - 1;
+                double v = 0.5;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                    const long i = (long)yy * W + xx;
+                    v = (faulty && faulty[i]) ? 0.5 : pi_in[i];
+                }
+                if (v < 1e-7) v = 1e-7;
+                if (v > 1.0 - 1e-7) v = 1.0 - 1e-7;
+                a += nu[k] * log(v / (1.0 - v));
+            }
+            pi_out[p] = 1.0 / (1.0 + exp(-a));
+        }
+}

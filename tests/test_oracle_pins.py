@@ -1,0 +1,457 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: a library routine that the method reduces
+to in a special case, a closed form, an invariant, or an alternative formulation the paper states as
+equivalent. They are chosen so that a plausible slip (a dropped or extra factor lambda, a reversed template,
+an off-by-one peak index, 0^beta = 1, a missing random-walk variance, a transposed stencil, a wrong edge
+rule) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2004_09211_gb300 import synth
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.json")))
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ------------------------------------------------------------------------------------------------------
+# Robust data term C(d) = z^T s_d^beta (Eq. beta_div2, histogram form)
+# ------------------------------------------------------------------------------------------------------
+
+
+def test_beta_one_is_matched_filter(orc):
+    """beta = 1 reduces to matched filtering (Sec. II-B): C(d) = numpy.correlate(z, h)[d - peak]."""
+    h, peak = synth.asymmetric_irf(L=13)
+    T = 64
+    z = _rng(0).poisson(2.0, size=(5, T)).astype(np.float64)
+    q = orc.params(T, len(h), peak, beta=1.0)
+    C = orc.cost(q, h, z)
+    for p in range(5):
+        ref = np.correlate(z[p], h.astype(np.float64), mode="valid")   # ref[u] = sum_j z[u + j] h[j]
+        np.testing.assert_allclose(C[p], ref[q.dmin - peak:q.dmax - peak + 1], rtol=1e-13, atol=1e-15)
+
+
+def test_photon_list_form_equals_histogram_form(orc):
+    """Sum over photons of f0(y_k|d)^beta (Eq. beta_div2) equals z^T s_d^beta on their histogram."""
+    h, peak = synth.asymmetric_irf(L=11)
+    T = 50
+    rng = _rng(1)
+    for beta in (0.2, 0.5, 1.0, 1.7):
+        y = rng.integers(0, T, size=40).astype(np.int32)      # repeated bins included
+        z = np.bincount(y, minlength=T).astype(np.float64)
+        q = orc.params(T, len(h), peak, beta=beta)
+        np.testing.assert_allclose(orc.cost_toa(q, h, y), orc.cost(q, h, z[None])[0], rtol=1e-13)
+
+
+def test_zero_taps_contribute_nothing(orc):
+    """0^beta = 0: an IRF with holes gives C(d) = (1/m)^beta * (photons on the non-zero taps), a windowed
+    count computed with numpy.correlate against the tap mask."""
+    L, T = 9, 40
+    mask = np.ones(L)
+    mask[[2, 5, 6]] = 0.0
+    h = (mask / mask.sum()).astype(np.float32)
+    peak = 0
+    z = _rng(2).poisson(1.5, size=T).astype(np.float64)
+    for beta in (0.05, 0.5, 1.0):
+        q = orc.params(T, L, peak, beta=beta)
+        ref = np.correlate(z, mask, mode="valid") * float(h[0]) ** beta   # h[0] = float32(1/m)
+        np.testing.assert_allclose(orc.cost(q, h, z[None])[0], ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("beta", [0.2, 0.5, 1.0, 2.0])
+def test_noiseless_template_is_recovered_strictly(orc, beta):
+    """z = A s_{d*} (no background): by Hoelder, sum_t s_{d*} s_d^beta < sum_t s_{d*}^{1+beta} for every
+    d != d*, so the minimum-divergence argmax is exactly d* and strict."""
+    h, peak = synth.asymmetric_irf(L=48)
+    T = 300
+    q = orc.params(T, len(h), peak, beta=beta)
+    for dstar in (q.dmin, 130, q.dmax):
+        z = np.zeros(T)
+        z[dstar - peak:dstar - peak + len(h)] = 1e4 * h
+        C = orc.cost(q, h, z[None])[0]
+        k = dstar - q.dmin
+        assert int(np.argmax(C)) == k
+        others = np.delete(C, k)
+        assert C[k] > others.max() * (1 + 1e-9)
+        est = orc.estimate(q, h, z[None])
+        assert int(est["argmax"][0]) == dstar
+
+
+def test_template_power_integral_is_shift_invariant(orc):
+    """On the full-support range the integral of f0^(1+beta) does not depend on d (the condition under
+    Eq. beta_div2); just outside it does, and the domain check rejects such ranges."""
+    h, peak = synth.asymmetric_irf(L=20)
+    T = 70
+    beta = 0.4
+    q = orc.params(T, len(h), peak, beta=beta)
+    ref = float(np.sum(h.astype(np.float64) ** (1 + beta)))
+    vals = [orc.template_power_sum(q, h, d, 1 + beta) for d in range(q.dmin, q.dmax + 1)]
+    np.testing.assert_allclose(vals, ref, rtol=1e-13)
+    assert orc.template_power_sum(q, h, q.dmin - 1, 1 + beta) < ref * (1 - 1e-6)
+    assert orc.template_power_sum(q, h, q.dmax + 1, 1 + beta) < ref * (1 - 1e-6)
+    assert orc.check_domain(orc.params(T, len(h), peak, dmin=peak - 1)) != 0
+    assert orc.check_domain(orc.params(T, len(h), peak, dmax=T - len(h) + peak + 1)) != 0
+    assert orc.check_domain(orc.params(T, len(h), peak, beta=0.0)) != 0
+
+
+# ------------------------------------------------------------------------------------------------------
+# Pseudo-posterior and its moments (Eq. approx_post, Sec. II-C)
+# ------------------------------------------------------------------------------------------------------
+
+
+def _sum_int(a, b):
+    return (a + b) * (b - a + 1) / 2.0
+
+
+def _sum_sq(a, b):
+    f = lambda n: n * (n + 1) * (2 * n + 1) / 6.0
+    return f(b) - f(a - 1)
+
+
+@pytest.mark.parametrize("beta", [0.3, 0.5, 1.0])
+def test_one_photon_box_irf_closed_form(orc, beta):
+    """One photon at t0 and a box IRF (h = 1/L): C(d) = L^-beta on the L depths whose template covers t0,
+    0 elsewhere. With a uniform prior the pseudo-posterior weights are E = exp(lambda L^-beta) on that window
+    and 1 elsewhere, lambda = (beta+1)/beta (Eq. beta_CE), so the moments are ratios of arithmetic series and
+    the argmax is the window's first depth."""
+    L, T, peak = 8, 90, 3
+    h = np.full(L, 1.0 / L, np.float32)          # 1/8 is exact in float32
+    t0 = 40
+    z = np.zeros(T)
+    z[t0] = 1.0
+    q = orc.params(T, L, peak, beta=beta)
+    a, b = q.dmin, q.dmax
+    w0, w1 = t0 + peak - L + 1, t0 + peak
+    E = math.exp((beta + 1) / beta * L ** (-beta))
+    S0 = (b - a + 1) + (E - 1) * L
+    S1 = _sum_int(a, b) + (E - 1) * _sum_int(w0, w1)
+    S2 = _sum_sq(a, b) + (E - 1) * _sum_sq(w0, w1)
+    mu = S1 / S0
+    var = S2 / S0 - mu * mu
+    est = orc.estimate(q, h, z[None])
+    assert int(est["argmax"][0]) == w0
+    np.testing.assert_allclose(est["mu"][0], mu, rtol=1e-12)
+    np.testing.assert_allclose(est["var"][0], var, rtol=1e-9)
+
+
+def test_translation_shifts_estimate(orc):
+    """Shifting the histogram and the prior mean by delta bins shifts argmax and mean by delta and leaves
+    the variance unchanged (away from the domain edges)."""
+    h, peak = synth.asymmetric_irf(L=30)
+    T = 400
+    q = orc.params(T, len(h), peak, beta=0.5)
+    rng = _rng(4)
+    z = np.zeros(T)
+    z[100:300] = rng.poisson(0.3, size=200)           # zeros near both ends, so shifts never wrap photons
+    z[150 - peak:150 - peak + len(h)] += rng.poisson(8 * h)
+    for delta in (1, 17, -23):
+        z1 = z
+        z2 = np.roll(z, delta)
+        e1 = orc.estimate(q, h, z1[None], prior_mu=[160.0], prior_var=[300.0])
+        e2 = orc.estimate(q, h, z2[None], prior_mu=[160.0 + delta], prior_var=[300.0])
+        assert int(e2["argmax"][0]) == int(e1["argmax"][0]) + delta
+        np.testing.assert_allclose(e2["mu"][0], e1["mu"][0] + delta, rtol=1e-12)
+        np.testing.assert_allclose(e2["var"][0], e1["var"][0], rtol=1e-8)
+
+
+def test_large_count_flat_prior_concentrates(orc):
+    """Symmetric IRF, many photons exactly on a template, uniform prior: mean -> d*, variance -> 0."""
+    h, peak = synth.gaussian_irf(3.0, 12)
+    T = 200
+    q = orc.params(T, len(h), peak, beta=0.5)
+    z = np.zeros(T)
+    z[90 - peak:90 - peak + len(h)] = np.rint(2000 * h)
+    e = orc.estimate(q, h, z[None])
+    assert int(e["argmax"][0]) == 90
+    assert abs(e["mu"][0] - 90) < 1e-6
+    assert e["var"][0] < 1e-6
+
+
+# ------------------------------------------------------------------------------------------------------
+# Spatio-temporal prior and filter step (Eq. predict, Eq. KL_div, Algorithm 1)
+# ------------------------------------------------------------------------------------------------------
+
+NU_ASYM = np.array([0.05, 0.10, 0.0, 0.15, 0.40, 0.20, 0.0, 0.10, 0.0])
+
+
+def test_empty_histogram_posterior_is_the_mixture_prior(orc):
+    """With no photons the pseudo-posterior is the prior of Eq. predict, a Gaussian mixture whose mean and
+    variance have closed forms: mu = sum nu_c m_c, var = sum nu_c (s_c^2 + m_c^2) - mu^2 with
+    s_c^2 = var_c + sigma_RW^2. On an integer grid far from the domain edges the discrete moments equal
+    these to ~exp(-2 pi^2 s^2). An asymmetric stencil catches transposed or mirrored neighbour offsets."""
+    h, peak = synth.gaussian_irf(3.0, 12)
+    T = 1200
+    sig2 = GOLD["sigma_rw2"]
+    q = orc.params(T, len(h), peak, beta=0.5, sigma_rw2=sig2, nu=NU_ASYM)
+    H = W = 3
+    rng = _rng(5)
+    mu_in = rng.uniform(560, 640, size=(H, W))
+    var_in = rng.uniform(0.5, 20.0, size=(H, W))
+    z = np.zeros((H, W, T))
+    out = orc.filter_step(q, h, z, mu_in, var_in)
+    m = []
+    s2 = []
+    nus = []
+    for k in range(9):               # neighbour (dy, dx) = (k // 3 - 1, k % 3 - 1) of the centre (1, 1)
+        if NU_ASYM[k] > 0:
+            nus.append(NU_ASYM[k])
+            m.append(mu_in[1 + k // 3 - 1, 1 + k % 3 - 1])
+            s2.append(var_in[1 + k // 3 - 1, 1 + k % 3 - 1] + sig2)
+    nus, m, s2 = map(np.array, (nus, m, s2))
+    mu = np.sum(nus * m)
+    var = np.sum(nus * (s2 + m * m)) - mu * mu
+    np.testing.assert_allclose(out["mu"][1, 1], mu, rtol=1e-10)
+    np.testing.assert_allclose(out["var"][1, 1], var, rtol=1e-8)
+
+
+def test_uniform_state_makes_weights_irrelevant(orc):
+    """A uniform state field makes every mixture component identical, so the result cannot depend on nu."""
+    h, peak = synth.asymmetric_irf(L=24)
+    T = 200
+    rng = _rng(6)
+    z = rng.poisson(0.4, size=(4, 5, T)).astype(np.float64)
+    mu_in = np.full((4, 5), 101.0)
+    var_in = np.full((4, 5), 40.0)
+    outs = []
+    for nu in (synth.cross_weights(0.5), NU_ASYM, np.eye(1, 9, 4).ravel()):
+        q = orc.params(T, len(h), peak, beta=0.5, nu=nu)
+        o = orc.filter_step(q, h, z, mu_in, var_in)
+        outs.append(o)
+    for o in outs[1:]:
+        # interior pixel only: edge pixels see out-of-view (flat) components with nu-dependent weight
+        np.testing.assert_array_equal(o["argmax"][1:-1, 1:-1], outs[0]["argmax"][1:-1, 1:-1])
+        np.testing.assert_allclose(o["mu"][1:-1, 1:-1], outs[0]["mu"][1:-1, 1:-1], rtol=1e-12)
+        np.testing.assert_allclose(o["var"][1:-1, 1:-1], outs[0]["var"][1:-1, 1:-1], rtol=1e-10)
+
+
+def test_filter_prior_with_centre_weight_only_equals_gaussian_prior(orc):
+    """nu = centre only: the prior is N(mu_in, var_in + sigma_RW^2) and the filter step equals the
+    single-frame estimate with that Gaussian prior."""
+    h, peak = synth.asymmetric_irf(L=24)
+    T = 150
+    rng = _rng(7)
+    z = rng.poisson(0.5, size=(3, 4, T)).astype(np.float64)
+    mu_in = rng.uniform(40, 120, size=(3, 4))
+    var_in = rng.uniform(1, 50, size=(3, 4))
+    q = orc.params(T, len(h), peak, beta=0.7, sigma_rw2=2.5, nu=np.eye(1, 9, 4).ravel())
+    f = orc.filter_step(q, h, z, mu_in, var_in)
+    e = orc.estimate(q, h, z, prior_mu=mu_in, prior_var=var_in + 2.5)
+    np.testing.assert_array_equal(f["argmax"], e["argmax"])
+    np.testing.assert_allclose(f["mu"], e["mu"], rtol=1e-12)
+    np.testing.assert_allclose(f["var"], e["var"], rtol=1e-10)
+
+
+def _cube(seed, H, W, T, h, peak):
+    rng = _rng(seed)
+    d = rng.integers(peak + 10, T - len(h) + peak - 10, size=(H, W))
+    z = rng.poisson(0.2, size=(H, W, T)).astype(np.float64)
+    for y in range(H):
+        for x in range(W):
+            z[y, x, d[y, x] - peak:d[y, x] - peak + len(h)] += rng.poisson(4 * h)
+    return z
+
+
+def test_filter_is_translation_equivariant(orc):
+    """Shifting the whole input (histograms and state) by one pixel shifts interior outputs by one pixel."""
+    h, peak = synth.asymmetric_irf(L=16)
+    T = 120
+    q = orc.params(T, len(h), peak, beta=0.5, nu=NU_ASYM)
+    H, W = 6, 7
+    z = _cube(8, H, W, T, h, peak)
+    rng = _rng(9)
+    mu_in = rng.uniform(30, 100, size=(H, W))
+    var_in = rng.uniform(1, 30, size=(H, W))
+    a = orc.filter_step(q, h, z, mu_in, var_in)
+    b = orc.filter_step(q, h, np.roll(z, (1, 1), (0, 1)), np.roll(mu_in, (1, 1), (0, 1)),
+                        np.roll(var_in, (1, 1), (0, 1)))
+    for k in ("argmax", "mu", "var"):
+        np.testing.assert_allclose(b[k][2:-1, 2:-1], a[k][1:-2, 1:-2], rtol=1e-12)
+
+
+def test_edge_pixels_see_flat_components(orc):
+    """An edge pixel equals the same pixel inside a larger image whose extra ring is absent (Sec. III-A:
+    out-of-view neighbours contribute the weakly informative Gaussian)."""
+    h, peak = synth.asymmetric_irf(L=16)
+    T = 120
+    q = orc.params(T, len(h), peak, beta=0.5, nu=NU_ASYM)
+    H, W = 4, 5
+    z = _cube(10, H, W, T, h, peak)
+    rng = _rng(11)
+    mu_in = rng.uniform(30, 100, size=(H, W))
+    var_in = rng.uniform(1, 30, size=(H, W))
+    a = orc.filter_step(q, h, z, mu_in, var_in)
+    zp = np.zeros((H + 2, W + 2, T))
+    zp[1:-1, 1:-1] = z
+    mp = np.full((H + 2, W + 2), 500.0)
+    vp = np.full((H + 2, W + 2), 2.0)
+    mp[1:-1, 1:-1] = mu_in
+    vp[1:-1, 1:-1] = var_in
+    pres = np.zeros((H + 2, W + 2), np.uint8)
+    pres[1:-1, 1:-1] = 1
+    b = orc.filter_step(q, h, zp, mp, vp, present_in=pres)
+    for k in ("argmax", "mu", "var"):
+        np.testing.assert_allclose(b[k][1:-1, 1:-1], a[k], rtol=1e-12)
+    # a faulty neighbour is treated like an absent one
+    fa = np.zeros((H, W), np.uint8)
+    fa[2, 2] = 1
+    pr = np.ones((H, W), np.uint8)
+    pr[2, 2] = 0
+    c = orc.filter_step(q, h, z, mu_in, var_in, faulty=fa)
+    d = orc.filter_step(q, h, z, mu_in, var_in, present_in=pr)
+    for k in ("argmax", "mu", "var"):
+        m = np.ones((H, W), bool)
+        m[2, 2] = False
+        np.testing.assert_allclose(c[k][m], d[k][m], rtol=1e-12)
+
+
+def test_faulty_pixel_posterior_is_prior(orc):
+    """A faulty pixel has no observations: its pseudo-posterior is its prior (Sec. III-B), the same as an
+    empty histogram. Its presence probability is 0.5, so in every prior (its own included) it enters as
+    the weakly informative Gaussian, like an absent pixel."""
+    h, peak = synth.asymmetric_irf(L=16)
+    T = 120
+    q = orc.params(T, len(h), peak, beta=0.5, nu=synth.cross_weights(0.5))
+    H, W = 3, 3
+    z = _cube(12, H, W, T, h, peak)
+    mu_in = np.full((H, W), 60.0)
+    var_in = np.full((H, W), 5.0)
+    fa = np.zeros((H, W), np.uint8)
+    fa[1, 1] = 1
+    a = orc.filter_step(q, h, z, mu_in, var_in, faulty=fa)
+    z0 = z.copy()
+    z0[1, 1] = 0
+    pr = np.ones((H, W), np.uint8)
+    pr[1, 1] = 0
+    b = orc.filter_step(q, h, z0, mu_in, var_in, present_in=pr)
+    for k in ("argmax", "mu", "var"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-12)
+
+
+def test_dependency_cone(orc):
+    """After n frames a pixel depends only on inputs within Chebyshev distance n: a crop with an n-pixel
+    margin reproduces the full-image result on its interior (this is how large frames are checked)."""
+    h, peak = synth.asymmetric_irf(L=16)
+    T = 100
+    q = orc.params(T, len(h), peak, beta=0.5, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    H, W, N = 9, 10, 3
+    zs = [_cube(20 + n, H, W, T, h, peak) for n in range(N)]
+    mu, var = orc.state_init(q, H, W)
+    for n in range(N):
+        o = orc.filter_step(q, h, zs[n], mu, var)
+        mu, var = o["mu"], o["var"]
+    y0, y1, x0, x1 = 2, 7, 3, 8            # crop with a margin of N around [5:4, 6:5] -> interior [5,6]
+    cm, cv = orc.state_init(q, y1 - y0, x1 - x0)
+    for n in range(N):
+        o = orc.filter_step(q, h, zs[n][y0:y1, x0:x1], cm, cv)
+        cm, cv = o["mu"], o["var"]
+    yy, xx = 2, 2                          # crop coordinates of full-image pixel (4, 5)
+    assert cm[yy, xx] == pytest.approx(mu[4, 5], rel=1e-12)
+    assert cv[yy, xx] == pytest.approx(var[4, 5], rel=1e-12)
+
+
+# ------------------------------------------------------------------------------------------------------
+# Background and reflectivity (Sec. II-E, MLE under Eq. lik_bg_poisson)
+# ------------------------------------------------------------------------------------------------------
+
+
+def test_intensity_box_irf_closed_form(orc):
+    """Box IRF (h = 1/L on the window): the Poisson MLE has per-region rates, b = K_out/(T-L) and
+    r/L + b = K_in/L, i.e. r = K_in - L K_out/(T-L) when that is >= 0; otherwise r = 0, b = K/T."""
+    L, T, peak = 8, 200, 4
+    h = np.full(L, 1.0 / L, np.float32)          # 1/8 is exact in float32
+    q = orc.params(T, L, peak)
+    rng = _rng(13)
+    for trial in range(20):
+        z = rng.poisson(rng.uniform(0.05, 2.0), size=T).astype(np.float64)
+        d = int(rng.integers(q.dmin, q.dmax + 1))
+        z[d - peak:d - peak + L] += rng.poisson(rng.uniform(0, 5), size=L) * (trial % 3 != 0)
+        Kin = z[d - peak:d - peak + L].sum()
+        Kout = z.sum() - Kin
+        r_ref = Kin - L * Kout / (T - L)
+        b_ref = Kout / (T - L)
+        if r_ref < 0:
+            r_ref, b_ref = 0.0, z.sum() / T
+        r, b = orc.intensity_mle(q, h, z, d)
+        assert r == pytest.approx(r_ref, rel=1e-9, abs=1e-9)
+        assert b == pytest.approx(b_ref, rel=1e-9, abs=1e-12)
+
+
+def test_intensity_noiseless_no_background(orc):
+    """All photons on the template and none outside: b = 0 and r = K / sum(h)."""
+    h, peak = synth.asymmetric_irf(L=48)
+    T = 500
+    q = orc.params(T, len(h), peak)
+    z = np.zeros(T)
+    z[200 - peak:200 - peak + len(h)] = np.rint(500 * h)
+    r, b = orc.intensity_mle(q, h, z, 200)
+    assert b == pytest.approx(0.0, abs=1e-9)
+    assert r == pytest.approx(z.sum() / float(np.sum(h.astype(np.float64))), rel=1e-9)
+
+
+def test_intensity_matches_generic_optimizer(orc):
+    """The MLE agrees with scipy's bounded optimiser on the 2-D Poisson log-likelihood (KKT point)."""
+    opt = pytest.importorskip("scipy.optimize")
+    h, peak = synth.asymmetric_irf(L=48)
+    hd = h.astype(np.float64)
+    T = 400
+    q = orc.params(T, len(h), peak)
+    rng = _rng(14)
+    for trial in range(8):
+        d = int(rng.integers(q.dmin, q.dmax + 1))
+        b_true = rng.uniform(0.005, 0.3)
+        r_true = rng.uniform(2, 40)
+        lam = np.full(T, b_true)
+        lam[d - peak:d - peak + len(h)] += r_true * hd
+        z = rng.poisson(lam).astype(np.float64)
+        r, b = orc.intensity_mle(q, h, z, d)
+
+        def nll(v):
+            rr, bb = v
+            m = np.full(T, bb)
+            m[d - peak:d - peak + len(h)] += rr * hd
+            m = np.maximum(m, 1e-300)
+            return -(np.sum(z * np.log(m)) - m.sum())
+
+        res = opt.minimize(nll, x0=[max(r, 1.0), max(b, 1e-3)], bounds=[(0, None), (1e-12, None)],
+                           method="L-BFGS-B", options=dict(ftol=1e-15, gtol=1e-12, maxiter=10000))
+        assert nll([r, b]) <= res.fun + 1e-7
+        assert r == pytest.approx(res.x[0], rel=1e-3, abs=1e-3)
+        assert b == pytest.approx(res.x[1], rel=1e-3, abs=1e-6)
+
+
+# ------------------------------------------------------------------------------------------------------
+# Prior probability of presence (Eq. prior_detect)
+# ------------------------------------------------------------------------------------------------------
+
+
+def test_pi_propagation_fixed_points_and_symmetry(orc):
+    nu = synth.cross_weights(GOLD["nu0"])
+    H, W = 5, 6
+    # constant pi with sum(nu) = 1 is a fixed point on interior pixels; 0.5 is a fixed point everywhere
+    out = orc.pi_propagate(nu, np.full((H, W), 0.8))
+    np.testing.assert_allclose(out[1:-1, 1:-1], 0.8, rtol=1e-12)
+    np.testing.assert_allclose(orc.pi_propagate(nu, np.full((H, W), 0.5)), 0.5, rtol=0, atol=1e-15)
+    # pi -> 1 - pi maps pi0 -> 1 - pi0 (logit is odd, sigmoid(-a) = 1 - sigmoid(a))
+    pi = _rng(15).uniform(0.01, 0.99, size=(H, W))
+    np.testing.assert_allclose(orc.pi_propagate(nu, 1 - pi), 1 - orc.pi_propagate(nu, pi), rtol=1e-12)
+    # an edge pixel sees out-of-view neighbours as pi = 0.5 (logit 0): constant 0.8 is pulled toward 0.5
+    corner = out[0, 0]
+    assert 0.5 < corner < 0.8
+    # nonlinear averaging of two opposite logits cancels exactly
+    nu2 = np.zeros(9)
+    nu2[3] = nu2[5] = 0.5
+    pi2 = np.full((1, 3), 0.5)
+    pi2[0, 0], pi2[0, 2] = 0.9, 0.1
+    assert orc.pi_propagate(nu2, pi2)[0, 1] == pytest.approx(0.5, abs=1e-15)
+    # faulty pixels are fixed at 0.5
+    fa = np.zeros((H, W), np.uint8)
+    fa[2, 3] = 1
+    assert orc.pi_propagate(nu, pi, faulty=fa)[2, 3] == 0.5
