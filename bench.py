@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the online robust depth-reconstruction hot path (one GPU per process).
+
+Workload (the video configuration): 256 x 256 pixels x 50 frames, T = 1500 bins, asymmetric 48-tap IRF
+(gamma rise + exponential tail), scene = tilted background plane + 3 moving rectangles/ellipses (1-3 px and
+5-20 bins per frame), 1-5 signal photons per pixel-frame, background per sequence for SBR 0.01, 0.1 and 1,
+each sequence filtered with beta = 0.2, 0.5 and 1.0 (9 runs), uint16 histograms. One step = the whole job:
+9 runs x 50 frames of spl_filter_step (prior from the previous frame, pseudo-posterior, moments,
+background/reflectivity) = 29.5 M pixel-frames. Histograms are generated on the device before timing and
+stay resident (29.6 GB; every frame is 197 MB, larger than the 129 MB L2, so no flush is needed between
+iterations).
+
+Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead, on a bounded sample of
+the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 256
+N_FRAMES = 50
+T = 1500
+L = 48
+SBRS = (0.01, 0.1, 1.0)
+BETAS = (0.2, 0.5, 1.0)
+SIGMA_RW2 = 3.0
+SEED = 2
+WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.1,1} x beta {0.2,0.5,1}"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per sequence (default 50)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------------------
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------------------------------------
+
+
+def make_sequences(frames: int, device):
+    """Three videos (one per SBR), [frames] tensors of [P, pitch] uint16 each, generated on `device`."""
+    from paper_2004_09211_gb300 import synth
+    h, peak = synth.asymmetric_irf(L=L)
+    sc = synth.moving_scene(H, W, frames, peak + 8, T - L + peak - 8, SEED)
+    hd = torch.from_numpy(h).to(device)
+    pitch = synth.pad_pitch(T)
+    gen = torch.Generator(device=device).manual_seed(SEED)
+    videos = []
+    for sbr in SBRS:
+        frames_z = []
+        for n in range(frames):
+            b = float(sc.signal[n].mean()) / (sbr * T)
+            mean = synth.expected_counts(torch.from_numpy(sc.depth[n]).to(device),
+                                         torch.from_numpy(sc.signal[n]).to(device), b, hd, peak, T)
+            z = synth.poisson_histograms(mean, gen).reshape(H * W, T)
+            frames_z.append(synth.pitched(z, pitch))
+            del mean
+        videos.append(frames_z)
+    return h, peak, hd, sc, videos
+
+
+def run_job(spl, prms, hd, videos, states, outs, stream, ev=None):
+    """One step: every (SBR, beta) run over all frames. Returns the number of kernel launches."""
+    launches = 0
+    for vi, frames_z in enumerate(videos):
+        for bi in range(len(BETAS)):
+            prm = prms[bi]
+            mu, var = states[vi][bi]
+            spl.spl_state_init(prm, mu[0], var[0], stream=stream)
+            launches += 1
+            for n, z in enumerate(frames_z):
+                src, dst = n & 1, (n + 1) & 1
+                if ev is not None:
+                    ev[0].append(torch.cuda.Event(enable_timing=True))
+                    ev[0][-1].record(stream)
+                spl.spl_filter_step(prm, z, hd, mu[src], var[src], out=dict(mu=mu[dst], var=var[dst], **outs),
+                                    stream=stream)
+                if ev is not None:
+                    ev[1].append(torch.cuda.Event(enable_timing=True))
+                    ev[1][-1].record(stream)
+                launches += 1
+    return launches
+
+
+def native(args):
+    import paper_2004_09211_gb300 as spl
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spl.load_library()
+    frames = args.frames
+    h, peak, hd, sc, videos = make_sequences(frames, dev)
+    P = H * W
+    prms = [spl.make_params(H, W, T, L, peak, beta=b, sigma_rw2=SIGMA_RW2) for b in BETAS]
+    states = [[([torch.empty(P, device=dev) for _ in range(2)], [torch.empty(P, device=dev) for _ in range(2)])
+               for _ in BETAS] for _ in SBRS]
+    outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                bg=torch.empty(P, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    units = len(SBRS) * len(BETAS) * frames * P
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            td.barrier()
+
+    for _ in range(args.warmup):
+        run_job(spl, prms, hd, videos, states, outs, stream)
+    barrier()
+    ev = ([], [])
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        launches = 0
+        for _ in range(args.steps):
+            launches += run_job(spl, prms, hd, videos, states, outs, stream, ev)
+        stop.record(stream)
+        barrier()
+    ms = start.elapsed_time(stop)
+    kern_ms = [a.elapsed_time(b) for a, b in zip(*ev)]
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (the fused filter step): algorithmic bytes per pixel-frame =
+    # histogram row (2 T) + previous state (mu, var) + outputs (mu, var, argmax, refl, bg)
+    alg_bytes = P * (2 * T + 8 + 20)
+    avg_kernel_s = statistics.mean(kern_ms) / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / avg_kernel_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "k_estimate<u16> (spl_filter_step)", "alg_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": avg_kernel_s * 1e3,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(spl, prms, hd, videos, dev, stream, P)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(h, peak, sc)
+
+    if rank == 0:
+        line = {
+            "metric": "pixel-frames/s", "value": value, "unit": "pixel-frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pixels": P, "frames": frames, "T": T, "L": L,
+                       "sequences": len(SBRS), "betas": list(BETAS), "hist": "uint16",
+                       "pixel_frames_per_step": units, "l2": "inputs larger than L2 (197 MB per frame), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        td.destroy_process_group()
+
+
+def end_to_end(spl, prms, hd, videos, dev, stream, P):
+    """Same job through the public API with the histograms in pinned HOST memory: every frame is copied
+    host -> device inside the timed region (double-buffered on a copy stream) and every frame's outputs
+    (mu, var, argmax, refl, bg) are read back to pinned host buffers."""
+    host = []
+    for v in videos:
+        hv = []
+        for z in v:
+            hz = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
+            hz.copy_(z)
+            hv.append(hz)
+        host.append(hv)
+    pitch = videos[0][0].shape[1]
+    dbuf = [torch.empty(P, pitch, dtype=torch.uint16, device=dev) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    hout = {k: torch.empty(P, dtype=dt).pin_memory() for k, dt in
+            (("mu", torch.float32), ("var", torch.float32), ("argmax", torch.int32), ("refl", torch.float32),
+             ("bg", torch.float32))}
+    mu = [torch.empty(P, device=dev) for _ in range(2)]
+    var = [torch.empty(P, device=dev) for _ in range(2)]
+    outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                bg=torch.empty(P, device=dev))
+    frames = len(host[0])
+    h2d = d2h = 0
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+
+    def job():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        seq = [(vi, bi, n) for vi in range(len(host)) for bi in range(len(prms)) for n in range(frames)]
+        with torch.cuda.stream(copy_stream):
+            dbuf[0].copy_(host[seq[0][0]][seq[0][2]], non_blocking=True)
+            copied[0].record(copy_stream)
+        for i, (vi, bi, n) in enumerate(seq):
+            s = i & 1
+            if i + 1 < len(seq):
+                nvi, _, nn = seq[i + 1]
+                with torch.cuda.stream(copy_stream):
+                    copy_stream.wait_event(consumed[1 - s])
+                    dbuf[1 - s].copy_(host[nvi][nn], non_blocking=True)
+                    copied[1 - s].record(copy_stream)
+            h2d += host[vi][n].numel() * 2
+            stream.wait_event(copied[s])
+            if n == 0:
+                spl.spl_state_init(prms[bi], mu[0], var[0], stream=stream)
+            src, dst = n & 1, (n + 1) & 1
+            o = spl.spl_filter_step(prms[bi], dbuf[s], hd, mu[src], var[src],
+                                    out=dict(mu=mu[dst], var=var[dst], **outs), stream=stream)
+            consumed[s].record(stream)
+            for k in hout:
+                hout[k].copy_(o[k], non_blocking=True)
+                d2h += o[k].numel() * 4
+        return len(seq)
+
+    job()  # warm-up (also primes the events)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    n = job()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    return {"value": n * P / dt, "unit": "pixel-frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "note": "histograms in pinned host memory, copied each frame; outputs read back each frame"}
+
+
+# ---------------------------------------------------------------------------------------------------------
+# CPU oracle baseline (the reference arm of this benchmark)
+# ---------------------------------------------------------------------------------------------------------
+
+CROP = 128         # oracle sample: a CROP x CROP window of the SBR 0.1 sequence, beta = 0.5
+CROP_FRAMES = 3
+
+
+def cpu_sample_inputs(h, peak, sc, frames=CROP_FRAMES, crop=CROP):
+    """The oracle's bounded sample: the first frames of the SBR = 0.1 sequence on a centred crop, generated
+    on the host from the same scene (a CPU random stream; the oracle is timed, not compared, here)."""
+    from paper_2004_09211_gb300 import synth
+    g = torch.Generator().manual_seed(SEED)
+    y0 = (H - crop) // 2
+    zs = []
+    for n in range(frames):
+        b = float(sc.signal[n].mean()) / (0.1 * T)
+        d = torch.from_numpy(sc.depth[n][y0:y0 + crop, y0:y0 + crop].copy())
+        s = torch.from_numpy(sc.signal[n][y0:y0 + crop, y0:y0 + crop].copy())
+        mean = synth.expected_counts(d, s, b, torch.from_numpy(h), peak, T)
+        zs.append(torch.poisson(mean, generator=g).numpy().astype(np.float64))
+    return zs
+
+
+def cpu_baseline(h, peak, sc, frames=CROP_FRAMES, crop=CROP):
+    from oracle import oracle as orc
+    from paper_2004_09211_gb300 import synth
+    cores = orc.set_threads(os.cpu_count() or 1)
+    zs = cpu_sample_inputs(h, peak, sc, frames, crop)
+    q = orc.params(T, L, peak, beta=0.5, sigma_rw2=SIGMA_RW2, nu=synth.cross_weights(0.5))
+    mu, var = orc.state_init(q, crop, crop)
+    t0 = time.perf_counter()
+    for z in zs:
+        e = orc.filter_step(q, h, z, mu, var)
+        mu, var = e["mu"], e["var"]
+        orc.intensity(q, h, z, mu)
+    dt = time.perf_counter() - t0
+    units = crop * crop * frames
+    return {"value": units / dt, "unit": "pixel-frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{crop}x{crop} crop x {frames} frames of the SBR 0.1 sequence, beta 0.5 "
+                      f"(filter step + intensity, FP64, OpenMP over pixels)", "seconds": dt}
+
+
+def reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2004_09211_gb300 import synth
+    h, peak = synth.asymmetric_irf(L=L)
+    sc = synth.moving_scene(H, W, CROP_FRAMES, peak + 8, T - L + peak - 8, SEED)
+    for _ in range(args.warmup):
+        cpu_baseline(h, peak, sc, frames=1, crop=32)
+    secs = []
+    vals = []
+    for _ in range(max(1, args.steps)):
+        r = cpu_baseline(h, peak, sc, frames=1)
+        secs.append(r["seconds"])
+        vals.append(r["value"])
+    value = statistics.mean(vals)
+    units = CROP * CROP
+    line = {"impl": "reference", "metric": "pixel-frames/s", "value": value, "unit": "pixel-frames/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{CROP}x{CROP} crop x 1 frame per step"},
+            "cpu_baseline": {"value": value, "unit": "pixel-frames/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": "pixel-frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "units_per_step": units}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        native(args)
+
+
+if __name__ == "__main__":
+    main()

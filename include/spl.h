@@ -1,0 +1,156 @@
+/*
+ * spl.h -- C ABI of libspl, the CUDA (sm_103a) hot path of the online robust depth reconstruction method of
+ * "Robust 3D reconstruction of dynamic scenes from single-photon lidar using Beta-divergences"
+ * (Legros et al., arXiv 2004.09211).
+ *
+ * General conventions
+ *   - Every array argument is a DEVICE pointer to memory the caller allocated and owns, unless the comment
+ *     says "host". The library keeps no pointer after a call returns.
+ *   - Calls are asynchronous: they validate their arguments on the host, enqueue kernels on `stream`
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream) and return. No call synchronises the
+ *     device, allocates device memory or copies device data to the host.
+ *   - Argument errors are reported before anything is launched: the call returns SPL_EINVAL and
+ *     spl_last_error() (a per-thread message) says which argument is wrong. A failed launch returns SPL_ECUDA.
+ *   - Depth and time are measured in histogram bins. h[0..L) is the tabulated instrument response (IRF) and
+ *     `peak` the index j_p of its maximum; a surface at depth d puts tap j in bin t = d - peak + j, i.e. the
+ *     template is s_d[t] = h[t - d + peak] (Eq. lik_ideal_poisson, Sec. II-D: the surface sits at the IRF
+ *     maximum).
+ *   - Candidate depths are the integers dmin..dmax (D = dmax - dmin + 1 of them). They must lie in the
+ *     full-support range [peak, T - L + peak], on which every template lies inside the histogram; that is the
+ *     condition under which the integral of f0^(1+beta) does not depend on d (Sec. II-B, below Eq. beta_div2,
+ *     and Sec. III-A on choosing T).
+ *   - IRF taps that are <= 0 or NaN count as zero (0^beta = 0). The IRF is used as given, never renormalised.
+ *   - Per-pixel maps are [H][W] row-major. Histograms are [P][pitch] with P = H*W; see spl_hist.
+ */
+#ifndef SPL_H
+#define SPL_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPL_API __attribute__((visibility("default")))
+#else
+#define SPL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPL_OK = 0,
+    SPL_EINVAL = 1,       /* invalid argument (checked on the host, nothing launched) */
+    SPL_ENOMEM = 2,       /* the call needed memory it could not get */
+    SPL_ECUDA = 3,        /* a CUDA launch or runtime call failed; spl_last_error() has the CUDA message */
+    SPL_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+    SPL_EUNSUPPORTED = 5  /* valid request outside what this build supports (e.g. L above SPL_MAX_TAPS) */
+} spl_status;
+
+/* Storage of the photon-count histograms z. Counts are non-negative integers in every format. */
+typedef enum {
+    SPL_HIST_U16 = 0,     /* uint16 counts                                      */
+    SPL_HIST_F16 = 1,     /* IEEE half counts (integers up to 2048 are exact)   */
+    SPL_HIST_F32 = 2      /* float counts                                       */
+} spl_hist_format;
+
+/* Largest IRF length and histogram length this build supports. */
+#define SPL_MAX_TAPS 128
+#define SPL_MAX_BINS 8192
+
+/* Histogram cube of one frame: pixel p's counts z_p[0..T) start at element p * pitch of `data`. pitch >= T,
+ * and pitch * element size must be a multiple of 16 bytes with `data` 16-byte aligned, so every row can be
+ * read with 16-byte loads. Elements T..pitch-1 are ignored. */
+typedef struct {
+    spl_hist_format fmt;
+    const void* data;     /* device */
+    int64_t pitch;        /* elements between consecutive pixels */
+} spl_hist;
+
+/* Fixed inputs of one frame (Algorithm 1's fixed parameters plus the problem geometry). */
+typedef struct {
+    int32_t H, W;         /* pixels per frame (P = H*W)                                         */
+    int32_t T;            /* histogram bins N_T (Eq. lik_ideal_poisson)                         */
+    int32_t L, peak;      /* IRF taps and the index of the IRF maximum                          */
+    int32_t dmin, dmax;   /* candidate depths, inclusive; see the conventions above             */
+    float beta;           /* beta-divergence parameter, > 0 (Eq. beta_div)                      */
+    float sigma_rw2;      /* random-walk variance sigma_RW^2 = s^2 of Algorithm 1, > 0          */
+    float nu[9];          /* 3x3 mixture weights of Eq. predict, row-major, nu[4] = centre;
+                             the paper's M = 5 choice is nu0 at the centre and (1 - nu0)/4 on the
+                             four edge neighbours. Each >= 0, finite, sum > 0.                  */
+} spl_params;
+
+/* Version string of the library. */
+SPL_API const char* spl_version(void);
+
+/* Message of the last failed call on this thread ("" if none). Valid until the next call on the thread. */
+SPL_API const char* spl_last_error(void);
+
+/*
+ * spl_depth_cost -- robust data term for every candidate depth (Sec. II-B).
+ *   C(d) = sum_t z_t h[t - d + peak]^beta, the histogram form of Eq. beta_div2: minimising the
+ *   beta-divergence between the empirical ToA distribution and f0(.|d) maximises z^T s_d^beta.
+ *   cost   : [P][D] float, cost[p][k] = C(dmin + k). May be NULL if only argmax is wanted.
+ *   argmax : [P] int32 (nullable) = the smallest d maximising C(d): the minimum-divergence estimator.
+ *   h      : [L] float IRF (device).
+ *   Uses H, W, T, L, peak, dmin, dmax, beta of prm.
+ */
+SPL_API spl_status spl_depth_cost(const spl_params* prm, const spl_hist* z, const float* h, float* cost,
+                          int32_t* argmax, void* stream);
+
+/*
+ * spl_depth_estimate -- single-frame pseudo-Bayesian depth estimate (Sec. II-C, Eq. approx_post).
+ *   log pseudo-posterior ell(d) = lambda C(d) + log f(d), lambda = (beta + 1) / beta (Eq. beta_CE), on the
+ *   integer grid dmin..dmax. f(d) = N(d; prior_mu[p], prior_var[p]) when prior_mu != NULL, else uniform
+ *   (then the argmax is the minimum-divergence estimator).
+ *   Outputs per pixel (all [P]): argmax (smallest maximiser of ell), mu and var = mean and variance of the
+ *   normalised pseudo-posterior on the grid (the depth estimate and its uncertainty).
+ *   refl, bg (nullable, both or neither): reflectivity r and background b per Sec. II-E. A pixel with
+ *   present[p] == 0 gets b = K/T, r = 0 (K = total photon count); otherwise (r, b) is the maximum-likelihood
+ *   estimate under Eq. lik_bg_poisson with the template at round-half-even(mu). present may be NULL
+ *   (every pixel present).
+ *   prior_var must be > 0 where given.
+ */
+SPL_API spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, const float* h, const float* prior_mu,
+                              const float* prior_var, const uint8_t* present, int32_t* argmax, float* mu,
+                              float* var, float* refl, float* bg, void* stream);
+
+/*
+ * spl_filter_step -- one frame of the online filter (one outer iteration of Algorithm 1).
+ *   Prior (Eq. predict): for each pixel p, a Gaussian mixture over the 3x3 stencil with weights nu. Stencil
+ *   entry p' contributes N(mu_in[p'], var_in[p'] + sigma_rw2) if p' is inside the frame, present_in[p'] != 0
+ *   and faulty[p'] == 0; otherwise the weakly informative N((dmin+dmax)/2, (dmax-dmin)^2/12 + sigma_rw2)
+ *   (Sec. III-A: absent and out-of-view neighbours). Entries with nu = 0 are skipped.
+ *   Pseudo-posterior as in spl_depth_estimate with that prior; a faulty pixel has no data (C = 0), so its
+ *   pseudo-posterior is its prior (Sec. III-B).
+ *   ADF (Eq. KL_div): mu_out, var_out = mean and variance of the pseudo-posterior (the Gaussian q_{p,n}).
+ *   mu_in/var_in/present_in describe frame n-1; present_now (frame n detections) selects the intensity rule
+ *   as in spl_depth_estimate. present_in, faulty, present_now may be NULL (all present / none faulty).
+ *   argmax, refl, bg are nullable (refl and bg both or neither). Faulty pixels get refl = bg = 0.
+ *   mu_out/var_out must not alias mu_in/var_in (neighbours read the previous frame); use two buffers.
+ */
+SPL_API spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                           const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                           const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
+                           float* refl, float* bg, void* stream);
+
+/*
+ * spl_state_init -- initial Gaussians of Algorithm 1 (n = 0): the weakly informative Gaussian of Sec. III-A,
+ *   mu = (dmin + dmax)/2 and var = (dmax - dmin)^2/12, for every pixel. mu, var: [P] float.
+ */
+SPL_API spl_status spl_state_init(const spl_params* prm, float* mu, float* var, void* stream);
+
+/*
+ * spl_pi_propagate -- prior probability of presence for the next frame (Eq. prior_detect):
+ *   pi0[p] = sigmoid(sum_k nu_k logit(pi[p + k])) over the 3x3 stencil of prm->nu. A neighbour outside the
+ *   frame enters with pi = 0.5 (no information); faulty pixels have pi = 0.5 as input and output
+ *   (Sec. III-B); pi is clamped to [1e-7, 1 - 1e-7] before the logit. pi_in, pi_out: [P] float, must not
+ *   alias. faulty nullable.
+ */
+SPL_API spl_status spl_pi_propagate(const spl_params* prm, const float* pi_in, const uint8_t* faulty, float* pi_out,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPL_H */

@@ -1,0 +1,216 @@
+"""Python binding of libspl (include/spl.h): robust single-photon lidar depth estimation and online
+spatio-temporal filtering after Legros et al., "Robust 3D reconstruction of dynamic scenes from single-photon
+lidar using Beta-divergences" (arXiv 2004.09211), on sm_103a.
+
+The functions below carry the C names and only marshal arguments: they check devices, dtypes and shapes of
+torch tensors, allocate outputs with torch when the caller passes none, and hand raw device pointers and the
+current CUDA stream to the library. Every step of the computation runs in the library's CUDA kernels; there is
+no CPU or PyTorch fallback, and a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import torch
+
+from . import _abi
+from ._abi import (SPL_HIST_F16, SPL_HIST_F32, SPL_HIST_U16, SPL_MAX_BINS, SPL_MAX_TAPS, SplError,
+                   spl_hist, spl_params)
+
+__all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate",
+           "spl_filter_step", "spl_state_init", "spl_pi_propagate", "SplError", "spl_params", "spl_hist",
+           "load_library", "cross_weights"]
+
+_FMT = {torch.uint16: SPL_HIST_U16, torch.float16: SPL_HIST_F16, torch.float32: SPL_HIST_F32}
+
+
+def load_library():
+    """Load (building first if needed) the CUDA library; returns the ctypes handle."""
+    return _abi.load()
+
+
+def cross_weights(nu0: float = 0.5):
+    """The paper's M = 5 neighbourhood weights (Sec. III-A): nu0 at the centre, (1 - nu0)/4 on N, S, E, W."""
+    w = [0.0] * 9
+    w[4] = nu0
+    for k in (1, 3, 5, 7):
+        w[k] = (1.0 - nu0) / 4.0
+    return w
+
+
+def make_params(H: int, W: int, T: int, L: int, peak: int, dmin: int | None = None, dmax: int | None = None,
+                beta: float = 0.5, sigma_rw2: float = 3.0, nu=None) -> spl_params:
+    """spl_params with dmin/dmax defaulting to the full-support range [peak, T - L + peak] and nu to the
+    M = 5 cross with nu0 = 0.5."""
+    q = spl_params()
+    q.H, q.W, q.T, q.L, q.peak = int(H), int(W), int(T), int(L), int(peak)
+    q.dmin = int(peak if dmin is None else dmin)
+    q.dmax = int(T - L + peak if dmax is None else dmax)
+    q.beta = float(beta)
+    q.sigma_rw2 = float(sigma_rw2)
+    w = cross_weights(0.5) if nu is None else [float(x) for x in (nu.tolist() if hasattr(nu, "tolist") else nu)]
+    assert len(w) == 9
+    for k in range(9):
+        q.nu[k] = w[k]
+    return q
+
+
+def spl_version() -> str:
+    return _abi.load().spl_version().decode()
+
+
+def spl_last_error() -> str:
+    m = _abi.load().spl_last_error()
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------------------------------------
+
+
+def _P(prm: spl_params) -> int:
+    return prm.H * prm.W
+
+
+def _D(prm: spl_params) -> int:
+    return prm.dmax - prm.dmin + 1
+
+
+def _dev(t: torch.Tensor | None, name: str, dtype, numel: int | None = None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype} (got {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements (got {t.numel()})")
+    return t.data_ptr()
+
+
+def _hist(prm: spl_params, z: torch.Tensor) -> spl_hist:
+    if not isinstance(z, torch.Tensor) or z.device.type != "cuda":
+        raise TypeError("z must be a CUDA tensor")
+    if z.dtype not in _FMT:
+        raise TypeError(f"z must be uint16, float16 or float32 (got {z.dtype})")
+    if not z.is_contiguous():
+        raise ValueError("z must be contiguous ([..., pitch] rows)")
+    pitch = z.shape[-1]
+    if z.numel() != _P(prm) * pitch:
+        raise ValueError(f"z has {z.numel()} elements; expected H*W*pitch = {_P(prm)}*{pitch}")
+    hz = spl_hist()
+    hz.fmt = _FMT[z.dtype]
+    hz.data = z.data_ptr()
+    hz.pitch = pitch
+    return hz
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _empty(shape, dtype, like: torch.Tensor):
+    return torch.empty(shape, dtype=dtype, device=like.device)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# the C entry points
+# ---------------------------------------------------------------------------------------------------------
+
+
+def spl_depth_cost(prm: spl_params, z: torch.Tensor, h: torch.Tensor, cost: torch.Tensor | None = None,
+                   argmax: torch.Tensor | None = None, want_cost: bool = True, stream=None):
+    """C(d) for every candidate (Eq. beta_div2, histogram form) and its argmax. Returns (cost, argmax)."""
+    P, D = _P(prm), _D(prm)
+    if cost is None and want_cost:
+        cost = _empty((P, D), torch.float32, z)
+    if argmax is None:
+        argmax = _empty((P,), torch.int32, z)
+    lib = _abi.load()
+    hz = _hist(prm, z)
+    _abi.check(lib.spl_depth_cost(ct.byref(prm), ct.byref(hz), _dev(h, "h", torch.float32, prm.L),
+                                  _dev(cost, "cost", torch.float32, P * D), _dev(argmax, "argmax", torch.int32, P),
+                                  _stream(stream)))
+    return cost, argmax
+
+
+def spl_depth_estimate(prm: spl_params, z: torch.Tensor, h: torch.Tensor, prior_mu=None, prior_var=None,
+                       present=None, intensity: bool = True, out: dict | None = None, stream=None) -> dict:
+    """Single-frame pseudo-posterior estimate (Eq. approx_post). Returns dict(argmax, mu, var[, refl, bg])."""
+    P = _P(prm)
+    o = dict(out or {})
+    o.setdefault("argmax", _empty((P,), torch.int32, z))
+    o.setdefault("mu", _empty((P,), torch.float32, z))
+    o.setdefault("var", _empty((P,), torch.float32, z))
+    if intensity:
+        o.setdefault("refl", _empty((P,), torch.float32, z))
+        o.setdefault("bg", _empty((P,), torch.float32, z))
+    lib = _abi.load()
+    hz = _hist(prm, z)
+    _abi.check(lib.spl_depth_estimate(
+        ct.byref(prm), ct.byref(hz), _dev(h, "h", torch.float32, prm.L),
+        _dev(prior_mu, "prior_mu", torch.float32, P), _dev(prior_var, "prior_var", torch.float32, P),
+        _dev(present, "present", torch.uint8, P), _dev(o["argmax"], "argmax", torch.int32, P),
+        _dev(o["mu"], "mu", torch.float32, P), _dev(o["var"], "var", torch.float32, P),
+        _dev(o.get("refl"), "refl", torch.float32, P), _dev(o.get("bg"), "bg", torch.float32, P),
+        _stream(stream)))
+    return o
+
+
+def spl_filter_step(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor, var_in: torch.Tensor,
+                    present_in=None, faulty=None, present_now=None, intensity: bool = True,
+                    out: dict | None = None, stream=None) -> dict:
+    """One frame of the online filter (Algorithm 1). Returns dict(mu, var, argmax[, refl, bg])."""
+    P = _P(prm)
+    o = dict(out or {})
+    o.setdefault("mu", _empty((P,), torch.float32, z))
+    o.setdefault("var", _empty((P,), torch.float32, z))
+    o.setdefault("argmax", _empty((P,), torch.int32, z))
+    if intensity:
+        o.setdefault("refl", _empty((P,), torch.float32, z))
+        o.setdefault("bg", _empty((P,), torch.float32, z))
+    lib = _abi.load()
+    hz = _hist(prm, z)
+    _abi.check(lib.spl_filter_step(
+        ct.byref(prm), ct.byref(hz), _dev(h, "h", torch.float32, prm.L),
+        _dev(mu_in, "mu_in", torch.float32, P), _dev(var_in, "var_in", torch.float32, P),
+        _dev(present_in, "present_in", torch.uint8, P), _dev(faulty, "faulty", torch.uint8, P),
+        _dev(present_now, "present_now", torch.uint8, P),
+        _dev(o["mu"], "mu", torch.float32, P), _dev(o["var"], "var", torch.float32, P),
+        _dev(o.get("argmax"), "argmax", torch.int32, P),
+        _dev(o.get("refl"), "refl", torch.float32, P), _dev(o.get("bg"), "bg", torch.float32, P),
+        _stream(stream)))
+    return o
+
+
+def spl_state_init(prm: spl_params, mu: torch.Tensor | None = None, var: torch.Tensor | None = None,
+                   device="cuda", stream=None):
+    """Initial Gaussians of Algorithm 1 (the weakly informative Gaussian everywhere). Returns (mu, var)."""
+    P = _P(prm)
+    if mu is None:
+        mu = torch.empty(P, dtype=torch.float32, device=device)
+    if var is None:
+        var = torch.empty(P, dtype=torch.float32, device=mu.device)
+    lib = _abi.load()
+    _abi.check(lib.spl_state_init(ct.byref(prm), _dev(mu, "mu", torch.float32, P),
+                                  _dev(var, "var", torch.float32, P), _stream(stream)))
+    return mu, var
+
+
+def spl_pi_propagate(prm: spl_params, pi_in: torch.Tensor, faulty=None, pi_out=None, stream=None):
+    """Prior presence probabilities for the next frame (Eq. prior_detect). Returns pi_out."""
+    P = _P(prm)
+    if pi_out is None:
+        pi_out = torch.empty_like(pi_in)
+    lib = _abi.load()
+    _abi.check(lib.spl_pi_propagate(ct.byref(prm), _dev(pi_in, "pi_in", torch.float32, P),
+                                    _dev(faulty, "faulty", torch.uint8, P), _dev(pi_out, "pi_out", torch.float32, P),
+                                    _stream(stream)))
+    return pi_out

@@ -1,0 +1,81 @@
+"""ctypes view of the C ABI in include/spl.h (no torch here).
+
+The shared library is the in-tree build paper_2004_09211_gb300/lib/libspl.so. Loading fails loudly when it
+is missing: there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libspl.so")
+
+SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ETIMEOUT, SPL_EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "SPL_OK", 1: "SPL_EINVAL", 2: "SPL_ENOMEM", 3: "SPL_ECUDA", 4: "SPL_ETIMEOUT",
+                5: "SPL_EUNSUPPORTED"}
+SPL_HIST_U16, SPL_HIST_F16, SPL_HIST_F32 = 0, 1, 2
+SPL_MAX_TAPS = 128
+SPL_MAX_BINS = 8192
+
+
+class spl_params(ct.Structure):
+    _fields_ = [("H", ct.c_int32), ("W", ct.c_int32), ("T", ct.c_int32), ("L", ct.c_int32),
+                ("peak", ct.c_int32), ("dmin", ct.c_int32), ("dmax", ct.c_int32), ("beta", ct.c_float),
+                ("sigma_rw2", ct.c_float), ("nu", ct.c_float * 9)]
+
+
+class spl_hist(ct.Structure):
+    _fields_ = [("fmt", ct.c_int), ("data", ct.c_void_p), ("pitch", ct.c_int64)]
+
+
+# name -> (restype, argtypes); mirrors include/spl.h
+_P = ct.POINTER(spl_params)
+_Hh = ct.POINTER(spl_hist)
+_vp = ct.c_void_p
+SIGNATURES = {
+    "spl_version": (ct.c_char_p, []),
+    "spl_last_error": (ct.c_char_p, []),
+    "spl_depth_cost": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp]),
+    "spl_depth_estimate": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "spl_filter_step": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "spl_state_init": (ct.c_int, [_P, _vp, _vp, _vp]),
+    "spl_pi_propagate": (ct.c_int, [_P, _vp, _vp, _vp, _vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SplError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str | None = None) -> ct.CDLL:
+    """Load libspl.so (building it first if the sources are newer). Raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if path is None:
+                from . import build as _build
+                if not _build.up_to_date():
+                    _build.build()
+            if not os.path.exists(p):
+                raise RuntimeError(f"libspl.so not found at {p}; build it with paper_2004_09211_gb300.build")
+            lib = ct.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != SPL_OK:
+        msg = load().spl_last_error()
+        raise SplError(status, msg.decode() if msg else "")

@@ -1,0 +1,214 @@
+// Host side of the C ABI declared in include/spl.h: argument validation, launch configuration, error
+// reporting. No call allocates, synchronises or copies device data.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "spl_internal.h"
+
+namespace spl {
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
+
+#define SPL_REQUIRE(cond, ...)              \
+    do {                                    \
+        if (!(cond)) {                      \
+            set_error(__VA_ARGS__);         \
+            return SPL_EINVAL;              \
+        }                                   \
+    } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t elem_size(int fmt) { return fmt == SPL_HIST_F32 ? 4 : 2; }
+
+// Geometry, domain and parameter checks shared by the depth calls (the domain reading is stated in spl.h).
+spl_status check_params(const spl_params* q, bool need_filter) {
+    SPL_REQUIRE(q != nullptr, "prm is NULL");
+    SPL_REQUIRE(q->H >= 1 && q->W >= 1, "H and W must be >= 1 (got %d x %d)", q->H, q->W);
+    SPL_REQUIRE(static_cast<long long>(q->H) * q->W <= (1LL << 31) - 1, "H*W exceeds 2^31-1");
+    SPL_REQUIRE(q->L >= 1, "L must be >= 1 (got %d)", q->L);
+    SPL_REQUIRE(q->T >= q->L, "T (%d) must be >= L (%d)", q->T, q->L);
+    SPL_REQUIRE(q->peak >= 0 && q->peak < q->L, "peak (%d) must be in [0, L)", q->peak);
+    SPL_REQUIRE(q->dmin <= q->dmax, "dmin (%d) > dmax (%d)", q->dmin, q->dmax);
+    SPL_REQUIRE(q->dmin >= q->peak && q->dmax <= q->T - q->L + q->peak,
+                "candidate depths [%d, %d] leave the full-support range [%d, %d]", q->dmin, q->dmax, q->peak,
+                q->T - q->L + q->peak);
+    SPL_REQUIRE(q->beta > 0.f && isfinite(q->beta), "beta must be finite and > 0 (got %g)", q->beta);
+    if (q->L > SPL_MAX_TAPS || q->T > SPL_MAX_BINS) {
+        set_error("L (%d) above %d or T (%d) above %d is not supported by this build", q->L, SPL_MAX_TAPS, q->T,
+                  SPL_MAX_BINS);
+        return SPL_EUNSUPPORTED;
+    }
+    if (need_filter) {
+        SPL_REQUIRE(q->sigma_rw2 > 0.f && isfinite(q->sigma_rw2), "sigma_rw2 must be finite and > 0 (got %g)",
+                    q->sigma_rw2);
+        float s = 0.f;
+        for (int k = 0; k < 9; ++k) {
+            SPL_REQUIRE(q->nu[k] >= 0.f && isfinite(q->nu[k]), "nu[%d] must be finite and >= 0 (got %g)", k,
+                        q->nu[k]);
+            s += q->nu[k];
+        }
+        SPL_REQUIRE(s > 0.f, "the mixture weights nu sum to 0");
+    }
+    return SPL_OK;
+}
+
+spl_status check_hist(const spl_params* q, const spl_hist* z) {
+    SPL_REQUIRE(z != nullptr && z->data != nullptr, "histogram z (or z->data) is NULL");
+    SPL_REQUIRE(z->fmt == SPL_HIST_U16 || z->fmt == SPL_HIST_F16 || z->fmt == SPL_HIST_F32,
+                "unknown histogram format %d", static_cast<int>(z->fmt));
+    SPL_REQUIRE(z->pitch >= q->T, "pitch (%lld) < T (%d)", static_cast<long long>(z->pitch), q->T);
+    SPL_REQUIRE((z->pitch * static_cast<int64_t>(elem_size(z->fmt))) % 16 == 0,
+                "pitch * element size must be a multiple of 16 bytes (pitch %lld)",
+                static_cast<long long>(z->pitch));
+    SPL_REQUIRE(aligned16(z->data), "z->data must be 16-byte aligned");
+    return SPL_OK;
+}
+
+spl_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SPL_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return SPL_ECUDA;
+}
+
+EstimateArgs base_args(const spl_params* q, const spl_hist* z, const float* h) {
+    EstimateArgs a;
+    memset(&a, 0, sizeof(a));
+    a.z = z->data;
+    a.pitch = z->pitch;
+    a.fmt = z->fmt;
+    a.h = h;
+    a.H = q->H;
+    a.W = q->W;
+    a.T = q->T;
+    a.L = q->L;
+    a.peak = q->peak;
+    a.dmin = q->dmin;
+    a.D = q->dmax - q->dmin + 1;
+    a.beta = q->beta;
+    a.lam2 = static_cast<float>((static_cast<double>(q->beta) + 1.0) / q->beta * 1.4426950408889634);
+    a.sigma_rw2 = q->sigma_rw2;
+    a.flat_m = 0.5f * static_cast<float>(q->dmin + q->dmax);
+    const double span = static_cast<double>(q->dmax - q->dmin);
+    a.flat_v = static_cast<float>(span * span / 12.0);
+    for (int k = 0; k < 9; ++k) a.nu[k] = q->nu[k];
+    return a;
+}
+
+}  // namespace
+}  // namespace spl
+
+using namespace spl;
+
+extern "C" {
+
+const char* spl_version(void) { return "libspl 0.1 (sm_103a)"; }
+
+const char* spl_last_error(void) { return g_err; }
+
+spl_status spl_depth_cost(const spl_params* prm, const spl_hist* z, const float* h, float* cost, int32_t* argmax,
+                          void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, false);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(cost != nullptr || argmax != nullptr, "both cost and argmax are NULL: nothing to compute");
+    EstimateArgs a = base_args(prm, z, h);
+    a.cost = cost;
+    a.argmax = argmax;
+    return cuda_status(launch_estimate(a, true, static_cast<cudaStream_t>(stream)), "spl_depth_cost launch");
+}
+
+spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, const float* h, const float* prior_mu,
+                              const float* prior_var, const uint8_t* present, int32_t* argmax, float* mu,
+                              float* var, float* refl, float* bg, void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, false);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(mu != nullptr && var != nullptr, "mu and var outputs are required");
+    SPL_REQUIRE((prior_mu == nullptr) == (prior_var == nullptr), "give both prior_mu and prior_var or neither");
+    SPL_REQUIRE((refl == nullptr) == (bg == nullptr), "give both refl and bg or neither");
+    EstimateArgs a = base_args(prm, z, h);
+    a.prior_mode = prior_mu ? PRIOR_GAUSS : PRIOR_UNIFORM;
+    a.pmu = prior_mu;
+    a.pvar = prior_var;
+    a.argmax = argmax;
+    a.mu = mu;
+    a.var = var;
+    a.refl = refl;
+    a.bg = bg;
+    a.present_now = present;
+    return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_depth_estimate launch");
+}
+
+spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                           const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                           const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
+                           float* refl, float* bg, void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, true);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(mu_in && var_in && mu_out && var_out, "mu_in, var_in, mu_out and var_out are required");
+    SPL_REQUIRE(mu_out != mu_in && var_out != var_in && mu_out != var_in && var_out != mu_in,
+                "outputs must not alias the previous-frame state");
+    SPL_REQUIRE((refl == nullptr) == (bg == nullptr), "give both refl and bg or neither");
+    EstimateArgs a = base_args(prm, z, h);
+    a.prior_mode = PRIOR_STENCIL;
+    a.pmu = mu_in;
+    a.pvar = var_in;
+    a.present_in = present_in;
+    a.faulty = faulty;
+    a.present_now = present_now;
+    a.argmax = argmax;
+    a.mu = mu_out;
+    a.var = var_out;
+    a.refl = refl;
+    a.bg = bg;
+    return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_filter_step launch");
+}
+
+spl_status spl_state_init(const spl_params* prm, float* mu, float* var, void* stream) {
+    g_err[0] = 0;
+    SPL_REQUIRE(prm != nullptr, "prm is NULL");
+    SPL_REQUIRE(prm->H >= 1 && prm->W >= 1, "H and W must be >= 1");
+    SPL_REQUIRE(prm->dmin <= prm->dmax, "dmin > dmax");
+    SPL_REQUIRE(mu != nullptr && var != nullptr, "mu and var are required");
+    const double span = static_cast<double>(prm->dmax - prm->dmin);
+    return cuda_status(launch_state_init(prm->H * prm->W, 0.5f * static_cast<float>(prm->dmin + prm->dmax),
+                                         static_cast<float>(span * span / 12.0), mu, var,
+                                         static_cast<cudaStream_t>(stream)),
+                       "spl_state_init launch");
+}
+
+spl_status spl_pi_propagate(const spl_params* prm, const float* pi_in, const uint8_t* faulty, float* pi_out,
+                            void* stream) {
+    g_err[0] = 0;
+    SPL_REQUIRE(prm != nullptr, "prm is NULL");
+    SPL_REQUIRE(prm->H >= 1 && prm->W >= 1, "H and W must be >= 1");
+    SPL_REQUIRE(pi_in != nullptr && pi_out != nullptr, "pi_in and pi_out are required");
+    SPL_REQUIRE(pi_in != pi_out, "pi_out must not alias pi_in");
+    for (int k = 0; k < 9; ++k)
+        SPL_REQUIRE(isfinite(prm->nu[k]), "nu[%d] is not finite", k);
+    return cuda_status(launch_pi_propagate(prm->H, prm->W, prm->nu, pi_in, faulty, pi_out,
+                                           static_cast<cudaStream_t>(stream)),
+                       "spl_pi_propagate launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Internal declarations shared by the translation units of libspl (never installed, never part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spl.h"
+
+namespace spl {
+
+enum PriorMode : int {
+    PRIOR_UNIFORM = 0,  // log f(d) = 0 on the grid
+    PRIOR_GAUSS = 1,    // one Gaussian per pixel, N(pmu[p], pvar[p])
+    PRIOR_STENCIL = 2   // Eq. predict: 3x3 Gaussian mixture from the previous frame's state
+};
+
+// Everything one launch of the fused per-pixel kernel needs. Plain device pointers and scalars.
+struct EstimateArgs {
+    // observations
+    const void* z;          // [P][pitch] counts
+    long long pitch;        // elements
+    int fmt;                // spl_hist_format
+    const float* h;         // [L] IRF
+    int H, W, T, L, peak, dmin, D;
+    float beta;
+    float lam2;             // lambda * log2(e), lambda = (beta + 1) / beta
+    // prior
+    int prior_mode;
+    const float* pmu;       // PRIOR_GAUSS: prior mean;  PRIOR_STENCIL: previous-frame mean
+    const float* pvar;      // PRIOR_GAUSS: prior var;   PRIOR_STENCIL: previous-frame variance
+    const uint8_t* present_in;
+    const uint8_t* faulty;
+    float sigma_rw2, flat_m, flat_v;
+    float nu[9];
+    // outputs
+    float* cost;            // [P][D] (cost-only launches)
+    int* argmax;
+    float* mu;
+    float* var;
+    float* refl;
+    float* bg;
+    const uint8_t* present_now;
+};
+
+// Launch geometry chosen on the host for one launch.
+struct Geometry {
+    int warps_per_cta;
+    int ctas;
+    size_t smem_bytes;
+};
+
+// Records a formatted message as this thread's last error.
+void set_error(const char* fmt, ...);
+
+// Kernel launchers (estimate.cu / aux.cu). They return cudaSuccess or the launch error.
+cudaError_t launch_estimate(const EstimateArgs& a, bool cost_only, cudaStream_t s);
+cudaError_t launch_state_init(int P, float m, float v, float* mu, float* var, cudaStream_t s);
+cudaError_t launch_pi_propagate(int H, int W, const float* nu, const float* pi_in, const uint8_t* faulty,
+                                float* pi_out, cudaStream_t s);
+
+}  // namespace spl

@@ -1,0 +1,108 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads, exports every entry point that
+include/spl.h declares, and rejects invalid arguments on the host before anything is launched."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_2004_09211_gb300 import _abi, make_params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"SPL_API\s+[\w\s\*]+?\b(spl_\w+)\s*\(", src)
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    lib = _abi.load()
+    names = declared_entry_points()
+    assert len(names) >= 7
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported by libspl.so"
+        assert n in _abi.SIGNATURES, f"{n} has no ctypes signature in the binding"
+
+
+def test_version_and_empty_error():
+    lib = _abi.load()
+    assert b"sm_103a" in lib.spl_version()
+
+
+def _call_cost(prm, data=0x1000, pitch=None, fmt=_abi.SPL_HIST_U16, h=0x2000, cost=0x3000, argmax=0x4000):
+    lib = _abi.load()
+    hz = _abi.spl_hist()
+    hz.fmt = fmt
+    hz.data = data
+    hz.pitch = prm.T if pitch is None else pitch
+    st = lib.spl_depth_cost(ct.byref(prm), ct.byref(hz), h, cost, argmax, None)
+    return st, lib.spl_last_error().decode()
+
+
+@pytest.mark.parametrize("mut, needle", [
+    (dict(dmin=5), "full-support"),                 # below peak
+    (dict(dmax=10_000), "full-support"),
+    (dict(beta=0.0), "beta"),
+    (dict(beta=float("nan")), "beta"),
+    (dict(L=0), "L must"),
+    (dict(T=10, L=20), "T (10) must be >= L"),
+    (dict(peak=30), "peak"),
+    (dict(H=0), "H and W"),
+])
+def test_invalid_parameters_rejected_on_host(mut, needle):
+    kw = dict(H=4, W=4, T=64, L=25, peak=12, dmin=12, dmax=51, beta=0.5)
+    kw.update(mut)
+    prm = make_params(kw["H"], kw["W"], kw["T"], kw["L"], kw["peak"], kw["dmin"], kw["dmax"], beta=kw["beta"])
+    st, msg = _call_cost(prm)
+    assert st == _abi.SPL_EINVAL, (st, msg)
+    assert needle in msg
+
+
+def test_histogram_layout_rejected_on_host():
+    prm = make_params(4, 4, 60, 25, 12)
+    assert _call_cost(prm, pitch=59)[0] == _abi.SPL_EINVAL                  # pitch < T
+    st, msg = _call_cost(prm, pitch=60)                                       # 120 B rows: not 16-B multiple
+    assert st == _abi.SPL_EINVAL and "16 bytes" in msg
+    assert _call_cost(prm, pitch=64, data=0x1008)[0] == _abi.SPL_EINVAL      # misaligned base
+    assert _call_cost(prm, pitch=64, fmt=7)[0] == _abi.SPL_EINVAL
+    assert _call_cost(prm, pitch=64, data=0)[0] == _abi.SPL_EINVAL
+    assert _call_cost(prm, pitch=64, cost=0, argmax=0)[0] == _abi.SPL_EINVAL
+
+
+def test_unsupported_sizes_reported():
+    prm = make_params(4, 4, 600, 200, 100)
+    st, msg = _call_cost(prm, pitch=600)
+    assert st == _abi.SPL_EUNSUPPORTED and "not supported" in msg
+
+
+def test_filter_argument_checks():
+    lib = _abi.load()
+    prm = make_params(4, 4, 64, 25, 12, sigma_rw2=0.0)
+    hz = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 64)
+    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                             0x6000, None, None, None, None)
+    assert st == _abi.SPL_EINVAL and "sigma_rw2" in lib.spl_last_error().decode()
+    prm = make_params(4, 4, 64, 25, 12, nu=[0] * 9)
+    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                             0x6000, None, None, None, None)
+    assert st == _abi.SPL_EINVAL and "sum to 0" in lib.spl_last_error().decode()
+    prm = make_params(4, 4, 64, 25, 12)
+    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x3000,
+                             0x6000, None, None, None, None)
+    assert st == _abi.SPL_EINVAL and "alias" in lib.spl_last_error().decode()
+    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                             0x6000, None, 0x7000, None, None)
+    assert st == _abi.SPL_EINVAL and "refl and bg" in lib.spl_last_error().decode()
+
+
+def test_pi_and_init_argument_checks():
+    lib = _abi.load()
+    prm = make_params(4, 4, 64, 25, 12)
+    assert lib.spl_pi_propagate(ct.byref(prm), 0x1000, None, 0x1000, None) == _abi.SPL_EINVAL
+    assert lib.spl_state_init(ct.byref(prm), None, 0x1000, None) == _abi.SPL_EINVAL
+    assert lib.spl_pi_propagate(None, 0x1000, None, 0x2000, None) == _abi.SPL_EINVAL

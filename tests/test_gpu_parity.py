@@ -1,0 +1,294 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle, element by element, on seeded
+synthetic inputs shaped like the paper's workloads. Tolerances are documented in tests/parity.py."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2004_09211_gb300 as spl
+from paper_2004_09211_gb300 import synth
+
+from parity import check_argmax, check_close, check_intensity
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _gpu_hist(z_np, T, dtype=torch.uint16):
+    """[..., T] counts -> contiguous device tensor [P, pitch] with 16-byte rows."""
+    z = torch.from_numpy(np.ascontiguousarray(z_np).astype(np.float32)).reshape(-1, T)
+    esz = 4 if dtype == torch.float32 else 2
+    pitch = synth.pad_pitch(T, esz)
+    if dtype == torch.uint16:
+        z = z.to(torch.int32).to(torch.uint16)
+    else:
+        z = z.to(dtype)
+    return synth.pitched(z, pitch).to(DEV)
+
+
+def single_frame_inputs(H=32, W=32, T=1024, seed=1, signal=10.0, bg_total=50.0):
+    """The single-frame workload: Gaussian IRF sigma = 3 bins over +-12 taps, smooth random surface scaled
+    to bins 100..900, Poisson signal mean `signal` at the shifted IRF plus background `bg_total` over all
+    bins."""
+    h, peak = synth.gaussian_irf(3.0, 12)
+    depth = synth.smooth_depth_map(H, W, 100, 900, seed)
+    g = torch.Generator().manual_seed(seed)
+    mean = synth.expected_counts(torch.from_numpy(depth), torch.full((H, W), signal, dtype=torch.float64),
+                                 bg_total / T, torch.from_numpy(h), peak, T)
+    z = torch.poisson(mean, generator=g).numpy().astype(np.float64)
+    return h, peak, depth, z
+
+
+def video_inputs(H, W, N, T, sbr, seed, L=48):
+    h, peak = synth.asymmetric_irf(L=L)
+    sc = synth.moving_scene(H, W, N, peak + 8, T - L + peak - 8, seed)
+    g = torch.Generator().manual_seed(seed)
+    zs = []
+    for n in range(N):
+        b = float(sc.signal[n].mean()) / (sbr * T)
+        mean = synth.expected_counts(torch.from_numpy(sc.depth[n]), torch.from_numpy(sc.signal[n]), b,
+                                     torch.from_numpy(h), peak, T)
+        zs.append(torch.poisson(mean, generator=g).numpy().astype(np.float64))
+    return h, peak, sc, zs
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------------------------------------------------------
+# spl_depth_cost
+# ------------------------------------------------------------------------------------------------------------
+
+
+def test_cost_single_frame(orc):
+    h, peak, depth, z = single_frame_inputs()
+    H, W, T = z.shape
+    q = orc.params(T, len(h), peak, beta=0.5)
+    C_orc = orc.cost(q, h, z).reshape(H * W, -1)
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.5)
+    hd = torch.from_numpy(h).to(DEV)
+    cost, am = spl.spl_depth_cost(prm, _gpu_hist(z, T), hd)
+    torch.cuda.synchronize()
+    check_close(_np(cost), C_orc, "C", atol=1e-6 * C_orc.max())
+    ties = check_argmax(_np(am), C_orc.argmax(1) + q.dmin, C_orc, q.dmin, "argmax C")
+    assert ties <= 2
+    # noiseless-enough surfaces: the minimum-divergence argmax lands on the true depth for most pixels
+    assert np.mean(np.abs(_np(am).reshape(H, W) - depth) <= 3) > 0.9
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.float32])
+def test_cost_formats_agree_exactly(orc, dtype):
+    """Counts are exact in every storage format, so the three formats give bit-identical C(d)."""
+    h, peak, depth, z = single_frame_inputs(H=8, W=12, T=1000, seed=3)
+    H, W, T = z.shape
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.5)
+    hd = torch.from_numpy(h).to(DEV)
+    c16, a16 = spl.spl_depth_cost(prm, _gpu_hist(z, T, torch.uint16), hd)
+    cx, ax = spl.spl_depth_cost(prm, _gpu_hist(z, T, dtype), hd)
+    torch.cuda.synchronize()
+    assert torch.equal(c16, cx) and torch.equal(a16, ax)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# spl_depth_estimate
+# ------------------------------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("beta", [0.2, 0.5, 1.0])
+def test_estimate_uniform_prior(orc, beta):
+    h, peak, depth, z = single_frame_inputs(seed=11)
+    H, W, T = z.shape
+    q = orc.params(T, len(h), peak, beta=beta)
+    e = orc.estimate(q, h, z, want_ell=True)
+    prm = spl.make_params(H, W, T, len(h), peak, beta=beta)
+    o = spl.spl_depth_estimate(prm, _gpu_hist(z, T), torch.from_numpy(h).to(DEV))
+    torch.cuda.synchronize()
+    check_argmax(_np(o["argmax"]), e["argmax"], e["ell"], q.dmin)
+    check_close(_np(o["mu"]), e["mu"], "mu")
+    check_close(_np(o["var"]), e["var"], "var", atol=1e-6)
+    check_intensity(orc, q, h, z, _np(o["mu"]), e["mu"], _np(o["refl"]), _np(o["bg"]))
+
+
+def test_estimate_gaussian_prior_and_presence(orc):
+    h, peak, depth, z = single_frame_inputs(H=16, W=20, seed=12, signal=4.0, bg_total=200.0)
+    H, W, T = z.shape
+    rng = np.random.default_rng(12)
+    pm = (depth + rng.normal(0, 15, size=depth.shape)).astype(np.float32)
+    pv = rng.uniform(1.0, 400.0, size=depth.shape).astype(np.float32)
+    present = (rng.random(depth.shape) < 0.7).astype(np.uint8)
+    q = orc.params(T, len(h), peak, beta=0.4)
+    e = orc.estimate(q, h, z, prior_mu=pm, prior_var=pv, want_ell=True)
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.4)
+    o = spl.spl_depth_estimate(prm, _gpu_hist(z, T), torch.from_numpy(h).to(DEV),
+                               prior_mu=torch.from_numpy(pm).to(DEV).reshape(-1),
+                               prior_var=torch.from_numpy(pv).to(DEV).reshape(-1),
+                               present=torch.from_numpy(present).to(DEV).reshape(-1))
+    torch.cuda.synchronize()
+    check_argmax(_np(o["argmax"]), e["argmax"], e["ell"], q.dmin)
+    check_close(_np(o["mu"]), e["mu"], "mu")
+    check_close(_np(o["var"]), e["var"], "var", atol=1e-6)
+    check_intensity(orc, q, h, z, _np(o["mu"]), e["mu"], _np(o["refl"]), _np(o["bg"]), present=present)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# spl_filter_step over short videos
+# ------------------------------------------------------------------------------------------------------------
+
+
+def _run_filter(orc, q, prm, h, zs, T, present=None, faulty=None, present_now=None, dtype=torch.uint16):
+    """Runs the GPU chain and the oracle chain independently and compares every frame."""
+    H, W = prm.H, prm.W
+    hd = torch.from_numpy(h).to(DEV)
+    mu_g, var_g = spl.spl_state_init(prm)
+    mu_o, var_o = orc.state_init(q, H, W)
+    dp = lambda a: None if a is None else torch.from_numpy(a).to(DEV).reshape(-1)
+    ties = 0
+    for n, z in enumerate(zs):
+        o = spl.spl_filter_step(prm, _gpu_hist(z, T, dtype), hd, mu_g, var_g, present_in=dp(present),
+                                faulty=dp(faulty), present_now=dp(present_now))
+        e = orc.filter_step(q, h, z, mu_o, var_o, present_in=present, faulty=faulty, want_ell=True)
+        torch.cuda.synchronize()
+        ties += check_argmax(_np(o["argmax"]), e["argmax"], e["ell"], q.dmin, f"argmax frame {n}")
+        check_close(_np(o["mu"]), e["mu"], f"mu frame {n}")
+        check_close(_np(o["var"]), e["var"], f"var frame {n}", atol=1e-6)
+        check_intensity(orc, q, h, z, _np(o["mu"]), e["mu"], _np(o["refl"]), _np(o["bg"]), present=present_now,
+                        faulty=faulty)
+        mu_g, var_g = o["mu"], o["var"]
+        mu_o, var_o = e["mu"], e["var"]
+    return ties
+
+
+@pytest.mark.parametrize("sbr,beta", [(0.01, 0.5), (0.1, 0.2), (1.0, 1.0)])
+def test_filter_video(orc, sbr, beta):
+    H, W, N, T = 20, 24, 5, 400
+    h, peak, sc, zs = video_inputs(H, W, N, T, sbr, seed=200 + int(sbr * 100))
+    q = orc.params(T, len(h), peak, beta=beta, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    prm = spl.make_params(H, W, T, len(h), peak, beta=beta, sigma_rw2=3.0)
+    ties = _run_filter(orc, q, prm, h, zs, T)
+    assert ties <= 3
+
+
+def test_filter_masks_and_stencil(orc):
+    """Absent and faulty pixels, a full asymmetric 3x3 stencil, presence-dependent intensity."""
+    H, W, N, T = 13, 17, 4, 300
+    h, peak, sc, zs = video_inputs(H, W, N, T, 0.1, seed=31, L=32)
+    rng = np.random.default_rng(31)
+    nu = np.array([0.05, 0.10, 0.02, 0.15, 0.40, 0.20, 0.03, 0.05, 0.0])
+    present = (rng.random((H, W)) < 0.8).astype(np.uint8)
+    faulty = (rng.random((H, W)) < 0.05).astype(np.uint8)
+    pnow = (rng.random((H, W)) < 0.6).astype(np.uint8)
+    q = orc.params(T, len(h), peak, beta=0.5, sigma_rw2=2.0, nu=nu)
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.5, sigma_rw2=2.0, nu=nu)
+    _run_filter(orc, q, prm, h, zs, T, present=present, faulty=faulty, present_now=pnow)
+
+
+@pytest.mark.parametrize("H,W,T,L,peak,dmin,dmax", [
+    (1, 37, 77, 1, 0, None, None),          # one-tap IRF, single row
+    (5, 1, 130, 7, 3, 20, 97),              # single column, sub-range of depths
+    (3, 3, 64, 64, 10, None, None),         # L = T: exactly one candidate
+    (7, 9, 333, 45, 40, None, None),        # odd T, padded pitch, D not a multiple of 32
+    (2, 70, 2049, 128, 60, None, None),     # largest supported IRF
+])
+def test_ragged_shapes(orc, H, W, T, L, peak, dmin, dmax):
+    rng = np.random.default_rng(H * 1000 + W)
+    h = rng.uniform(0.0, 1.0, size=L).astype(np.float32)
+    h[peak] = 2.0
+    h /= h.sum()
+    q = orc.params(T, L, peak, dmin, dmax, beta=0.6, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    z = rng.poisson(0.3, size=(H, W, T)).astype(np.float64)
+    dlo, dhi = q.dmin, q.dmax
+    for y in range(H):
+        for x in range(W):
+            d = int(rng.integers(dlo, dhi + 1))
+            z[y, x, d - peak:d - peak + L] += rng.poisson(6 * h)
+    prm = spl.make_params(H, W, T, L, peak, dmin, dmax, beta=0.6, sigma_rw2=3.0)
+    cost, am = spl.spl_depth_cost(prm, _gpu_hist(z, T), torch.from_numpy(h).to(DEV))
+    torch.cuda.synchronize()
+    C = orc.cost(q, h, z).reshape(H * W, -1)
+    check_close(_np(cost), C, "C", atol=1e-6 * C.max())
+    check_argmax(_np(am), C.argmax(1) + q.dmin, C, q.dmin)
+    _run_filter(orc, q, prm, h, [z, z[::-1].copy()], T)
+
+
+def test_empty_histograms_give_the_prior(orc):
+    """No photons: the GPU posterior moments equal the prior's (and the oracle's)."""
+    h, peak = synth.asymmetric_irf(L=48)
+    H, W, T = 6, 6, 500
+    z = np.zeros((H, W, T))
+    q = orc.params(T, len(h), peak, beta=0.5, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.5)
+    _run_filter(orc, q, prm, h, [z, z, z], T)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Auxiliary kernels
+# ------------------------------------------------------------------------------------------------------------
+
+
+def test_pi_propagate(orc):
+    H, W = 33, 45
+    rng = np.random.default_rng(7)
+    pi = rng.uniform(0, 1, size=(H, W)).astype(np.float32)
+    pi[0, :5] = [0.0, 1.0, 1e-9, 1 - 1e-9, 0.5]
+    faulty = (rng.random((H, W)) < 0.05).astype(np.uint8)
+    nu = synth.cross_weights(0.5)
+    prm = spl.make_params(H, W, 64, 8, 4, nu=nu)
+    out = spl.spl_pi_propagate(prm, torch.from_numpy(pi).to(DEV).reshape(-1),
+                               faulty=torch.from_numpy(faulty).to(DEV).reshape(-1))
+    torch.cuda.synchronize()
+    ref = orc.pi_propagate(nu, pi, faulty)
+    check_close(_np(out), ref, "pi0", rtol=1e-5, atol=1e-6)
+
+
+def test_state_init(orc):
+    prm = spl.make_params(5, 7, 300, 20, 6, dmin=30, dmax=250)
+    mu, var = spl.spl_state_init(prm)
+    torch.cuda.synchronize()
+    q = orc.params(300, 20, 6, 30, 250)
+    m, v = orc.state_init(q, 5, 7)
+    check_close(_np(mu), m, "mu0", rtol=0)
+    check_close(_np(var), v, "var0", rtol=1e-7)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Full-size frame (the video workload's 256 x 256 x 1500 geometry), checked on sampled pixels
+# ------------------------------------------------------------------------------------------------------------
+
+
+def test_full_size_video_frames_sampled(orc):
+    """Two frames of a 256 x 256, T = 1500 video with the full launch configuration, compared on sampled
+    pixels: after n frames a pixel depends only on inputs within Chebyshev distance n (the oracle's
+    dependency-cone pin), so the oracle runs on (2n+1)^2 crops."""
+    H = W = 256
+    N, T, L = 2, 1500, 48
+    h, peak = synth.asymmetric_irf(L=L)
+    sc = synth.moving_scene(H, W, N, peak + 8, T - L + peak - 8, seed=251)
+    g = torch.Generator(device=DEV).manual_seed(251)
+    hd = torch.from_numpy(h).to(DEV)
+    prm = spl.make_params(H, W, T, L, peak, beta=0.5, sigma_rw2=3.0)
+    pitch = synth.pad_pitch(T)
+    zs = []
+    for n in range(N):
+        b = float(sc.signal[n].mean()) / (0.1 * T)
+        mean = synth.expected_counts(torch.from_numpy(sc.depth[n]).to(DEV), torch.from_numpy(sc.signal[n]).to(DEV),
+                                     b, hd, peak, T)
+        zs.append(synth.pitched(synth.poisson_histograms(mean, g).reshape(-1, T), pitch))
+    mu, var = spl.spl_state_init(prm)
+    for n in range(N):
+        o = spl.spl_filter_step(prm, zs[n], hd, mu, var)
+        mu, var = o["mu"], o["var"]
+    torch.cuda.synchronize()
+    q = orc.params(T, L, peak, beta=0.5, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    samples = [(0, 0), (0, 255), (255, 0), (255, 255), (128, 77), (3, 200), (200, 1), (97, 254)]
+    zc = [z[:, :T].reshape(H, W, T) for z in zs]
+    for (y, x) in samples:
+        y0, y1 = max(0, y - N), min(H, y + N + 1)
+        x0, x1 = max(0, x - N), min(W, x + N + 1)
+        m, v = orc.state_init(q, y1 - y0, x1 - x0)
+        for n in range(N):
+            crop = _np(zc[n][y0:y1, x0:x1]).astype(np.float64)
+            e = orc.filter_step(q, h, crop, m, v)
+            m, v = e["mu"], e["var"]
+        check_close(_np(mu.reshape(H, W)[y, x]), m[y - y0, x - x0], f"mu[{y},{x}]")
+        check_close(_np(var.reshape(H, W)[y, x]), v[y - y0, x - x0], f"var[{y},{x}]", atol=1e-6)
