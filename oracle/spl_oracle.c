@@ -355,7 +355,9 @@ void orc_intensity(const orc_params* q, const double* h, const double* z, long P
 
 /* pi0[p] = sigmoid(sum_k nu_k logit(pi[p + k])). Readings: a neighbour outside the image enters with
  * pi = 0.5 (logit 0, no information); a faulty pixel has pi = 0.5 (Sec. III-B), both as input and as
- * output; pi is clamped to [1e-7, 1 - 1e-7] before the logit. */
+ * output; pi is limited to [1e-7, 1 - 1e-7] before the logit, applied as the equivalent clamp of the logit
+ * to +-log(1e7 - 1) (logit is monotone), so that a single-precision implementation clamps at the same
+ * value. */
 void orc_pi_propagate(int H, int W, const double* nu, const double* pi_in, const uint8_t* faulty,
                       double* pi_out) {
     for (int y = 0; y < H; ++y)
@@ -373,9 +375,11 @@ void orc_pi_propagate(int H, int W, const double* nu, const double* pi_in, const
                     const long i = (long)yy * W + xx;
                     v = (faulty && faulty[i]) ? 0.5 : pi_in[i];
                 }
-                if (v < 1e-7) v = 1e-7;
-                if (v > 1.0 - 1e-7) v = 1.0 - 1e-7;
-                a += nu[k] * log(v / (1.0 - v));
+                const double lmax = log(1e7 - 1.0);
+                double lg = log(v) - log1p(-v);
+                if (!(lg > -lmax)) lg = -lmax;
+                if (!(lg < lmax)) lg = lmax;
+                a += nu[k] * lg;
             }
             pi_out[p] = 1.0 / (1.0 + exp(-a));
         }

@@ -15,11 +15,15 @@ __global__ void k_state_init(long long P, float m, float v, float* mu, float* va
     }
 }
 
+constexpr float kLogitMax = 16.1180956f;  // log(1e7 - 1)
+
 struct Nu {
     float w[9];
 };
 
-// pi0 = sigmoid(sum_k nu_k logit(clamp(pi[p + k]))) with out-of-view neighbours and faulty pixels at 0.5.
+// pi0 = sigmoid(sum_k nu_k logit(pi[p + k])) with out-of-view neighbours and faulty pixels at 0.5. pi is
+// limited to [1e-7, 1 - 1e-7] through the equivalent clamp of its logit to +-log(1e7 - 1): 1 - 1e-7 has no
+// exact float, while the logit bound is the same in every precision.
 __global__ void k_pi_propagate(int H, int W, Nu nu, const float* __restrict__ pi_in,
                                const uint8_t* __restrict__ faulty, float* __restrict__ pi_out) {
     const long long P = static_cast<long long>(H) * W;
@@ -39,8 +43,9 @@ __global__ void k_pi_propagate(int H, int W, Nu nu, const float* __restrict__ pi
                 const long long i = static_cast<long long>(yy) * W + xx;
                 v = (faulty && faulty[i]) ? 0.5f : pi_in[i];
             }
-            v = fminf(fmaxf(v, 1e-7f), 1.f - 1e-7f);
-            acc = fmaf(nu.w[k], logf(v / (1.f - v)), acc);
+            float lg = logf(v) - log1pf(-v);   // 1 - v is exact for v >= 0.5
+            lg = fminf(fmaxf(lg, -kLogitMax), kLogitMax);
+            acc = fmaf(nu.w[k], lg, acc);
         }
         pi_out[p] = 1.f / (1.f + expf(-acc));
     }
