@@ -61,8 +61,9 @@ def _np(t):
 # ------------------------------------------------------------------------------------------------------------
 
 
-def test_cost_single_frame(orc):
-    h, peak, depth, z = single_frame_inputs()
+@pytest.mark.parametrize("bg_total", [50.0, 3000.0])
+def test_cost_single_frame(orc, bg_total):
+    h, peak, depth, z = single_frame_inputs(bg_total=bg_total)
     H, W, T = z.shape
     q = orc.params(T, len(h), peak, beta=0.5)
     C_orc = orc.cost(q, h, z).reshape(H * W, -1)
@@ -73,8 +74,8 @@ def test_cost_single_frame(orc):
     check_close(_np(cost), C_orc, "C", atol=1e-6 * C_orc.max())
     ties = check_argmax(_np(am), C_orc.argmax(1) + q.dmin, C_orc, q.dmin, "argmax C")
     assert ties <= 2
-    # noiseless-enough surfaces: the minimum-divergence argmax lands on the true depth for most pixels
-    assert np.mean(np.abs(_np(am).reshape(H, W) - depth) <= 3) > 0.9
+    if bg_total < 100:   # strong enough signal: the minimum-divergence argmax lands on the true depth
+        assert np.mean(np.abs(_np(am).reshape(H, W) - depth) <= 3) > 0.8
 
 
 @pytest.mark.parametrize("dtype", [torch.float16, torch.float32])
@@ -95,9 +96,10 @@ def test_cost_formats_agree_exactly(orc, dtype):
 # ------------------------------------------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("beta", [0.2, 0.5, 1.0])
-def test_estimate_uniform_prior(orc, beta):
-    h, peak, depth, z = single_frame_inputs(seed=11)
+@pytest.mark.parametrize("beta,bg_total", [(0.2, 50.0), (0.5, 50.0), (1.0, 50.0), (0.5, 3000.0)])
+def test_estimate_uniform_prior(orc, beta, bg_total):
+    """bg_total 50: about 60 non-empty bins per pixel (zero-skip correlation); 3000: about 950 (dense)."""
+    h, peak, depth, z = single_frame_inputs(seed=11, bg_total=bg_total)
     H, W, T = z.shape
     q = orc.params(T, len(h), peak, beta=beta)
     e = orc.estimate(q, h, z, want_ell=True)
@@ -159,9 +161,10 @@ def _run_filter(orc, q, prm, h, zs, T, present=None, faulty=None, present_now=No
     return ties
 
 
-@pytest.mark.parametrize("sbr,beta", [(0.01, 0.5), (0.1, 0.2), (1.0, 1.0)])
-def test_filter_video(orc, sbr, beta):
-    H, W, N, T = 20, 24, 5, 400
+@pytest.mark.parametrize("sbr,beta,T", [(0.01, 0.5, 400), (0.1, 0.2, 400), (1.0, 1.0, 400), (0.002, 0.5, 600)])
+def test_filter_video(orc, sbr, beta, T):
+    """SBR 0.002 puts about 450 non-empty bins in each pixel (dense correlation); the others use zero skip."""
+    H, W, N = 20, 24, 5
     h, peak, sc, zs = video_inputs(H, W, N, T, sbr, seed=200 + int(sbr * 100))
     q = orc.params(T, len(h), peak, beta=beta, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
     prm = spl.make_params(H, W, T, len(h), peak, beta=beta, sigma_rw2=3.0)
