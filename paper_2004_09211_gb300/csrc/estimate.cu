@@ -3,21 +3,29 @@
 // (Eq. KL_div), and the background/reflectivity estimate (Sec. II-E).
 //
 // Mapping. One warp owns one pixel at a time (persistent grid-stride loop over pixels). The warp streams the
-// pixel's histogram row from HBM once, with 16-byte loads, into its shared-memory slice, and keeps per-chunk
-// photon counts (a chunk is the 8 bins of one 16-byte load, 4 for float counts) as a prefix sum.
+// pixel's histogram row from HBM once with 16-byte loads into its shared-memory slice and keeps a prefix sum
+// of photon counts per 16-byte chunk (8 bins; 4 for float counts).
 //
-// Correlation. C(d) = sum_j g_j z[d - peak + j] with g = h^beta. A pixel with few non-empty bins (the usual
-// case for photon-starved data) is correlated from a compacted list of its non-empty bins (exact zero skip);
-// a dense pixel uses the direct sum over taps. Both give the exact sum of the same products in FP32.
+// Correlation. C(d) = sum_j g_j z[d - peak + j] (g = h^beta) for every candidate, into shared memory. A row
+// with few non-empty bins (photon-starved data) is scattered from a compacted list of those bins (exact zero
+// skip); a denser row uses a register-blocked direct sum (8 candidates per lane, taps in groups of 4).
 //
-// Pruned epilogue. The candidates are processed in blocks of 32 (one per lane). For each block the kernel
-// first bounds its log2 pseudo-posterior from above: lambda*log2(e)*max(g)*(photons in the block's window)
-// plus the largest value the log2 prior can take on the block's depth interval. The block with the largest
-// bound is evaluated exactly; its maximum is a lower bound LB of the global maximum. Every block whose upper
-// bound is below LB - 64 (log2 units) holds only weights below 2^-64 relative to the maximum and is skipped;
-// with at most 8192 candidates at distance at most 8192 bins, the skipped mass changes the moments by less
-// than 8192^3 * 2^-64 < 3e-8 (bins^2). The argmax always lies in an evaluated block. All other blocks are
-// evaluated exactly, so argmax, mean and variance are those of the full grid to FP32 accuracy.
+// Epilogue. ell(d) = lambda C(d) + log f(d) in log2 units. Candidates are grouped in blocks of 32. Each block
+// gets an upper bound of ell (lambda log2(e) max(g) times the photons in the block's window, plus the prior's
+// largest value on the block). The block with the largest bound is evaluated exactly; its best value LB is a
+// lower bound of the maximum, and every block whose bound is below LB - 64 is dropped: its weights are below
+// 2^-64 of the maximum, so the moments move by less than 8192^3 * 2^-64 < 3e-8 bins^2.
+//   * Few surviving blocks (a concentrated posterior): each is evaluated exactly in the log domain.
+//   * Many (a broad posterior): the weights 2^(ell - ref) are formed directly in the linear domain over the
+//     surviving range, each lane walking a contiguous run of candidates. The data factor costs one exp2 per
+//     candidate; each mixture component is advanced by the exact two-multiply recurrence of a Gaussian on a
+//     unit grid (value ratio, then ratio of ratios), restarted from exact exponentials every 16 candidates.
+//     All values are scaled by fixed upper bounds so nothing overflows; a value that underflows is below
+//     2^-126 while the largest weight is required to be at least 2^-60 (checked), so the dropped mass is
+//     below 2^-62 per candidate. When that check or the component-width condition (variance >= 1.5 bins^2,
+//     so 16 steps cannot underflow a component near its own peak) fails, the exact log-domain path runs.
+// Moments are then taken in a second pass centred on the argmax (no cancellation between S2/S0 and the
+// squared offset of the mean).
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -29,8 +37,10 @@ namespace {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLog2TwoPi = 2.6514961294723187f;  // log2(2 pi)
 constexpr int kMaxComp = 10;                        // 9 stencil entries + 1 merged weakly informative one
-constexpr int kNnzSparse = 256;                     // zero-skip correlation up to this many non-empty bins
-constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for skipping a block
+constexpr int kNnzScatter = 160;                    // scatter (zero-skip) correlation up to this many bins
+constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for dropping a block
+constexpr int kFewBlocks = 6;                       // at most this many surviving blocks: exact log path
+constexpr int kRestart = 16;                        // exact restart interval of the mixture recurrences
 
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -70,12 +80,12 @@ __device__ __forceinline__ void warp_argmax(float& v, int& i) {
 // Shared-memory slice of one warp (all offsets in 4-byte words; every array starts 16-byte aligned).
 struct Slice {
     int nch;     // chunks per row
-    int zs;      // dense counts as float, nch * CB words
-    int ent;     // non-empty bins (bin, count) as uint2, kNnzSparse entries
+    int zs;      // dense counts as float, nch * CB words + 16 zero words (read past the row by the dense sum)
+    int ent;     // non-empty bins (bin, count) as uint2, kNnzScatter entries
     int cps;     // photon-count prefix over chunks, nch + 1 words
-    int cpe;     // entry-index prefix over chunks, nch + 1 words
+    int cpe;     // non-empty-bin prefix over chunks, nch + 1 words
     int ubs;     // per-block upper bounds, NB words
-    int cs;      // log2 pseudo-posterior (or C) per candidate, NB * 32 words
+    int cs;      // C, then ell or weights, per candidate: NB * 32 words
     int words;   // total
 };
 
@@ -86,8 +96,8 @@ __host__ __device__ __forceinline__ Slice make_slice(int T, int D, int cb) {
     s.nch = (T + cb - 1) / cb;
     const int nb = (D + 31) / 32;
     s.zs = 0;
-    s.ent = round4(s.nch * cb);
-    s.cps = s.ent + 2 * kNnzSparse;
+    s.ent = round4(s.nch * cb) + 16;
+    s.cps = s.ent + 2 * kNnzScatter;
     s.cpe = s.cps + round4(s.nch + 1);
     s.ubs = s.cpe + round4(s.nch + 1);
     s.cs = s.ubs + round4(nb);
@@ -166,7 +176,10 @@ __device__ __forceinline__ void warp_scan2(float* x, int* y, int n, int lane) {
     __syncwarp();
 }
 
-// Mixture prior in log2 units: component c contributes 2^(ca[c] - ck[c] (d - cm[c])^2).
+// ------------------------------------------------------------------------------------------------------------
+// Prior (Eq. predict) in log2 units: component c contributes 2^(ca[c] - ck[c] (d - cm[c])^2)
+// ------------------------------------------------------------------------------------------------------------
+
 struct Prior {
     float ca[kMaxComp], ck[kMaxComp], cm[kMaxComp], cv[kMaxComp], cw[kMaxComp];
     int n;
@@ -267,51 +280,108 @@ __device__ __forceinline__ float log2_prior_bound(const Prior& pr, float lo, flo
     return pr.n > 1 ? mx + lg2(static_cast<float>(pr.n)) + 1e-3f : mx + 1e-3f;
 }
 
-// C(d) for the candidate c = 32 b + lane of block b (clamped to the last candidate for lanes past D).
-__device__ __forceinline__ float block_cost(const float* __restrict__ gs, const float* zs, const uint2* ent,
-                                            const int* cpe, bool sparse, int b, int lane, int D, int L, int u0,
-                                            int cb) {
-    const int c = min(32 * b + lane, D - 1);
-    const int t0 = u0 + c;  // first bin of this candidate's template
-    if (sparse) {
-        const int s_bin = u0 + 32 * b;
-        const int e_bin = u0 + min(32 * b + 31, D - 1) + L - 1;
-        const int e0 = cpe[s_bin / cb], e1 = cpe[e_bin / cb + 1];
-        float acc = 0.f;
-        for (int e = e0; e < e1; ++e) {
-            const uint2 en = ent[e];
-            const unsigned j = en.x - static_cast<unsigned>(t0);
-            if (j < static_cast<unsigned>(L)) acc = fmaf(__uint_as_float(en.y), gs[j], acc);
-        }
-        return acc;
-    }
-    const float* zz = zs + t0;
-    float acc0 = 0.f, acc1 = 0.f;
-    int j = 0;
-    for (; j + 4 <= L; j += 4) {
-        const float4 g4 = *reinterpret_cast<const float4*>(gs + j);
-        acc0 = fmaf(g4.x, zz[j], acc0);
-        acc1 = fmaf(g4.y, zz[j + 1], acc1);
-        acc0 = fmaf(g4.z, zz[j + 2], acc0);
-        acc1 = fmaf(g4.w, zz[j + 3], acc1);
-    }
-    for (; j < L; ++j) acc0 = fmaf(gs[j], zz[j], acc0);
-    return acc0 + acc1;
+// ------------------------------------------------------------------------------------------------------------
+// Correlation C(d) for every candidate into cs[0 .. 32 NB)
+// ------------------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void zero_words(float* x, int n4, int lane) {
+    for (int i = lane; i < n4; i += 32) reinterpret_cast<float4*>(x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
 }
+
+// Zero skip: every non-empty bin t scatters z_t g_j into C at candidate t - u0 - j (lanes over taps j).
+__device__ __forceinline__ void corr_scatter(const float* __restrict__ gs, const uint2* ent, int nnz, float* cs,
+                                             int NB, int D, int L, int u0, int lane) {
+    zero_words(cs, NB * 8, lane);
+    for (int e = 0; e < nnz; ++e) {
+        const uint2 en = ent[e];
+        const float zc = __uint_as_float(en.y);
+        const int cb = static_cast<int>(en.x) - u0;  // candidate whose tap 0 falls on this bin
+        for (int j = lane; j < L; j += 32) {
+            const int c = cb - j;
+            if (c >= 0 && c < D) cs[c] = fmaf(zc, gs[j], cs[c]);
+        }
+        __syncwarp();
+    }
+}
+
+// Dense rows: a lane computes 8 consecutive candidates per 256-candidate super-block. Super-blocks start at
+// candidate -(u0 & 3) so every lane's window starts on a 16-byte boundary of zs (candidates < 0 are dropped).
+// Windows may read up to 11 words past the last bin of the row: zs carries 16 zero words there.
+__device__ __forceinline__ void corr_dense(const float* __restrict__ gs, const float* zs, float* cs, int D, int L,
+                                           int u0, int lane) {
+    for (int cb = -(u0 & 3); cb < D; cb += 256) {
+        const int cl = cb + 8 * lane;
+        if (cl < D && cl + 7 >= 0) {
+            const float4* z4 = reinterpret_cast<const float4*>(zs + u0 + cl);
+            const float4* g4 = reinterpret_cast<const float4*>(gs);
+            float acc[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+            float4 c0 = z4[0], c1 = z4[1];
+            for (int jg = 0; jg < L; jg += 4) {
+                const float4 nx = z4[jg / 4 + 2];
+                const float4 g = g4[jg / 4];
+                const float w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, nx.x, nx.y, nx.z, nx.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    acc[r] = fmaf(g.x, w[r], acc[r]);
+                    acc[r] = fmaf(g.y, w[r + 1], acc[r]);
+                    acc[r] = fmaf(g.z, w[r + 2], acc[r]);
+                    acc[r] = fmaf(g.w, w[r + 3], acc[r]);
+                }
+                c0 = c1;
+                c1 = nx;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (cl + r >= 0 && cl + r < D) cs[cl + r] = acc[r];
+        }
+    }
+    __syncwarp();
+}
+
+// C(d) for all candidates of one pixel (row already in zs, prefix sums in cps/cpe).
+template <int CB>
+__device__ __forceinline__ void correlate(const float* __restrict__ gs, const float* zs, uint2* ent, const int* cpe,
+                                          float* cs, int nch, bool empty, int nnz, int NB, int D, int L, int u0,
+                                          int lane) {
+    if (empty) {
+        zero_words(cs, NB * 8, lane);
+    } else if (nnz <= kNnzScatter) {
+        for (int i = lane; i < nch; i += 32) {  // compact the non-empty bins, in bin order
+            int o = cpe[i];
+            if (cpe[i + 1] == o) continue;
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                const float v = zs[i * CB + k];
+                if (v != 0.f) ent[o++] = make_uint2(static_cast<unsigned>(i * CB + k), __float_as_uint(v));
+            }
+        }
+        __syncwarp();
+        corr_scatter(gs, ent, nnz, cs, NB, D, L, u0, lane);
+    } else {
+        corr_dense(gs, zs, cs, D, L, u0, lane);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// The kernel
+// ------------------------------------------------------------------------------------------------------------
 
 template <int FMT, bool COST_ONLY>
 __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     extern __shared__ __align__(16) float dyn[];
-    __shared__ __align__(16) float gs[SPL_MAX_TAPS];  // g_j = h_j^beta (0 for taps <= 0)
-    __shared__ float as[SPL_MAX_TAPS];                 // h_j / sum(h): normalised template (intensity model)
+    __shared__ __align__(16) float gs[SPL_MAX_TAPS + 4];  // g_j = h_j^beta (0 for taps <= 0 and for j >= L)
+    __shared__ float as[SPL_MAX_TAPS];                     // h_j / sum(h): normalised template (intensity)
     __shared__ float s_hsum, s_gmax;
     constexpr int CB = FMT == SPL_HIST_F32 ? 4 : 8;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int j = threadIdx.x; j < SPL_MAX_TAPS; j += blockDim.x) {
+    for (int j = threadIdx.x; j < SPL_MAX_TAPS + 4; j += blockDim.x) {
         const float hj = j < a.L ? a.h[j] : 0.f;
         gs[j] = hj > 0.f ? powf(hj, a.beta) : 0.f;
-        as[j] = hj > 0.f ? hj : 0.f;
+        if (j < SPL_MAX_TAPS) as[j] = hj > 0.f ? hj : 0.f;
     }
     __syncthreads();
     if (warp == 0) {
@@ -343,6 +413,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     float* ubs = base + sl.ubs;
     float* cs = base + sl.cs;
     const long long P = static_cast<long long>(a.H) * a.W;
+    if (lane < 4) reinterpret_cast<float4*>(zs + sl.nch * CB)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     for (long long p = static_cast<long long>(blockIdx.x) * nwarps + warp; p < P;
          p += static_cast<long long>(gridDim.x) * nwarps) {
@@ -378,33 +449,20 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             __syncwarp();
             warp_scan2(cps, cpe, sl.nch, lane);
         }
-        const bool sparse = !faulty && nnz <= kNnzSparse;
-        if (sparse) {
-            // compact the non-empty bins, in bin order, at the offsets the scan produced
-            for (int i = lane; i < sl.nch; i += 32) {
-                int o = cpe[i];
-                if (cpe[i + 1] == o) continue;
-#pragma unroll
-                for (int k = 0; k < CB; ++k) {
-                    const float v = zs[i * CB + k];
-                    if (v != 0.f) ent[o++] = make_uint2(static_cast<unsigned>(i * CB + k), __float_as_uint(v));
-                }
-            }
-            __syncwarp();
-        }
+        const bool empty = faulty || nnz == 0;
+
+        // ---- 2. C(d) for every candidate ----
+        correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane);
 
         if (COST_ONLY) {
             float best = -INFINITY;
             int bidx = 0x7fffffff;
-            for (int b = 0; b < NB; ++b) {
-                const float acc = block_cost(gs, zs, ent, cpe, sparse, b, lane, D, L, u0, CB);
-                const int c = 32 * b + lane;
-                if (c < D) {
-                    if (a.cost) __stcs(a.cost + p * D + c, acc);
-                    if (acc > best) {
-                        best = acc;
-                        bidx = c;
-                    }
+            for (int c = lane; c < D; c += 32) {
+                const float acc = cs[c];
+                if (a.cost) __stcs(a.cost + p * D + c, acc);
+                if (acc > best) {
+                    best = acc;
+                    bidx = c;
                 }
             }
             if (a.argmax) {
@@ -415,20 +473,21 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             continue;
         }
 
-        // ---- 2. prior and per-block upper bounds of the log2 pseudo-posterior ----
+        // ---- 3. prior and per-block upper bounds of the log2 pseudo-posterior ----
         Prior pr;
         build_prior(a, p, pr);
         const float lam2 = a.lam2;
-        float ubest = -INFINITY;
+        float ubest = -INFINITY, nmax = 0.f;
         int ub_b = 0x7fffffff;
         for (int b = lane; b < NB; b += 32) {
             const int s_bin = u0 + 32 * b;
             const int last = min(32 * b + 31, D - 1);
             const int e_bin = u0 + last + L - 1;
-            const float nb = faulty ? 0.f : cps[e_bin / CB + 1] - cps[s_bin / CB];
+            const float nb = empty ? 0.f : cps[e_bin / CB + 1] - cps[s_bin / CB];
             const float ub = lam2 * gmax * nb * 1.0001f +
                              log2_prior_bound(pr, static_cast<float>(a.dmin + 32 * b), static_cast<float>(a.dmin + last));
             ubs[b] = ub;
+            nmax = fmaxf(nmax, nb);
             if (ub > ubest) {
                 ubest = ub;
                 ub_b = b;
@@ -436,67 +495,163 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         }
         warp_argmax(ubest, ub_b);
         if (ub_b >= NB) ub_b = 0;  // every bound was NaN (invalid inputs): keep the block index in range
+        nmax = warp_max(nmax);
         __syncwarp();
 
-        // ---- 3. exact log2 pseudo-posterior on every block that can matter, and its argmax ----
+        // exact best value of the block with the largest bound: a lower bound of the maximum
+        float lb;
+        {
+            const int c = 32 * ub_b + lane;
+            float l = -INFINITY;
+            if (c < D) l = fmaf(lam2, cs[c], log2_prior(pr, static_cast<float>(a.dmin + c)));
+            lb = warp_max(l);
+        }
+        const float thr = lb - kPrune2;
+        int nsurv = 0, bfirst = NB, blast = -1;
+        for (int w0 = 0; w0 < NB; w0 += 32) {
+            const unsigned m =
+                __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
+            if (m) {
+                nsurv += __popc(m);
+                bfirst = min(bfirst, w0 + __ffs(m) - 1);
+                blast = w0 + 31 - __clz(m);
+            }
+        }
+
         float best = -INFINITY;
         int bidx = 0x7fffffff;
-        auto eval_block = [&](int b) {
-            const float acc = faulty ? 0.f : block_cost(gs, zs, ent, cpe, sparse, b, lane, D, L, u0, CB);
-            const int c = 32 * b + lane;
-            float l = fmaf(lam2, acc, log2_prior(pr, static_cast<float>(a.dmin + c)));
-            if (c >= D) l = -INFINITY;
-            cs[c] = l;
-            if (l > best || (l == best && c < bidx)) {
-                best = l;
-                bidx = c;
-            }
-        };
-        eval_block(ub_b);
-        const float thr = warp_max(best) - kPrune2;
-        for (int w0 = 0; w0 < NB; w0 += 32) {
-            unsigned m = __ballot_sync(0xffffffffu, w0 + lane < NB && ubs[w0 + lane] >= thr);
-            if (w0 <= ub_b && ub_b < w0 + 32) m &= ~(1u << (ub_b - w0));
-            while (m) {
-                const int b = w0 + __ffs(m) - 1;
-                m &= m - 1;
-                eval_block(b);
-            }
-        }
-        warp_argmax(best, bidx);
-        if (bidx == 0x7fffffff) bidx = 0;  // every ell was NaN (invalid inputs): keep indices in range
-        __syncwarp();
+        float mu_out = 0.f;
+        bool done = false;
 
-        // ---- 4. moments of the normalised weights 2^(ell - max), centred on the argmax ----
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int w0 = 0; w0 < NB; w0 += 32) {
-            unsigned m = __ballot_sync(0xffffffffu, w0 + lane < NB && ubs[w0 + lane] >= thr);
-            if (w0 <= ub_b && ub_b < w0 + 32) m |= 1u << (ub_b - w0);
-            while (m) {
-                const int b = w0 + __ffs(m) - 1;
-                m &= m - 1;
-                const int c = 32 * b + lane;
-                const float w = ex2(cs[c] - best);  // 0 for lanes past D (ell = -inf)
-                const float dd = static_cast<float>(c - bidx);
-                s0 += w;
-                s1 = fmaf(w, dd, s1);
-                s2 = fmaf(w * dd, dd, s2);
+        // ---- 4a. broad posterior: linear-domain weights over the surviving range ----
+        if (nsurv > kFewBlocks) {
+            float minv = INFINITY, sref = 0.f;
+            if (pr.n > 0) sref = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < kMaxComp; ++i)
+                if (i < pr.n) {
+                    minv = fminf(minv, pr.cv[i]);
+                    sref = fmaxf(sref, pr.ca[i]);
+                }
+            if (!(minv < 1.5f)) {
+                const float xref = lam2 * gmax * nmax * 1.0001f;  // >= lambda log2(e) C(d) for every d
+                const int c_lo = 32 * bfirst, c_hi = min(32 * blast + 31, D - 1);
+                const int run = (c_hi - c_lo + 32) >> 5;
+                const int r0 = c_lo + lane * run, r1 = min(r0 + run, c_hi + 1);
+                float v[kMaxComp], q[kMaxComp], kk[kMaxComp];
+#pragma unroll
+                for (int i = 0; i < kMaxComp; ++i) {
+                    v[i] = q[i] = 0.f;
+                    kk[i] = i < pr.n ? ex2(-2.f * pr.ck[i]) : 0.f;
+                }
+                for (int c = r0; c < r1; ++c) {
+                    const float d = static_cast<float>(a.dmin + c);
+                    if (((c - r0) & (kRestart - 1)) == 0) {  // exact restart of every component
+#pragma unroll
+                        for (int i = 0; i < kMaxComp; ++i)
+                            if (i < pr.n) {
+                                const float e = d - pr.cm[i];
+                                v[i] = ex2(pr.ca[i] - pr.ck[i] * e * e - sref);
+                                q[i] = ex2(fminf(-pr.ck[i] * (2.f * e + 1.f), 100.f));
+                            }
+                    }
+                    float m = pr.n == 0 ? 1.f : 0.f;
+#pragma unroll
+                    for (int i = 0; i < kMaxComp; ++i)
+                        if (i < pr.n) {
+                            m += v[i];
+                            v[i] *= q[i];
+                            q[i] *= kk[i];
+                        }
+                    const float w = ex2(fmaf(lam2, cs[c], -xref)) * m;
+                    cs[c] = w;
+                    if (w > best) {
+                        best = w;
+                        bidx = c;
+                    }
+                }
+                warp_argmax(best, bidx);
+                __syncwarp();
+                if (best >= 0x1p-60f) {
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+                    for (int c = r0; c < r1; ++c) {
+                        const float w = cs[c];
+                        const float dd = static_cast<float>(c - bidx);
+                        s0 += w;
+                        s1 = fmaf(w, dd, s1);
+                        s2 = fmaf(w * dd, dd, s2);
+                    }
+                    s0 = warp_sum(s0);
+                    s1 = warp_sum(s1);
+                    s2 = warp_sum(s2);
+                    const float m1 = s1 / s0;
+                    mu_out = static_cast<float>(a.dmin + bidx) + m1;
+                    if (lane == 0) {
+                        a.mu[p] = mu_out;
+                        a.var[p] = fmaxf(s2 / s0 - m1 * m1, 0.f);
+                        if (a.argmax) a.argmax[p] = a.dmin + bidx;
+                    }
+                    done = true;
+                } else {
+                    // the weights overwrote C on the surviving range: recompute it for the exact path
+                    correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane);
+                }
             }
         }
-        s0 = warp_sum(s0);
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
-        const float m1 = s1 / s0;
-        const float mu = static_cast<float>(a.dmin + bidx) + m1;
-        const float var = fmaxf(s2 / s0 - m1 * m1, 0.f);
-        if (lane == 0) {
-            a.mu[p] = mu;
-            a.var[p] = var;
-            if (a.argmax) a.argmax[p] = a.dmin + bidx;
+
+        // ---- 4b. concentrated posterior (or fallback): exact log-domain ell on the surviving blocks ----
+        if (!done) {
+            best = -INFINITY;
+            bidx = 0x7fffffff;
+            for (int w0 = 0; w0 < NB; w0 += 32) {
+                unsigned m =
+                    __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
+                while (m) {
+                    const int b = w0 + __ffs(m) - 1;
+                    m &= m - 1;
+                    const int c = 32 * b + lane;
+                    float l = -INFINITY;
+                    if (c < D) l = fmaf(lam2, cs[c], log2_prior(pr, static_cast<float>(a.dmin + c)));
+                    cs[c] = l;
+                    if (l > best || (l == best && c < bidx)) {
+                        best = l;
+                        bidx = c;
+                    }
+                }
+            }
+            warp_argmax(best, bidx);
+            if (bidx == 0x7fffffff) bidx = 0;  // every ell was NaN (invalid inputs): keep indices in range
+            __syncwarp();
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int w0 = 0; w0 < NB; w0 += 32) {
+                unsigned m =
+                    __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
+                while (m) {
+                    const int b = w0 + __ffs(m) - 1;
+                    m &= m - 1;
+                    const int c = 32 * b + lane;
+                    const float w = ex2(cs[c] - best);  // 0 for lanes past D (ell = -inf)
+                    const float dd = static_cast<float>(c - bidx);
+                    s0 += w;
+                    s1 = fmaf(w, dd, s1);
+                    s2 = fmaf(w * dd, dd, s2);
+                }
+            }
+            s0 = warp_sum(s0);
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            const float m1 = s1 / s0;
+            mu_out = static_cast<float>(a.dmin + bidx) + m1;
+            if (lane == 0) {
+                a.mu[p] = mu_out;
+                a.var[p] = fmaxf(s2 / s0 - m1 * m1, 0.f);
+                if (a.argmax) a.argmax[p] = a.dmin + bidx;
+            }
         }
 
         // ---- 5. background b and reflectivity r (Sec. II-E) ----
         if (a.refl) {
+            const float mu = mu_out;
             float r = 0.f, b = 0.f;
             const bool present = a.present_now ? a.present_now[p] != 0 : true;
             if (faulty) {
@@ -562,9 +717,9 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                         if (g > 0.f) lo = f; else hi = f;
                         float fn = f + g / gp;  // Newton step on psi (psi' = -gp)
                         if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
-                        const bool done = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
+                        const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
                         f = fn;
-                        if (done) break;
+                        if (conv) break;
                     }
                 }
                 r = f * K / hsum;

@@ -295,3 +295,38 @@ def test_full_size_video_frames_sampled(orc):
             m, v = e["mu"], e["var"]
         check_close(_np(mu.reshape(H, W)[y, x]), m[y - y0, x - x0], f"mu[{y},{x}]")
         check_close(_np(var.reshape(H, W)[y, x]), v[y - y0, x - x0], f"var[{y},{x}]", atol=1e-6)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Epilogue paths: linear-domain weights, their fallback, narrow components
+# ------------------------------------------------------------------------------------------------------------
+
+
+def test_broad_posterior_fallback_when_weights_underflow(orc):
+    """1000 photons in each of 79 consecutive bins: the photon-count bound of the data term exceeds the best
+    value by far more than the float range, so the linear-domain weights underflow and the exact log-domain
+    path must take over; results still match the oracle."""
+    h, peak = synth.asymmetric_irf(L=48)
+    H, W, T = 2, 3, 600
+    z = np.zeros((H, W, T))
+    for i, s in enumerate((100, 250, 400, 130, 333, 480)):
+        z[i // W, i % W, s:s + 79] = 1000.0
+    q = orc.params(T, len(h), peak, beta=0.1)
+    e = orc.estimate(q, h, z, want_ell=True)
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.1)
+    o = spl.spl_depth_estimate(prm, _gpu_hist(z, T), torch.from_numpy(h).to(DEV))
+    torch.cuda.synchronize()
+    check_argmax(_np(o["argmax"]), e["argmax"], e["ell"], q.dmin)
+    check_close(_np(o["mu"]), e["mu"], "mu")
+    check_close(_np(o["var"]), e["var"], "var", atol=1e-6)
+
+
+@pytest.mark.parametrize("sigma_rw2", [0.3, 50.0])
+def test_filter_component_widths(orc, sigma_rw2):
+    """sigma_RW^2 = 0.3 makes mixture components narrower than the recurrence allows (exact log path);
+    50 keeps every posterior broad (linear-domain path on most pixels)."""
+    H, W, N, T = 12, 14, 4, 350
+    h, peak, sc, zs = video_inputs(H, W, N, T, 0.3, seed=41)
+    q = orc.params(T, len(h), peak, beta=0.5, sigma_rw2=sigma_rw2, nu=synth.cross_weights(0.5))
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.5, sigma_rw2=sigma_rw2)
+    _run_filter(orc, q, prm, h, zs, T)
