@@ -37,7 +37,8 @@ namespace {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLog2TwoPi = 2.6514961294723187f;  // log2(2 pi)
 constexpr int kMaxComp = 10;                        // 9 stencil entries + 1 merged weakly informative one
-constexpr int kNnzScatter = 160;                    // scatter (zero-skip) correlation up to this many bins
+constexpr int kNnzScatter = 24;                     // zero skip by scatter up to this many non-empty bins
+constexpr int kNnzSparse = 320;                     // zero skip by gather up to this many (list capacity)
 constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for dropping a block
 constexpr int kFewBlocks = 6;                       // at most this many surviving blocks: exact log path
 constexpr int kRestart = 16;                        // exact restart interval of the mixture recurrences
@@ -79,9 +80,10 @@ __device__ __forceinline__ void warp_argmax(float& v, int& i) {
 
 // Shared-memory slice of one warp (all offsets in 4-byte words; every array starts 16-byte aligned).
 struct Slice {
-    int nch;     // chunks per row
+    int nch;     // 16-byte chunks per row
+    int raw;     // the next pixel's row as loaded (cp.async target), nch * 4 words
     int zs;      // dense counts as float, nch * CB words + 16 zero words (read past the row by the dense sum)
-    int ent;     // non-empty bins (bin, count) as uint2, kNnzScatter entries
+    int ent;     // non-empty bins (bin, count) as uint2, kNnzSparse entries
     int cps;     // photon-count prefix over chunks, nch + 1 words
     int cpe;     // non-empty-bin prefix over chunks, nch + 1 words
     int ubs;     // per-block upper bounds, NB words
@@ -95,9 +97,10 @@ __host__ __device__ __forceinline__ Slice make_slice(int T, int D, int cb) {
     Slice s;
     s.nch = (T + cb - 1) / cb;
     const int nb = (D + 31) / 32;
-    s.zs = 0;
-    s.ent = round4(s.nch * cb) + 16;
-    s.cps = s.ent + 2 * kNnzScatter;
+    s.raw = 0;
+    s.zs = s.nch * 4;
+    s.ent = s.zs + round4(s.nch * cb) + 16;
+    s.cps = s.ent + 2 * kNnzSparse;
     s.cpe = s.cps + round4(s.nch + 1);
     s.ubs = s.cpe + round4(s.nch + 1);
     s.cs = s.ubs + round4(nb);
@@ -105,20 +108,39 @@ __host__ __device__ __forceinline__ Slice make_slice(int T, int D, int cb) {
     return s;
 }
 
-// Loads chunk i (16 bytes) of pixel p's row and converts it to floats; bins >= T read as 0.
+// ------------------------------------------------------------------------------------------------------------
+// Input staging: the histogram row and the neighbour states of the NEXT pixel are requested while the current
+// pixel is processed, so HBM and L2 latency overlap compute.
+// ------------------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Requests pixel p's row (nch 16-byte chunks) into raw.
+__device__ __forceinline__ void request_row(const EstimateArgs& a, long long p, float* raw, int nch, int esz,
+                                            int lane) {
+    const char* row = static_cast<const char*>(a.z) + p * a.pitch * esz;
+    for (int i = lane; i < nch; i += 32) cp_async16(raw + 4 * i, row + 16 * i);
+}
+
+// Converts 16-byte chunk i of the staged row to floats; bins >= T read as 0.
 template <int FMT>
-__device__ __forceinline__ void load_chunk(const EstimateArgs& a, long long p, int i, float* f) {
+__device__ __forceinline__ void convert_chunk(const float* raw, int i, int T, float* f) {
     if (FMT == SPL_HIST_F32) {
-        const float4 v = __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(a.z) + p * a.pitch) + i);
+        const float4 v = reinterpret_cast<const float4*>(raw)[i];
         f[0] = v.x;
         f[1] = v.y;
         f[2] = v.z;
         f[3] = v.w;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (i * 4 + k >= a.T) f[k] = 0.f;
+            if (i * 4 + k >= T) f[k] = 0.f;
     } else {
-        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(a.z) + p * a.pitch) + i);
+        const uint4 v = reinterpret_cast<const uint4*>(raw)[i];
         const unsigned w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -133,8 +155,44 @@ __device__ __forceinline__ void load_chunk(const EstimateArgs& a, long long p, i
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-            if (i * 8 + k >= a.T) f[k] = 0.f;
+            if (i * 8 + k >= T) f[k] = 0.f;
     }
+}
+
+// One pixel's prior inputs, one stencil entry per lane (lanes 0-8; lane 0 for a per-pixel Gaussian prior).
+struct Nbr {
+    float m, v;
+    int info;    // entry is inside the frame, present and not faulty
+    int faulty;  // lane 0: the pixel itself is faulty
+};
+
+__device__ __forceinline__ Nbr request_nbr(const EstimateArgs& a, long long p, long long P, int lane) {
+    Nbr r;
+    r.m = r.v = 0.f;
+    r.info = r.faulty = 0;
+    if (p >= P) return r;
+    if (a.prior_mode == PRIOR_GAUSS) {
+        if (lane == 0) {
+            r.m = a.pmu[p];
+            r.v = a.pvar[p];
+            r.info = 1;
+        }
+    } else if (a.prior_mode == PRIOR_STENCIL && lane < 9) {
+        const int y = static_cast<int>(p / a.W), x = static_cast<int>(p - static_cast<long long>(y) * a.W);
+        const int yy = y + lane / 3 - 1, xx = x + lane % 3 - 1;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+            const long long i = static_cast<long long>(yy) * a.W + xx;
+            // independent loads (no load waits on another), selected when consumed
+            const float m = a.pmu[i], v = a.pvar[i];
+            const int pres = a.present_in ? a.present_in[i] : 1;
+            const int fl = a.faulty ? a.faulty[i] : 0;
+            r.m = m;
+            r.v = v;
+            r.info = (pres != 0) && (fl == 0);
+        }
+    }
+    if (a.faulty && lane == 0) r.faulty = a.faulty[p] != 0;
+    return r;
 }
 
 // In-place exclusive prefix sum of n values (float array x and int array y) of a warp's slice, with the
@@ -181,65 +239,59 @@ __device__ __forceinline__ void warp_scan2(float* x, int* y, int n, int lane) {
 // ------------------------------------------------------------------------------------------------------------
 
 struct Prior {
-    float ca[kMaxComp], ck[kMaxComp], cm[kMaxComp], cv[kMaxComp], cw[kMaxComp];
+    float ca[kMaxComp], ck[kMaxComp], cm[kMaxComp];
+    float minv;  // smallest component variance
     int n;
 };
 
-// Adds weight w to the component N(m, v), merging it with an identical one already present.
-__device__ __forceinline__ void prior_add(Prior& pr, float w, float m, float v) {
-    bool merged = false;
-#pragma unroll
-    for (int i = 0; i < kMaxComp; ++i)
-        if (i < pr.n && !merged && pr.cm[i] == m && pr.cv[i] == v) {
-            pr.cw[i] += w;
-            merged = true;
-        }
-    if (merged) return;
-#pragma unroll
-    for (int i = 0; i < kMaxComp; ++i)
-        if (i == pr.n) {
-            pr.cm[i] = m;
-            pr.cv[i] = v;
-            pr.cw[i] = w;
-        }
-    ++pr.n;
-}
-
-__device__ __forceinline__ void prior_finish(Prior& pr) {
-#pragma unroll
-    for (int i = 0; i < kMaxComp; ++i)
-        if (i < pr.n) {
-            pr.ca[i] = lg2(pr.cw[i]) - 0.5f * (kLog2TwoPi + lg2(pr.cv[i]));
-            pr.ck[i] = kLog2e / (2.f * pr.cv[i]);
-        }
-}
-
-__device__ __forceinline__ void build_prior(const EstimateArgs& a, long long p, Prior& pr) {
-    pr.n = 0;
+// Lane-parallel construction: lane k (< 9) owns stencil entry k. Entries with identical Gaussians (every
+// weakly informative one, and equal neighbour states) are merged by matching their (mean, variance) bits and
+// summing their weights; the distinct components are then broadcast to every lane in lane order.
+__device__ __forceinline__ void build_prior(const EstimateArgs& a, const Nbr& nb, int lane, Prior& pr) {
+    float w = 0.f, m = 0.f, v = 1.f;
     if (a.prior_mode == PRIOR_GAUSS) {
-        prior_add(pr, 1.f, a.pmu[p], a.pvar[p]);
-    } else if (a.prior_mode == PRIOR_STENCIL) {
-        const int y = static_cast<int>(p / a.W), x = static_cast<int>(p - static_cast<long long>(y) * a.W);
-        float flat_w = 0.f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float w = a.nu[k];
-            if (!(w > 0.f)) continue;
-            const int yy = y + k / 3 - 1, xx = x + k % 3 - 1;
-            bool informative = false;
-            long long i = 0;
-            if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
-                i = static_cast<long long>(yy) * a.W + xx;
-                informative = (a.present_in ? a.present_in[i] != 0 : true) && !(a.faulty && a.faulty[i]);
-            }
-            if (informative)
-                prior_add(pr, w, a.pmu[i], a.pvar[i] + a.sigma_rw2);
-            else
-                flat_w += w;  // every weakly informative entry is the same Gaussian
+        if (lane == 0) {
+            w = 1.f;
+            m = nb.m;
+            v = nb.v;
         }
-        if (flat_w > 0.f) prior_add(pr, flat_w, a.flat_m, a.flat_v + a.sigma_rw2);
+    } else if (a.prior_mode == PRIOR_STENCIL && lane < 9) {
+        w = a.nu[lane];
+        if (nb.info) {
+            m = nb.m;
+            v = nb.v + a.sigma_rw2;
+        } else {
+            m = a.flat_m;
+            v = a.flat_v + a.sigma_rw2;
+        }
     }
-    prior_finish(pr);
+    const bool act = w > 0.f;
+    const unsigned long long key =
+        act ? (static_cast<unsigned long long>(__float_as_uint(m)) << 32) | __float_as_uint(v)
+            : 0xFFFFFFFF00000000ull | static_cast<unsigned>(lane);
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    float wsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float wk = __shfl_sync(0xffffffffu, w, k);
+        if ((peers >> k) & 1u) wsum += wk;
+    }
+    const bool leader = act && lane == __ffs(peers) - 1;
+    unsigned lead = __ballot_sync(0xffffffffu, leader);
+    pr.n = __popc(lead);
+    const float ca_l = lg2(wsum) - 0.5f * (kLog2TwoPi + lg2(v));
+    const float ck_l = kLog2e / (2.f * v);
+    pr.minv = INFINITY;
+#pragma unroll
+    for (int i = 0; i < kMaxComp; ++i) {
+        const int src = lead ? __ffs(lead) - 1 : 0;
+        lead &= lead - 1;
+        pr.ca[i] = __shfl_sync(0xffffffffu, ca_l, src);
+        pr.ck[i] = __shfl_sync(0xffffffffu, ck_l, src);
+        pr.cm[i] = __shfl_sync(0xffffffffu, m, src);
+        const float vi = __shfl_sync(0xffffffffu, v, src);
+        if (i < pr.n) pr.minv = fminf(pr.minv, vi);
+    }
 }
 
 // log2 of the prior density at depth d (up to the constant shared by all d).
@@ -281,7 +333,7 @@ __device__ __forceinline__ float log2_prior_bound(const Prior& pr, float lo, flo
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Correlation C(d) for every candidate into cs[0 .. 32 NB)
+// Correlation C(d) for every candidate into cs[0 .. 32 NB); each routine returns max_d C(d) (warp-uniform)
 // ------------------------------------------------------------------------------------------------------------
 
 __device__ __forceinline__ void zero_words(float* x, int n4, int lane) {
@@ -289,9 +341,9 @@ __device__ __forceinline__ void zero_words(float* x, int n4, int lane) {
     __syncwarp();
 }
 
-// Zero skip: every non-empty bin t scatters z_t g_j into C at candidate t - u0 - j (lanes over taps j).
-__device__ __forceinline__ void corr_scatter(const float* __restrict__ gs, const uint2* ent, int nnz, float* cs,
-                                             int NB, int D, int L, int u0, int lane) {
+// Very sparse rows: every non-empty bin t scatters z_t g_j into C at candidate t - u0 - j (lanes over taps).
+__device__ __forceinline__ float corr_scatter(const float* __restrict__ gs, const uint2* ent, int nnz, float* cs,
+                                              int NB, int D, int L, int u0, int lane) {
     zero_words(cs, NB * 8, lane);
     for (int e = 0; e < nnz; ++e) {
         const uint2 en = ent[e];
@@ -303,13 +355,40 @@ __device__ __forceinline__ void corr_scatter(const float* __restrict__ gs, const
         }
         __syncwarp();
     }
+    float mx = 0.f;
+    for (int c = lane; c < D; c += 32) mx = fmaxf(mx, cs[c]);
+    return warp_max(mx);
+}
+
+// Sparse rows: each candidate (one per lane, 32 per block) gathers the non-empty bins of its block's window
+// from the compacted list; the list's chunk prefix gives the window's first and last entries.
+__device__ __forceinline__ float corr_gather(const float* __restrict__ gs, const uint2* ent, const int* cpe,
+                                             float* cs, int NB, int D, int L, int u0, int cb, int lane) {
+    float mx = 0.f;
+    for (int b = 0; b < NB; ++b) {
+        const int c = 32 * b + lane;
+        const int t0 = u0 + min(c, D - 1);
+        const int e0 = cpe[(u0 + 32 * b) / cb];
+        const int e1 = cpe[(u0 + min(32 * b + 31, D - 1) + L - 1) / cb + 1];
+        float acc = 0.f;
+        for (int e = e0; e < e1; ++e) {
+            const uint2 en = ent[e];
+            const unsigned j = en.x - static_cast<unsigned>(t0);
+            if (j < static_cast<unsigned>(L)) acc = fmaf(__uint_as_float(en.y), gs[j], acc);
+        }
+        cs[c] = acc;
+        if (c < D) mx = fmaxf(mx, acc);
+    }
+    __syncwarp();
+    return warp_max(mx);
 }
 
 // Dense rows: a lane computes 8 consecutive candidates per 256-candidate super-block. Super-blocks start at
 // candidate -(u0 & 3) so every lane's window starts on a 16-byte boundary of zs (candidates < 0 are dropped).
 // Windows may read up to 11 words past the last bin of the row: zs carries 16 zero words there.
-__device__ __forceinline__ void corr_dense(const float* __restrict__ gs, const float* zs, float* cs, int D, int L,
-                                           int u0, int lane) {
+__device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const float* zs, float* cs, int D, int L,
+                                            int u0, int lane) {
+    float mx = 0.f;
     for (int cb = -(u0 & 3); cb < D; cb += 256) {
         const int cl = cb + 8 * lane;
         if (cl < D && cl + 7 >= 0) {
@@ -335,20 +414,26 @@ __device__ __forceinline__ void corr_dense(const float* __restrict__ gs, const f
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r)
-                if (cl + r >= 0 && cl + r < D) cs[cl + r] = acc[r];
+                if (cl + r >= 0 && cl + r < D) {
+                    cs[cl + r] = acc[r];
+                    mx = fmaxf(mx, acc[r]);
+                }
         }
     }
     __syncwarp();
+    return warp_max(mx);
 }
 
-// C(d) for all candidates of one pixel (row already in zs, prefix sums in cps/cpe).
+// C(d) for all candidates of one pixel (row in zs, prefix sums in cps/cpe). Returns max C.
 template <int CB>
-__device__ __forceinline__ void correlate(const float* __restrict__ gs, const float* zs, uint2* ent, const int* cpe,
-                                          float* cs, int nch, bool empty, int nnz, int NB, int D, int L, int u0,
-                                          int lane) {
+__device__ __forceinline__ float correlate(const float* __restrict__ gs, const float* zs, uint2* ent,
+                                           const int* cpe, float* cs, int nch, bool empty, int nnz, int NB, int D,
+                                           int L, int u0, int lane) {
     if (empty) {
         zero_words(cs, NB * 8, lane);
-    } else if (nnz <= kNnzScatter) {
+        return 0.f;
+    }
+    if (nnz <= kNnzSparse) {
         for (int i = lane; i < nch; i += 32) {  // compact the non-empty bins, in bin order
             int o = cpe[i];
             if (cpe[i + 1] == o) continue;
@@ -359,10 +444,10 @@ __device__ __forceinline__ void correlate(const float* __restrict__ gs, const fl
             }
         }
         __syncwarp();
-        corr_scatter(gs, ent, nnz, cs, NB, D, L, u0, lane);
-    } else {
-        corr_dense(gs, zs, cs, D, L, u0, lane);
+        if (nnz <= kNnzScatter) return corr_scatter(gs, ent, nnz, cs, NB, D, L, u0, lane);
+        return corr_gather(gs, ent, cpe, cs, NB, D, L, u0, CB, lane);
     }
+    return corr_dense(gs, zs, cs, D, L, u0, lane);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -406,6 +491,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     const int T = a.T, L = a.L, D = a.D, u0 = a.dmin - a.peak, NB = (D + 31) >> 5;
     const Slice sl = make_slice(T, D, CB);
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
+    float* raw = base + sl.raw;
     float* zs = base + sl.zs;
     uint2* ent = reinterpret_cast<uint2*>(base + sl.ent);
     float* cps = base + sl.cps;
@@ -413,19 +499,28 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     float* ubs = base + sl.ubs;
     float* cs = base + sl.cs;
     const long long P = static_cast<long long>(a.H) * a.W;
+    const long long stride = static_cast<long long>(gridDim.x) * nwarps;
+    constexpr int ESZ = FMT == SPL_HIST_F32 ? 4 : 2;
     if (lane < 4) reinterpret_cast<float4*>(zs + sl.nch * CB)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    for (long long p = static_cast<long long>(blockIdx.x) * nwarps + warp; p < P;
-         p += static_cast<long long>(gridDim.x) * nwarps) {
-        const bool faulty = !COST_ONLY && a.faulty && a.faulty[p];
+    long long p = static_cast<long long>(blockIdx.x) * nwarps + warp;
+    if (p < P) request_row(a, p, raw, sl.nch, ESZ, lane);
+    cp_async_commit();
+    Nbr nb_next = request_nbr(a, p, P, lane);
 
-        // ---- 1. histogram row -> shared memory, per-chunk photon and non-empty-bin counts ----
+    for (; p < P; p += stride) {
+        const Nbr nb = nb_next;
+        const bool faulty = !COST_ONLY && __shfl_sync(0xffffffffu, nb.faulty, 0) != 0;
+        cp_async_wait_all();
+        __syncwarp();
+
+        // ---- 1. staged row -> floats in shared memory, per-chunk photon and non-empty-bin counts ----
         float K = 0.f;
         int nnz = 0;
         if (!faulty) {
             for (int i = lane; i < sl.nch; i += 32) {
                 float f[CB];
-                load_chunk<FMT>(a, p, i, f);
+                convert_chunk<FMT>(raw, i, T, f);
                 float s = 0.f;
                 int c = 0;
 #pragma unroll
@@ -446,13 +541,19 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             }
             K = warp_sum(K);
             nnz = static_cast<int>(warp_sum(static_cast<float>(nnz)));
-            __syncwarp();
-            warp_scan2(cps, cpe, sl.nch, lane);
         }
+        __syncwarp();  // the staged row is consumed: stage the next pixel's inputs behind this pixel's work
+        {
+            const long long pn = p + stride;
+            if (pn < P) request_row(a, pn, raw, sl.nch, ESZ, lane);
+            cp_async_commit();
+            nb_next = request_nbr(a, pn, P, lane);
+        }
+        if (!faulty) warp_scan2(cps, cpe, sl.nch, lane);
         const bool empty = faulty || nnz == 0;
 
         // ---- 2. C(d) for every candidate ----
-        correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane);
+        const float cmax = correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane);
 
         if (COST_ONLY) {
             float best = -INFINITY;
@@ -475,9 +576,9 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
 
         // ---- 3. prior and per-block upper bounds of the log2 pseudo-posterior ----
         Prior pr;
-        build_prior(a, p, pr);
+        build_prior(a, nb, lane, pr);
         const float lam2 = a.lam2;
-        float ubest = -INFINITY, nmax = 0.f;
+        float ubest = -INFINITY;
         int ub_b = 0x7fffffff;
         for (int b = lane; b < NB; b += 32) {
             const int s_bin = u0 + 32 * b;
@@ -487,7 +588,6 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             const float ub = lam2 * gmax * nb * 1.0001f +
                              log2_prior_bound(pr, static_cast<float>(a.dmin + 32 * b), static_cast<float>(a.dmin + last));
             ubs[b] = ub;
-            nmax = fmaxf(nmax, nb);
             if (ub > ubest) {
                 ubest = ub;
                 ub_b = b;
@@ -495,7 +595,6 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         }
         warp_argmax(ubest, ub_b);
         if (ub_b >= NB) ub_b = 0;  // every bound was NaN (invalid inputs): keep the block index in range
-        nmax = warp_max(nmax);
         __syncwarp();
 
         // exact best value of the block with the largest bound: a lower bound of the maximum
@@ -523,18 +622,14 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         float mu_out = 0.f;
         bool done = false;
 
-        // ---- 4a. broad posterior: linear-domain weights over the surviving range ----
-        if (nsurv > kFewBlocks) {
-            float minv = INFINITY, sref = 0.f;
-            if (pr.n > 0) sref = -INFINITY;
+        // ---- 4a. linear-domain weights over the surviving range (when its exactness conditions hold) ----
+        if ((blast - bfirst + 1) <= max(8, 2 * nsurv) && !(pr.minv < 1.5f)) {
+            {
+                float sref = pr.n > 0 ? -INFINITY : 0.f;
 #pragma unroll
-            for (int i = 0; i < kMaxComp; ++i)
-                if (i < pr.n) {
-                    minv = fminf(minv, pr.cv[i]);
-                    sref = fmaxf(sref, pr.ca[i]);
-                }
-            if (!(minv < 1.5f)) {
-                const float xref = lam2 * gmax * nmax * 1.0001f;  // >= lambda log2(e) C(d) for every d
+                for (int i = 0; i < kMaxComp; ++i)
+                    if (i < pr.n) sref = fmaxf(sref, pr.ca[i]);
+                const float xref = lam2 * cmax;  // lambda log2(e) max_d C(d)
                 const int c_lo = 32 * bfirst, c_hi = min(32 * blast + 31, D - 1);
                 const int run = (c_hi - c_lo + 32) >> 5;
                 const int r0 = c_lo + lane * run, r1 = min(r0 + run, c_hi + 1);
@@ -732,6 +827,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         }
         __syncwarp();
     }
+    cp_async_wait_all();  // no copy may still target this CTA's shared memory when it exits
 }
 
 // Bytes of dynamic shared memory one warp needs.
