@@ -8,7 +8,8 @@
 //
 // Correlation. C(d) = sum_j g_j z[d - peak + j] (g = h^beta) for every candidate, into shared memory. A row
 // with few non-empty bins (photon-starved data) is scattered from a compacted list of those bins (exact zero
-// skip); a denser row uses a register-blocked direct sum (8 candidates per lane, taps in groups of 4).
+// skip: each lane accumulates a contiguous run of candidates from the bins that reach it); a denser row uses
+// a register-blocked direct sum (8 candidates per lane, taps in groups of 4).
 //
 // Epilogue. ell(d) = lambda C(d) + log f(d) in log2 units. Candidates are grouped in blocks of 32. Each block
 // gets an upper bound of ell (lambda log2(e) max(g) times the photons in the block's window, plus the prior's
@@ -37,8 +38,7 @@ namespace {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLog2TwoPi = 2.6514961294723187f;  // log2(2 pi)
 constexpr int kMaxComp = 10;                        // 9 stencil entries + 1 merged weakly informative one
-constexpr int kNnzScatter = 24;                     // zero skip by scatter up to this many non-empty bins
-constexpr int kNnzSparse = 320;                     // zero skip by gather up to this many (list capacity)
+constexpr int kNnzSparse = 320;                     // zero-skip correlation up to this many non-empty bins
 constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for dropping a block
 constexpr int kFewBlocks = 6;                       // at most this many surviving blocks: exact log path
 constexpr int kRestart = 16;                        // exact restart interval of the mixture recurrences
@@ -341,43 +341,30 @@ __device__ __forceinline__ void zero_words(float* x, int n4, int lane) {
     __syncwarp();
 }
 
-// Very sparse rows: every non-empty bin t scatters z_t g_j into C at candidate t - u0 - j (lanes over taps).
-__device__ __forceinline__ float corr_scatter(const float* __restrict__ gs, const uint2* ent, int nnz, float* cs,
-                                              int NB, int D, int L, int u0, int lane) {
-    zero_words(cs, NB * 8, lane);
-    for (int e = 0; e < nnz; ++e) {
-        const uint2 en = ent[e];
-        const float zc = __uint_as_float(en.y);
-        const int cb = static_cast<int>(en.x) - u0;  // candidate whose tap 0 falls on this bin
-        for (int j = lane; j < L; j += 32) {
-            const int c = cb - j;
-            if (c >= 0 && c < D) cs[c] = fmaf(zc, gs[j], cs[c]);
-        }
-        __syncwarp();
-    }
+// Sparse rows: lane l owns the contiguous run [r0, r1) of candidates and adds z_t g_{t-u0-c} into each
+// candidate c of its run for every non-empty bin t whose taps reach the run (the bins come from the compacted
+// list, the chunk prefix gives the first and last relevant entries). No other lane writes the run, so the
+// accumulation needs no synchronisation.
+__device__ __forceinline__ float corr_runs(const float* __restrict__ gs, const uint2* ent, const int* cpe,
+                                           float* cs, int D, int L, int u0, int cb, int lane) {
+    const int run = (D + 31) >> 5;
+    const int r0 = lane * run, r1 = min(r0 + run, D);
+    for (int c = r0; c < r1; ++c) cs[c] = 0.f;
     float mx = 0.f;
-    for (int c = lane; c < D; c += 32) mx = fmaxf(mx, cs[c]);
-    return warp_max(mx);
-}
-
-// Sparse rows: each candidate (one per lane, 32 per block) gathers the non-empty bins of its block's window
-// from the compacted list; the list's chunk prefix gives the window's first and last entries.
-__device__ __forceinline__ float corr_gather(const float* __restrict__ gs, const uint2* ent, const int* cpe,
-                                             float* cs, int NB, int D, int L, int u0, int cb, int lane) {
-    float mx = 0.f;
-    for (int b = 0; b < NB; ++b) {
-        const int c = 32 * b + lane;
-        const int t0 = u0 + min(c, D - 1);
-        const int e0 = cpe[(u0 + 32 * b) / cb];
-        const int e1 = cpe[(u0 + min(32 * b + 31, D - 1) + L - 1) / cb + 1];
-        float acc = 0.f;
-        for (int e = e0; e < e1; ++e) {
+    if (r0 < r1) {
+        const int e_lo = cpe[(u0 + r0) / cb];
+        const int e_hi = cpe[(u0 + r1 - 1 + L - 1) / cb + 1];
+        for (int e = e_lo; e < e_hi; ++e) {
             const uint2 en = ent[e];
-            const unsigned j = en.x - static_cast<unsigned>(t0);
-            if (j < static_cast<unsigned>(L)) acc = fmaf(__uint_as_float(en.y), gs[j], acc);
+            const float zc = __uint_as_float(en.y);
+            const int tc = static_cast<int>(en.x) - u0;  // candidate whose tap 0 falls on this bin
+            const int lo = max(tc - L + 1, r0), hi = min(tc, r1 - 1);
+            for (int c = lo; c <= hi; ++c) {
+                const float v = fmaf(zc, gs[tc - c], cs[c]);
+                cs[c] = v;
+                mx = fmaxf(mx, v);
+            }
         }
-        cs[c] = acc;
-        if (c < D) mx = fmaxf(mx, acc);
     }
     __syncwarp();
     return warp_max(mx);
@@ -444,8 +431,7 @@ __device__ __forceinline__ float correlate(const float* __restrict__ gs, const f
             }
         }
         __syncwarp();
-        if (nnz <= kNnzScatter) return corr_scatter(gs, ent, nnz, cs, NB, D, L, u0, lane);
-        return corr_gather(gs, ent, cpe, cs, NB, D, L, u0, CB, lane);
+        return corr_runs(gs, ent, cpe, cs, D, L, u0, CB, lane);
     }
     return corr_dense(gs, zs, cs, D, L, u0, lane);
 }
@@ -599,11 +585,15 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
 
         // exact best value of the block with the largest bound: a lower bound of the maximum
         float lb;
+        int cstar;  // its best candidate: the centre of the one-pass moments below
         {
             const int c = 32 * ub_b + lane;
             float l = -INFINITY;
             if (c < D) l = fmaf(lam2, cs[c], log2_prior(pr, static_cast<float>(a.dmin + c)));
-            lb = warp_max(l);
+            cstar = c < D ? c : 0x7fffffff;
+            warp_argmax(l, cstar);
+            lb = l;
+            if (cstar >= D) cstar = min(32 * ub_b, D - 1);
         }
         const float thr = lb - kPrune2;
         int nsurv = 0, bfirst = NB, blast = -1;
@@ -639,6 +629,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                     v[i] = q[i] = 0.f;
                     kk[i] = i < pr.n ? ex2(-2.f * pr.ck[i]) : 0.f;
                 }
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
                 for (int c = r0; c < r1; ++c) {
                     const float d = static_cast<float>(a.dmin + c);
                     if (((c - r0) & (kRestart - 1)) == 0) {  // exact restart of every component
@@ -664,26 +655,42 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                         best = w;
                         bidx = c;
                     }
+                    const float dd = static_cast<float>(c - cstar);
+                    s0 += w;
+                    s1 = fmaf(w, dd, s1);
+                    s2 = fmaf(w * dd, dd, s2);
                 }
                 warp_argmax(best, bidx);
                 __syncwarp();
                 if (best >= 0x1p-60f) {
-                    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-                    for (int c = r0; c < r1; ++c) {
-                        const float w = cs[c];
-                        const float dd = static_cast<float>(c - bidx);
-                        s0 += w;
-                        s1 = fmaf(w, dd, s1);
-                        s2 = fmaf(w * dd, dd, s2);
-                    }
                     s0 = warp_sum(s0);
                     s1 = warp_sum(s1);
                     s2 = warp_sum(s2);
-                    const float m1 = s1 / s0;
-                    mu_out = static_cast<float>(a.dmin + bidx) + m1;
+                    float ctr = static_cast<float>(cstar);
+                    float m1 = s1 / s0;
+                    float var = s2 / s0 - m1 * m1;
+                    if (m1 * m1 > 4.f * var + 1.f) {
+                        // the centre is far from the mean: second pass centred on the rounded mean
+                        const int cc = __float2int_rn(ctr + m1);
+                        s0 = s1 = s2 = 0.f;
+                        for (int c = r0; c < r1; ++c) {
+                            const float w = cs[c];
+                            const float dd = static_cast<float>(c - cc);
+                            s0 += w;
+                            s1 = fmaf(w, dd, s1);
+                            s2 = fmaf(w * dd, dd, s2);
+                        }
+                        s0 = warp_sum(s0);
+                        s1 = warp_sum(s1);
+                        s2 = warp_sum(s2);
+                        ctr = static_cast<float>(cc);
+                        m1 = s1 / s0;
+                        var = s2 / s0 - m1 * m1;
+                    }
+                    mu_out = static_cast<float>(a.dmin) + ctr + m1;
                     if (lane == 0) {
                         a.mu[p] = mu_out;
-                        a.var[p] = fmaxf(s2 / s0 - m1 * m1, 0.f);
+                        a.var[p] = fmaxf(var, 0.f);
                         if (a.argmax) a.argmax[p] = a.dmin + bidx;
                     }
                     done = true;
@@ -773,7 +780,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                     kin += zj[q];
                     za = fmaf(zj[q], aj[q], za);
                     if (zj[q] > 0.f) {
-                        if (aj[q] > 0.f) p1 += zj[q] * (aj[q] - u) / aj[q];
+                        if (aj[q] > 0.f) p1 += zj[q] * __fdividef(aj[q] - u, aj[q]);
                         else zero_tap = true;
                     }
                 }
@@ -799,7 +806,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
 #pragma unroll
                         for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
                             if (zj[q] > 0.f) {
-                                const float e = (aj[q] - u) / fmaf(f, aj[q] - u, u);
+                                const float e = __fdividef(aj[q] - u, fmaf(f, aj[q] - u, u));
                                 g = fmaf(zj[q], e, g);
                                 gp = fmaf(zj[q] * e, e, gp);
                             }
@@ -807,10 +814,11 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                         g = warp_sum(g);
                         gp = warp_sum(gp);
                         const float om = 1.f - f;
-                        g -= kout / om;
-                        gp += kout / (om * om);
+                        const float rom = __fdividef(1.f, om);
+                        g = fmaf(-kout, rom, g);
+                        gp = fmaf(kout * rom, rom, gp);
                         if (g > 0.f) lo = f; else hi = f;
-                        float fn = f + g / gp;  // Newton step on psi (psi' = -gp)
+                        float fn = f + __fdividef(g, gp);  // Newton step on psi (psi' = -gp)
                         if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
                         const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
                         f = fn;
