@@ -149,6 +149,77 @@ SPL_API spl_status spl_state_init(const spl_params* prm, float* mu, float* var, 
 SPL_API spl_status spl_pi_propagate(const spl_params* prm, const float* pi_in, const uint8_t* faulty, float* pi_out,
                             void* stream);
 
+/* ------------------------------------------------------------------------------------------------------------
+ * Batched filtering of many independent sequences from photon time-of-arrival lists
+ *
+ * The photon data of one pixel and frame is its set of ToAs y_k (Sec. II-A, Eq. lik_ideal) as integer bins in
+ * [0, T), stored in CSR form: the photons of pixel p are bins[offsets[p] .. offsets[p+1]). With photon lists
+ * the data term is C(d) = sum_k h[y_k - d + peak]^beta, the photon-sum form of Eq. beta_div2 (repeated bins
+ * count once per photon), which equals the histogram form on the histogram of the list. Everything else is
+ * spl_filter_step. Sequences may differ in every spl_params field (H, W, T, L, peak, dmin, dmax, beta,
+ * sigma_rw2, nu) and in their IRF.
+ *
+ * A batch plan owns a small device work queue and per-frame descriptor tables ("slots"). Typical use:
+ *   spl_batch_create(prms, nseq, nslots, &b);              allocates device tables
+ *   spl_batch_set(b, slot, frames) for each slot;          uploads pointers (synchronous, outside capture)
+ *   spl_batch_tune(b, slot, stream);                       optional: times tile sizes on real data
+ *   spl_batch_step(b, slot, stream) for frame after frame; one persistent launch each; capturable in a
+ *                                                          CUDA graph (a memset and a kernel launch)
+ *   spl_batch_status(b, &flags); spl_batch_destroy(b);
+ * ------------------------------------------------------------------------------------------------------------ */
+
+/* Device pointers of one sequence for one frame (all [P] of that sequence unless stated). */
+typedef struct {
+    const float* h;            /* [L] IRF of the sequence                                              */
+    const int32_t* offsets;    /* [P + 1] CSR offsets into bins, non-decreasing, offsets[0] = 0          */
+    const int32_t* bins;       /* photon ToA bins in [0, T)                                              */
+    const float* mu_in;        /* previous-frame Gaussians (as spl_filter_step)                          */
+    const float* var_in;
+    const uint8_t* present_in; /* nullable                                                               */
+    const uint8_t* faulty;     /* nullable                                                               */
+    const uint8_t* present_now;/* nullable                                                               */
+    float* mu_out;             /* must not alias mu_in / var_in                                          */
+    float* var_out;
+    int32_t* argmax;           /* nullable                                                               */
+    float* refl;               /* nullable (refl and bg both or neither)                                 */
+    float* bg;
+} spl_seq_frame;
+
+typedef struct spl_batch spl_batch;
+
+/* Device-side conditions recorded by spl_batch_step (read with spl_batch_status). */
+#define SPL_BATCH_BAD_BIN 1u       /* a photon bin outside [0, T): the photon was ignored              */
+#define SPL_BATCH_TOO_MANY 2u      /* a pixel had more than SPL_MAX_PHOTONS photons: outputs set to NaN */
+#define SPL_MAX_PHOTONS 1024
+
+/* Creates a plan for nseq sequences (prms: host array, validated like spl_filter_step) with nslots
+ * descriptor tables, on the current device. Allocates device memory (SPL_ENOMEM if it cannot). */
+SPL_API spl_status spl_batch_create(const spl_params* prms, int nseq, int nslots, spl_batch** out);
+
+/* Frees the plan's device memory. Must not be called while a step of the plan is in flight. */
+SPL_API void spl_batch_destroy(spl_batch* b);
+
+/* Uploads the per-sequence pointers of one frame (frames: host array of nseq) into table `slot`.
+ * Synchronous (a host-to-device copy); call it outside stream capture. */
+SPL_API spl_status spl_batch_set(spl_batch* b, int slot, const spl_seq_frame* frames);
+
+/* Runs one frame of every sequence (one outer iteration of Algorithm 1 each) from table `slot` on `stream`:
+ * a reset of the slot's work-queue head and one persistent kernel whose warps take (sequence, pixel-tile)
+ * units largest-first. Asynchronous, allocation-free; may be captured in a CUDA graph. Steps of the same
+ * slot must not run concurrently. */
+SPL_API spl_status spl_batch_step(spl_batch* b, int slot, void* stream);
+
+/* Times every candidate tile size (pixels per work unit) on table `slot` and keeps the fastest (the outputs
+ * of that slot are written several times with the same values). Synchronises the stream. */
+SPL_API spl_status spl_batch_tune(spl_batch* b, int slot, void* stream);
+
+/* Reports the plan's launch configuration (any pointer may be NULL). */
+SPL_API spl_status spl_batch_info(const spl_batch* b, int* tile, int* units, int* ctas, int* warps_per_cta);
+
+/* Reads and clears the device-side condition flags (SPL_BATCH_*) accumulated since the last call.
+ * Synchronous. */
+SPL_API spl_status spl_batch_status(spl_batch* b, uint32_t* flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,12 +14,13 @@ import ctypes as ct
 import torch
 
 from . import _abi
-from ._abi import (SPL_HIST_F16, SPL_HIST_F32, SPL_HIST_U16, SPL_MAX_BINS, SPL_MAX_TAPS, SplError,
-                   spl_hist, spl_params)
+from ._abi import (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY, SPL_HIST_F16, SPL_HIST_F32, SPL_HIST_U16,
+                   SPL_MAX_BINS, SPL_MAX_PHOTONS, SPL_MAX_TAPS, SplError, spl_hist, spl_params, spl_seq_frame)
 
 __all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate",
-           "spl_filter_step", "spl_state_init", "spl_pi_propagate", "SplError", "spl_params", "spl_hist",
-           "load_library", "cross_weights"]
+           "spl_filter_step", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
+           "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status", "SplError",
+           "spl_params", "spl_hist", "spl_seq_frame", "load_library", "cross_weights"]
 
 _FMT = {torch.uint16: SPL_HIST_U16, torch.float16: SPL_HIST_F16, torch.float32: SPL_HIST_F32}
 
@@ -214,3 +215,60 @@ def spl_pi_propagate(prm: spl_params, pi_in: torch.Tensor, faulty=None, pi_out=N
                                     _dev(faulty, "faulty", torch.uint8, P), _dev(pi_out, "pi_out", torch.float32, P),
                                     _stream(stream)))
     return pi_out
+
+
+# ---------------------------------------------------------------------------------------------------------
+# batched photon-list filtering
+# ---------------------------------------------------------------------------------------------------------
+
+
+def spl_batch_create(prms, nslots: int = 1):
+    """Plan for len(prms) sequences and nslots frame tables. Returns an opaque handle (int)."""
+    arr = (spl_params * len(prms))(*prms)
+    h = ct.c_void_p()
+    _abi.check(_abi.load().spl_batch_create(arr, len(prms), int(nslots), ct.byref(h)))
+    return h.value
+
+
+def spl_batch_destroy(handle) -> None:
+    if handle:
+        _abi.load().spl_batch_destroy(handle)
+
+
+_FRAME_KEYS = {"h": torch.float32, "offsets": torch.int32, "bins": torch.int32, "mu_in": torch.float32,
+               "var_in": torch.float32, "present_in": torch.uint8, "faulty": torch.uint8,
+               "present_now": torch.uint8, "mu_out": torch.float32, "var_out": torch.float32,
+               "argmax": torch.int32, "refl": torch.float32, "bg": torch.float32}
+
+
+def spl_batch_set(handle, slot: int, frames) -> None:
+    """Uploads one frame's device pointers for every sequence (frames: list of dicts of CUDA tensors keyed like
+    spl_seq_frame). The tensors must stay alive while steps of this slot may run."""
+    arr = (spl_seq_frame * len(frames))()
+    for i, fr in enumerate(frames):
+        for k, dt in _FRAME_KEYS.items():
+            setattr(arr[i], k, _dev(fr.get(k), f"frames[{i}].{k}", dt))
+    _abi.check(_abi.load().spl_batch_set(handle, int(slot), arr))
+
+
+def spl_batch_step(handle, slot: int, stream=None) -> None:
+    """One frame of every sequence from table `slot` (asynchronous; capturable in a CUDA graph)."""
+    _abi.check(_abi.load().spl_batch_step(handle, int(slot), _stream(stream)))
+
+
+def spl_batch_tune(handle, slot: int, stream=None) -> None:
+    """Times the candidate tile sizes on table `slot` and keeps the fastest (synchronous)."""
+    _abi.check(_abi.load().spl_batch_tune(handle, int(slot), _stream(stream)))
+
+
+def spl_batch_info(handle) -> dict:
+    v = [ct.c_int() for _ in range(4)]
+    _abi.check(_abi.load().spl_batch_info(handle, *[ct.byref(x) for x in v]))
+    return dict(tile=v[0].value, units=v[1].value, ctas=v[2].value, warps_per_cta=v[3].value)
+
+
+def spl_batch_status(handle) -> int:
+    """Reads and clears the device-side condition flags (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY)."""
+    f = ct.c_uint32()
+    _abi.check(_abi.load().spl_batch_status(handle, ct.byref(f)))
+    return int(f.value)

@@ -30,6 +30,16 @@ class spl_hist(ct.Structure):
     _fields_ = [("fmt", ct.c_int), ("data", ct.c_void_p), ("pitch", ct.c_int64)]
 
 
+class spl_seq_frame(ct.Structure):
+    _fields_ = [(n, ct.c_void_p) for n in ("h", "offsets", "bins", "mu_in", "var_in", "present_in", "faulty",
+                                           "present_now", "mu_out", "var_out", "argmax", "refl", "bg")]
+
+
+SPL_BATCH_BAD_BIN = 1
+SPL_BATCH_TOO_MANY = 2
+SPL_MAX_PHOTONS = 1024
+
+
 # name -> (restype, argtypes); mirrors include/spl.h
 _P = ct.POINTER(spl_params)
 _Hh = ct.POINTER(spl_hist)
@@ -42,6 +52,13 @@ SIGNATURES = {
     "spl_filter_step": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_state_init": (ct.c_int, [_P, _vp, _vp, _vp]),
     "spl_pi_propagate": (ct.c_int, [_P, _vp, _vp, _vp, _vp]),
+    "spl_batch_create": (ct.c_int, [_P, ct.c_int, ct.c_int, ct.POINTER(ct.c_void_p)]),
+    "spl_batch_destroy": (None, [_vp]),
+    "spl_batch_set": (ct.c_int, [_vp, ct.c_int, ct.POINTER(spl_seq_frame)]),
+    "spl_batch_step": (ct.c_int, [_vp, ct.c_int, _vp]),
+    "spl_batch_tune": (ct.c_int, [_vp, ct.c_int, _vp]),
+    "spl_batch_info": (ct.c_int, [_vp] + [ct.POINTER(ct.c_int)] * 4),
+    "spl_batch_status": (ct.c_int, [_vp, ct.POINTER(ct.c_uint32)]),
 }
 
 _lock = threading.Lock()

@@ -33,6 +33,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 size_t elem_size(int fmt) { return fmt == SPL_HIST_F32 ? 4 : 2; }
 
+}  // namespace
+
 // Geometry, domain and parameter checks shared by the depth calls (the domain reading is stated in spl.h).
 spl_status check_params(const spl_params* q, bool need_filter) {
     SPL_REQUIRE(q != nullptr, "prm is NULL");
@@ -64,6 +66,8 @@ spl_status check_params(const spl_params* q, bool need_filter) {
     }
     return SPL_OK;
 }
+
+namespace {
 
 spl_status check_hist(const spl_params* q, const spl_hist* z) {
     SPL_REQUIRE(z != nullptr && z->data != nullptr, "histogram z (or z->data) is NULL");

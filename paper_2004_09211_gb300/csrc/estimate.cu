@@ -1,82 +1,29 @@
-// Fused per-pixel kernel: robust data term (Eq. beta_div2), pseudo-posterior on the depth grid
-// (Eq. approx_post) with the spatio-temporal Gaussian-mixture prior (Eq. predict), moment matching
+// Fused per-pixel kernel over photon-count histograms: robust data term (Eq. beta_div2), pseudo-posterior on the
+// depth grid (Eq. approx_post) with the spatio-temporal Gaussian-mixture prior (Eq. predict), moment matching
 // (Eq. KL_div), and the background/reflectivity estimate (Sec. II-E).
 //
-// Mapping. One warp owns one pixel at a time (persistent grid-stride loop over pixels). The warp streams the
-// pixel's histogram row from HBM once with 16-byte loads into its shared-memory slice and keeps a prefix sum
-// of photon counts per 16-byte chunk (8 bins; 4 for float counts).
+// Mapping. One warp owns one pixel at a time (persistent grid-stride loop over pixels). While a pixel is
+// processed, the next pixel's histogram row is copied into the warp's shared-memory slice with cp.async and its
+// neighbour states are loaded into registers, so HBM and L2 latency overlap compute.
 //
 // Correlation. C(d) = sum_j g_j z[d - peak + j] (g = h^beta) for every candidate, into shared memory. A row
-// with few non-empty bins (photon-starved data) is scattered from a compacted list of those bins (exact zero
+// with few non-empty bins (photon-starved data) is correlated from a compacted list of those bins (exact zero
 // skip: each lane accumulates a contiguous run of candidates from the bins that reach it); a denser row uses
 // a register-blocked direct sum (8 candidates per lane, taps in groups of 4).
 //
-// Epilogue. ell(d) = lambda C(d) + log f(d) in log2 units. Candidates are grouped in blocks of 32. Each block
-// gets an upper bound of ell (lambda log2(e) max(g) times the photons in the block's window, plus the prior's
-// largest value on the block). The block with the largest bound is evaluated exactly; its best value LB is a
-// lower bound of the maximum, and every block whose bound is below LB - 64 is dropped: its weights are below
-// 2^-64 of the maximum, so the moments move by less than 8192^3 * 2^-64 < 3e-8 bins^2.
-//   * Few surviving blocks (a concentrated posterior): each is evaluated exactly in the log domain.
-//   * Many (a broad posterior): the weights 2^(ell - ref) are formed directly in the linear domain over the
-//     surviving range, each lane walking a contiguous run of candidates. The data factor costs one exp2 per
-//     candidate; each mixture component is advanced by the exact two-multiply recurrence of a Gaussian on a
-//     unit grid (value ratio, then ratio of ratios), restarted from exact exponentials every 16 candidates.
-//     All values are scaled by fixed upper bounds so nothing overflows; a value that underflows is below
-//     2^-126 while the largest weight is required to be at least 2^-60 (checked), so the dropped mass is
-//     below 2^-62 per candidate. When that check or the component-width condition (variance >= 1.5 bins^2,
-//     so 16 steps cannot underflow a component near its own peak) fails, the exact log-domain path runs.
-// Moments are then taken in a second pass centred on the argmax (no cancellation between S2/S0 and the
-// squared offset of the mean).
+// The pseudo-posterior moments and the intensity MLE are in pixel.cuh (shared with the photon-list kernel).
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "pixel.cuh"
 #include "spl_internal.h"
 
 namespace spl {
 namespace {
 
-constexpr float kLog2e = 1.4426950408889634f;
-constexpr float kLog2TwoPi = 2.6514961294723187f;  // log2(2 pi)
-constexpr int kMaxComp = 10;                        // 9 stencil entries + 1 merged weakly informative one
-constexpr int kNnzSparse = 320;                     // zero-skip correlation up to this many non-empty bins
-constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for dropping a block
-constexpr int kFewBlocks = 6;                       // at most this many surviving blocks: exact log path
-constexpr int kRestart = 16;                        // exact restart interval of the mixture recurrences
+using namespace px;
 
-__device__ __forceinline__ float ex2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Butterfly arg-max: every lane ends with the same (value, index); ties go to the smaller index.
-__device__ __forceinline__ void warp_argmax(float& v, int& i) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-        if (ov > v || (ov == v && oi < i)) {
-            v = ov;
-            i = oi;
-        }
-    }
-}
+constexpr int kNnzSparse = 320;  // zero-skip correlation up to this many non-empty bins
 
 // Shared-memory slice of one warp (all offsets in 4-byte words; every array starts 16-byte aligned).
 struct Slice {
@@ -235,111 +182,8 @@ __device__ __forceinline__ void warp_scan2(float* x, int* y, int n, int lane) {
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Prior (Eq. predict) in log2 units: component c contributes 2^(ca[c] - ck[c] (d - cm[c])^2)
-// ------------------------------------------------------------------------------------------------------------
-
-struct Prior {
-    float ca[kMaxComp], ck[kMaxComp], cm[kMaxComp];
-    float minv;  // smallest component variance
-    int n;
-};
-
-// Lane-parallel construction: lane k (< 9) owns stencil entry k. Entries with identical Gaussians (every
-// weakly informative one, and equal neighbour states) are merged by matching their (mean, variance) bits and
-// summing their weights; the distinct components are then broadcast to every lane in lane order.
-__device__ __forceinline__ void build_prior(const EstimateArgs& a, const Nbr& nb, int lane, Prior& pr) {
-    float w = 0.f, m = 0.f, v = 1.f;
-    if (a.prior_mode == PRIOR_GAUSS) {
-        if (lane == 0) {
-            w = 1.f;
-            m = nb.m;
-            v = nb.v;
-        }
-    } else if (a.prior_mode == PRIOR_STENCIL && lane < 9) {
-        w = a.nu[lane];
-        if (nb.info) {
-            m = nb.m;
-            v = nb.v + a.sigma_rw2;
-        } else {
-            m = a.flat_m;
-            v = a.flat_v + a.sigma_rw2;
-        }
-    }
-    const bool act = w > 0.f;
-    const unsigned long long key =
-        act ? (static_cast<unsigned long long>(__float_as_uint(m)) << 32) | __float_as_uint(v)
-            : 0xFFFFFFFF00000000ull | static_cast<unsigned>(lane);
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    float wsum = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const float wk = __shfl_sync(0xffffffffu, w, k);
-        if ((peers >> k) & 1u) wsum += wk;
-    }
-    const bool leader = act && lane == __ffs(peers) - 1;
-    unsigned lead = __ballot_sync(0xffffffffu, leader);
-    pr.n = __popc(lead);
-    const float ca_l = lg2(wsum) - 0.5f * (kLog2TwoPi + lg2(v));
-    const float ck_l = kLog2e / (2.f * v);
-    pr.minv = INFINITY;
-#pragma unroll
-    for (int i = 0; i < kMaxComp; ++i) {
-        const int src = lead ? __ffs(lead) - 1 : 0;
-        lead &= lead - 1;
-        pr.ca[i] = __shfl_sync(0xffffffffu, ca_l, src);
-        pr.ck[i] = __shfl_sync(0xffffffffu, ck_l, src);
-        pr.cm[i] = __shfl_sync(0xffffffffu, m, src);
-        const float vi = __shfl_sync(0xffffffffu, v, src);
-        if (i < pr.n) pr.minv = fminf(pr.minv, vi);
-    }
-}
-
-// log2 of the prior density at depth d (up to the constant shared by all d).
-__device__ __forceinline__ float log2_prior(const Prior& pr, float d) {
-    if (pr.n == 0) return 0.f;
-    if (pr.n == 1) {
-        const float e = d - pr.cm[0];
-        return pr.ca[0] - pr.ck[0] * e * e;
-    }
-    float t[kMaxComp];
-    float mx = -INFINITY;
-#pragma unroll
-    for (int i = 0; i < kMaxComp; ++i) {
-        if (i >= pr.n) break;
-        const float e = d - pr.cm[i];
-        t[i] = pr.ca[i] - pr.ck[i] * e * e;
-        mx = fmaxf(mx, t[i]);
-    }
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < kMaxComp; ++i) {
-        if (i >= pr.n) break;
-        s += ex2(t[i] - mx);
-    }
-    return mx + lg2(s);
-}
-
-// Upper bound of log2_prior over depths [lo, hi].
-__device__ __forceinline__ float log2_prior_bound(const Prior& pr, float lo, float hi) {
-    if (pr.n == 0) return 0.f;
-    float mx = -INFINITY;
-#pragma unroll
-    for (int i = 0; i < kMaxComp; ++i) {
-        if (i >= pr.n) break;
-        const float e = fmaxf(fmaxf(lo - pr.cm[i], pr.cm[i] - hi), 0.f);
-        mx = fmaxf(mx, pr.ca[i] - pr.ck[i] * e * e);
-    }
-    return pr.n > 1 ? mx + lg2(static_cast<float>(pr.n)) + 1e-3f : mx + 1e-3f;
-}
-
-// ------------------------------------------------------------------------------------------------------------
 // Correlation C(d) for every candidate into cs[0 .. 32 NB); each routine returns max_d C(d) (warp-uniform)
 // ------------------------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ void zero_words(float* x, int n4, int lane) {
-    for (int i = lane; i < n4; i += 32) reinterpret_cast<float4*>(x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-}
 
 // Sparse rows: lane l owns the contiguous run [r0, r1) of candidates and adds z_t g_{t-u0-c} into each
 // candidate c of its run for every non-empty bin t whose taps reach the run (the bins come from the compacted
@@ -560,200 +404,47 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             continue;
         }
 
-        // ---- 3. prior and per-block upper bounds of the log2 pseudo-posterior ----
+        // ---- 3. prior (Eq. predict) from the staged neighbour states ----
         Prior pr;
-        build_prior(a, nb, lane, pr);
-        const float lam2 = a.lam2;
-        float ubest = -INFINITY;
-        int ub_b = 0x7fffffff;
-        for (int b = lane; b < NB; b += 32) {
-            const int s_bin = u0 + 32 * b;
-            const int last = min(32 * b + 31, D - 1);
-            const int e_bin = u0 + last + L - 1;
-            const float nb = empty ? 0.f : cps[e_bin / CB + 1] - cps[s_bin / CB];
-            const float ub = lam2 * gmax * nb * 1.0001f +
-                             log2_prior_bound(pr, static_cast<float>(a.dmin + 32 * b), static_cast<float>(a.dmin + last));
-            ubs[b] = ub;
-            if (ub > ubest) {
-                ubest = ub;
-                ub_b = b;
-            }
-        }
-        warp_argmax(ubest, ub_b);
-        if (ub_b >= NB) ub_b = 0;  // every bound was NaN (invalid inputs): keep the block index in range
-        __syncwarp();
-
-        // exact best value of the block with the largest bound: a lower bound of the maximum
-        float lb;
-        int cstar;  // its best candidate: the centre of the one-pass moments below
         {
-            const int c = 32 * ub_b + lane;
-            float l = -INFINITY;
-            if (c < D) l = fmaf(lam2, cs[c], log2_prior(pr, static_cast<float>(a.dmin + c)));
-            cstar = c < D ? c : 0x7fffffff;
-            warp_argmax(l, cstar);
-            lb = l;
-            if (cstar >= D) cstar = min(32 * ub_b, D - 1);
-        }
-        const float thr = lb - kPrune2;
-        int nsurv = 0, bfirst = NB, blast = -1;
-        for (int w0 = 0; w0 < NB; w0 += 32) {
-            const unsigned m =
-                __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
-            if (m) {
-                nsurv += __popc(m);
-                bfirst = min(bfirst, w0 + __ffs(m) - 1);
-                blast = w0 + 31 - __clz(m);
+            float w = 0.f, m = 0.f, v = 1.f;
+            if (a.prior_mode == PRIOR_GAUSS) {
+                if (lane == 0) {
+                    w = 1.f;
+                    m = nb.m;
+                    v = nb.v;
+                }
+            } else if (a.prior_mode == PRIOR_STENCIL && lane < 9) {
+                w = a.nu[lane];
+                m = nb.info ? nb.m : a.flat_m;
+                v = (nb.info ? nb.v : a.flat_v) + a.sigma_rw2;
             }
+            build_prior(w, m, v, lane, pr);
         }
 
-        float best = -INFINITY;
-        int bidx = 0x7fffffff;
-        float mu_out = 0.f;
-        bool done = false;
-
-        // ---- 4a. linear-domain weights over the surviving range (when its exactness conditions hold) ----
-        if ((blast - bfirst + 1) <= max(8, 2 * nsurv) && !(pr.minv < 1.5f)) {
-            {
-                float sref = pr.n > 0 ? -INFINITY : 0.f;
-#pragma unroll
-                for (int i = 0; i < kMaxComp; ++i)
-                    if (i < pr.n) sref = fmaxf(sref, pr.ca[i]);
-                const float xref = lam2 * cmax;  // lambda log2(e) max_d C(d)
-                const int c_lo = 32 * bfirst, c_hi = min(32 * blast + 31, D - 1);
-                const int run = (c_hi - c_lo + 32) >> 5;
-                const int r0 = c_lo + lane * run, r1 = min(r0 + run, c_hi + 1);
-                float v[kMaxComp], q[kMaxComp], kk[kMaxComp];
-#pragma unroll
-                for (int i = 0; i < kMaxComp; ++i) {
-                    v[i] = q[i] = 0.f;
-                    kk[i] = i < pr.n ? ex2(-2.f * pr.ck[i]) : 0.f;
-                }
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-                for (int c = r0; c < r1; ++c) {
-                    const float d = static_cast<float>(a.dmin + c);
-                    if (((c - r0) & (kRestart - 1)) == 0) {  // exact restart of every component
-#pragma unroll
-                        for (int i = 0; i < kMaxComp; ++i)
-                            if (i < pr.n) {
-                                const float e = d - pr.cm[i];
-                                v[i] = ex2(pr.ca[i] - pr.ck[i] * e * e - sref);
-                                q[i] = ex2(fminf(-pr.ck[i] * (2.f * e + 1.f), 100.f));
-                            }
-                    }
-                    float m = pr.n == 0 ? 1.f : 0.f;
-#pragma unroll
-                    for (int i = 0; i < kMaxComp; ++i)
-                        if (i < pr.n) {
-                            m += v[i];
-                            v[i] *= q[i];
-                            q[i] *= kk[i];
-                        }
-                    const float w = ex2(fmaf(lam2, cs[c], -xref)) * m;
-                    cs[c] = w;
-                    if (w > best) {
-                        best = w;
-                        bidx = c;
-                    }
-                    const float dd = static_cast<float>(c - cstar);
-                    s0 += w;
-                    s1 = fmaf(w, dd, s1);
-                    s2 = fmaf(w * dd, dd, s2);
-                }
-                warp_argmax(best, bidx);
-                __syncwarp();
-                if (best >= 0x1p-60f) {
-                    s0 = warp_sum(s0);
-                    s1 = warp_sum(s1);
-                    s2 = warp_sum(s2);
-                    float ctr = static_cast<float>(cstar);
-                    float m1 = s1 / s0;
-                    float var = s2 / s0 - m1 * m1;
-                    if (m1 * m1 > 4.f * var + 1.f) {
-                        // the centre is far from the mean: second pass centred on the rounded mean
-                        const int cc = __float2int_rn(ctr + m1);
-                        s0 = s1 = s2 = 0.f;
-                        for (int c = r0; c < r1; ++c) {
-                            const float w = cs[c];
-                            const float dd = static_cast<float>(c - cc);
-                            s0 += w;
-                            s1 = fmaf(w, dd, s1);
-                            s2 = fmaf(w * dd, dd, s2);
-                        }
-                        s0 = warp_sum(s0);
-                        s1 = warp_sum(s1);
-                        s2 = warp_sum(s2);
-                        ctr = static_cast<float>(cc);
-                        m1 = s1 / s0;
-                        var = s2 / s0 - m1 * m1;
-                    }
-                    mu_out = static_cast<float>(a.dmin) + ctr + m1;
-                    if (lane == 0) {
-                        a.mu[p] = mu_out;
-                        a.var[p] = fmaxf(var, 0.f);
-                        if (a.argmax) a.argmax[p] = a.dmin + bidx;
-                    }
-                    done = true;
-                } else {
-                    // the weights overwrote C on the surviving range: recompute it for the exact path
-                    correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane);
-                }
-            }
-        }
-
-        // ---- 4b. concentrated posterior (or fallback): exact log-domain ell on the surviving blocks ----
-        if (!done) {
-            best = -INFINITY;
-            bidx = 0x7fffffff;
-            for (int w0 = 0; w0 < NB; w0 += 32) {
-                unsigned m =
-                    __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
-                while (m) {
-                    const int b = w0 + __ffs(m) - 1;
-                    m &= m - 1;
-                    const int c = 32 * b + lane;
-                    float l = -INFINITY;
-                    if (c < D) l = fmaf(lam2, cs[c], log2_prior(pr, static_cast<float>(a.dmin + c)));
-                    cs[c] = l;
-                    if (l > best || (l == best && c < bidx)) {
-                        best = l;
-                        bidx = c;
-                    }
-                }
-            }
-            warp_argmax(best, bidx);
-            if (bidx == 0x7fffffff) bidx = 0;  // every ell was NaN (invalid inputs): keep indices in range
-            __syncwarp();
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int w0 = 0; w0 < NB; w0 += 32) {
-                unsigned m =
-                    __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
-                while (m) {
-                    const int b = w0 + __ffs(m) - 1;
-                    m &= m - 1;
-                    const int c = 32 * b + lane;
-                    const float w = ex2(cs[c] - best);  // 0 for lanes past D (ell = -inf)
-                    const float dd = static_cast<float>(c - bidx);
-                    s0 += w;
-                    s1 = fmaf(w, dd, s1);
-                    s2 = fmaf(w * dd, dd, s2);
-                }
-            }
-            s0 = warp_sum(s0);
-            s1 = warp_sum(s1);
-            s2 = warp_sum(s2);
-            const float m1 = s1 / s0;
-            mu_out = static_cast<float>(a.dmin + bidx) + m1;
-            if (lane == 0) {
-                a.mu[p] = mu_out;
-                a.var[p] = fmaxf(s2 / s0 - m1 * m1, 0.f);
-                if (a.argmax) a.argmax[p] = a.dmin + bidx;
-            }
+        // ---- 4. argmax, mean and variance of the pseudo-posterior (Eq. approx_post, Eq. KL_div) ----
+        Grid grid;
+        grid.D = D;
+        grid.NB = NB;
+        grid.dmin = a.dmin;
+        grid.u0 = u0;
+        grid.L = L;
+        grid.lam2 = a.lam2;
+        grid.gmax = gmax;
+        int bidx;
+        float mu, var;
+        posterior(
+            grid, pr, cmax, empty, cs, ubs, [&](int s_bin, int e_bin) { return cps[e_bin / CB + 1] - cps[s_bin / CB]; },
+            [&]() { correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane); }, lane, bidx, mu,
+            var);
+        if (lane == 0) {
+            a.mu[p] = mu;
+            a.var[p] = var;
+            if (a.argmax) a.argmax[p] = a.dmin + bidx;
         }
 
         // ---- 5. background b and reflectivity r (Sec. II-E) ----
         if (a.refl) {
-            const float mu = mu_out;
             float r = 0.f, b = 0.f;
             const bool present = a.present_now ? a.present_now[p] != 0 : true;
             if (faulty) {
@@ -762,71 +453,15 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                 r = 0.f;
                 b = K / static_cast<float>(T);
             } else {
-                // MLE of the signal fraction f of the two-component model "template a_t, uniform 1/T"
-                // (Eq. lik_bg with the template at round(mu)); then r = f K / sum(h), b = (1 - f) K / T.
-                // psi(f) = sum_W z (a - u) / (u + f (a - u)) - Kout / (1 - f) is decreasing on [0, 1):
-                // safeguarded Newton on psi with the bracket [lo, hi] kept around its root.
-                int t0 = __float2int_rn(mu) - a.peak;
-                t0 = min(max(t0, 0), T - L);
-                const float u = 1.f / static_cast<float>(T);
+                const int t0 = min(max(__float2int_rn(mu) - a.peak, 0), T - L);  // template at round(mu)
                 float zj[SPL_MAX_TAPS / 32], aj[SPL_MAX_TAPS / 32];
-                float kin = 0.f, za = 0.f, p1 = 0.f;
-                bool zero_tap = false;
 #pragma unroll
                 for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
                     const int j = lane + 32 * q;
                     zj[q] = j < L ? zs[t0 + j] : 0.f;
                     aj[q] = j < L ? as[j] : 0.f;
-                    kin += zj[q];
-                    za = fmaf(zj[q], aj[q], za);
-                    if (zj[q] > 0.f) {
-                        if (aj[q] > 0.f) p1 += zj[q] * __fdividef(aj[q] - u, aj[q]);
-                        else zero_tap = true;
-                    }
                 }
-                kin = warp_sum(kin);
-                za = warp_sum(za);
-                p1 = warp_sum(p1);
-                zero_tap = __any_sync(0xffffffffu, zero_tap);
-                const float kout = fmaxf(K - kin, 0.f);
-                const float psi0 = static_cast<float>(T) * za - K;
-                float f;
-                if (!(psi0 > 0.f)) {
-                    f = 0.f;
-                } else if (!(kout > 0.f) && !zero_tap && p1 >= 0.f) {
-                    f = 1.f;
-                } else {
-                    float lo = 0.f, hi = 1.f;
-                    // start from the box-template estimate (window excess over the flat background)
-                    const float fr = static_cast<float>(L) * u;
-                    f = fr < 1.f ? (kin - K * fr) / (K * (1.f - fr)) : 0.5f;
-                    f = fminf(fmaxf(f, 0.02f), 0.98f);
-                    for (int it = 0; it < 64; ++it) {
-                        float g = 0.f, gp = 0.f;
-#pragma unroll
-                        for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
-                            if (zj[q] > 0.f) {
-                                const float e = __fdividef(aj[q] - u, fmaf(f, aj[q] - u, u));
-                                g = fmaf(zj[q], e, g);
-                                gp = fmaf(zj[q] * e, e, gp);
-                            }
-                        }
-                        g = warp_sum(g);
-                        gp = warp_sum(gp);
-                        const float om = 1.f - f;
-                        const float rom = __fdividef(1.f, om);
-                        g = fmaf(-kout, rom, g);
-                        gp = fmaf(kout * rom, rom, gp);
-                        if (g > 0.f) lo = f; else hi = f;
-                        float fn = f + __fdividef(g, gp);  // Newton step on psi (psi' = -gp)
-                        if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
-                        const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
-                        f = fn;
-                        if (conv) break;
-                    }
-                }
-                r = f * K / hsum;
-                b = (1.f - f) * K * u;
+                intensity_mle<SPL_MAX_TAPS / 32>(zj, aj, K, L, T, hsum, r, b);
             }
             if (lane == 0) {
                 a.refl[p] = r;

@@ -1,0 +1,419 @@
+// Per-pixel device code shared by the histogram kernel (estimate.cu) and the photon-list batch kernel
+// (batch.cu): one warp per pixel, the candidate depths of the pixel in shared memory.
+//
+//   build_prior     Eq. predict: the Gaussian-mixture prior of one pixel (lanes 0-8 own the 3x3 entries).
+//   posterior       Eq. approx_post + Eq. KL_div: argmax, mean and variance of the pseudo-posterior on the
+//                   integer grid, from C(d) already in shared memory, with bound-based block pruning and the
+//                   linear-domain evaluation described below.
+//   intensity_mle   Sec. II-E: background and reflectivity by maximum likelihood under Eq. lik_bg_poisson.
+//
+// Pruning. Candidates are grouped in blocks of 32. Each block gets an upper bound of ell = lambda log2(e) C(d)
+// + log2 f(d): lambda log2(e) max(g) times the photons in the block's window, plus the prior's largest value
+// on the block. The block with the largest bound is evaluated exactly; its best value LB is a lower bound of
+// the maximum, and every block whose bound is below LB - 64 is dropped: its weights are below 2^-64 of the
+// maximum, so the moments move by less than 8192^3 * 2^-64 < 3e-8 bins^2. The argmax always lies in a kept
+// block.
+//
+// Linear-domain evaluation. Over the range of kept blocks the weights 2^(ell - ref) are formed directly: each
+// lane walks a contiguous run of candidates; the data factor costs one exp2 per candidate and each mixture
+// component is advanced by the exact two-multiply recurrence of a Gaussian on a unit grid (value ratio, then
+// ratio of ratios), restarted from exact exponentials every 16 candidates. All values are scaled by upper
+// bounds so nothing overflows; a value that underflows is below 2^-126 while the largest weight must be at
+// least 2^-60 (checked), so the lost mass is below 2^-62 per candidate. Components narrower than 1.5 bins^2
+// (where 16 steps could underflow a component near its own peak), a scattered set of kept blocks, or a failed
+// check send the pixel through the exact log-domain path instead. The moments are accumulated in the same
+// pass about the best candidate of the leading block, and again about the rounded mean when that centre lies
+// more than two standard deviations away (so S2/S0 and the squared offset of the mean never cancel badly).
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+namespace spl {
+namespace px {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLog2TwoPi = 2.6514961294723187f;  // log2(2 pi)
+constexpr int kMaxComp = 10;                        // 9 stencil entries + 1 merged weakly informative one
+constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for dropping a block
+constexpr int kRestart = 16;                        // exact restart interval of the mixture recurrences
+
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Butterfly arg-max: every lane ends with the same (value, index); ties go to the smaller index.
+__device__ __forceinline__ void warp_argmax(float& v, int& i) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+}
+
+__device__ __forceinline__ void zero_words(float* x, int n4, int lane) {
+    for (int i = lane; i < n4; i += 32) reinterpret_cast<float4*>(x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Prior (Eq. predict) in log2 units: component c contributes 2^(ca[c] - ck[c] (d - cm[c])^2)
+// ------------------------------------------------------------------------------------------------------------
+
+struct Prior {
+    float ca[kMaxComp], ck[kMaxComp], cm[kMaxComp];
+    float minv;  // smallest component variance
+    int n;
+};
+
+// Lane k (< 9) passes stencil entry k as (weight w, mean m, variance v); w = 0 marks an unused entry. Entries
+// with identical Gaussians (every weakly informative one, and equal neighbour states) are merged by matching
+// their (mean, variance) bits and summing their weights; the distinct components are then broadcast to every
+// lane in lane order.
+__device__ __forceinline__ void build_prior(float w, float m, float v, int lane, Prior& pr) {
+    const bool act = w > 0.f;
+    if (!act) v = 1.f;
+    const unsigned long long key =
+        act ? (static_cast<unsigned long long>(__float_as_uint(m)) << 32) | __float_as_uint(v)
+            : 0xFFFFFFFF00000000ull | static_cast<unsigned>(lane);
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    float wsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float wk = __shfl_sync(0xffffffffu, w, k);
+        if ((peers >> k) & 1u) wsum += wk;
+    }
+    const bool leader = act && lane == __ffs(peers) - 1;
+    unsigned lead = __ballot_sync(0xffffffffu, leader);
+    pr.n = __popc(lead);
+    const float ca_l = lg2(wsum) - 0.5f * (kLog2TwoPi + lg2(v));
+    const float ck_l = kLog2e / (2.f * v);
+    pr.minv = INFINITY;
+#pragma unroll
+    for (int i = 0; i < kMaxComp; ++i) {
+        const int src = lead ? __ffs(lead) - 1 : 0;
+        lead &= lead - 1;
+        pr.ca[i] = __shfl_sync(0xffffffffu, ca_l, src);
+        pr.ck[i] = __shfl_sync(0xffffffffu, ck_l, src);
+        pr.cm[i] = __shfl_sync(0xffffffffu, m, src);
+        const float vi = __shfl_sync(0xffffffffu, v, src);
+        if (i < pr.n) pr.minv = fminf(pr.minv, vi);
+    }
+}
+
+// log2 of the prior density at depth d (up to the constant shared by all d), by log-sum-exp.
+__device__ __forceinline__ float log2_prior(const Prior& pr, float d) {
+    if (pr.n == 0) return 0.f;
+    if (pr.n == 1) {
+        const float e = d - pr.cm[0];
+        return pr.ca[0] - pr.ck[0] * e * e;
+    }
+    float t[kMaxComp];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < kMaxComp; ++i) {
+        if (i >= pr.n) break;
+        const float e = d - pr.cm[i];
+        t[i] = pr.ca[i] - pr.ck[i] * e * e;
+        mx = fmaxf(mx, t[i]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < kMaxComp; ++i) {
+        if (i >= pr.n) break;
+        s += ex2(t[i] - mx);
+    }
+    return mx + lg2(s);
+}
+
+// Upper bound of log2_prior over depths [lo, hi].
+__device__ __forceinline__ float log2_prior_bound(const Prior& pr, float lo, float hi) {
+    if (pr.n == 0) return 0.f;
+    float mx = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < kMaxComp; ++i) {
+        if (i >= pr.n) break;
+        const float e = fmaxf(fmaxf(lo - pr.cm[i], pr.cm[i] - hi), 0.f);
+        mx = fmaxf(mx, pr.ca[i] - pr.ck[i] * e * e);
+    }
+    return pr.n > 1 ? mx + lg2(static_cast<float>(pr.n)) + 1e-3f : mx + 1e-3f;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Pseudo-posterior moments
+// ------------------------------------------------------------------------------------------------------------
+
+struct Grid {
+    int D, NB, dmin, u0, L;  // candidates, blocks of 32, first depth, first bin of candidate 0, taps
+    float lam2, gmax;        // lambda log2(e), max_j g_j
+};
+
+// cs[0 .. D) holds C(d) on entry; cs[0 .. 32 NB) and ubs[0 .. NB) are scratch. count(s, e) returns an upper
+// bound of the photons in bins [s, e] (evaluated per lane). restore() writes C back into cs (needed only on
+// the rare fallback from the linear path). Outputs: index of the smallest maximiser, mean depth and variance.
+template <class Count, class Restore>
+__device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float cmax, bool empty, float* cs,
+                                          float* ubs, Count count, Restore restore, int lane, int& bidx_out,
+                                          float& mu_out, float& var_out) {
+    const int D = g.D, NB = g.NB;
+    const float lam2 = g.lam2;
+    // per-block upper bounds of ell
+    float ubest = -INFINITY;
+    int ub_b = 0x7fffffff;
+    for (int b = lane; b < NB; b += 32) {
+        const int last = min(32 * b + 31, D - 1);
+        const float nb = empty ? 0.f : count(g.u0 + 32 * b, g.u0 + last + g.L - 1);
+        const float ub = lam2 * g.gmax * nb * 1.0001f +
+                         log2_prior_bound(pr, static_cast<float>(g.dmin + 32 * b), static_cast<float>(g.dmin + last));
+        ubs[b] = ub;
+        if (ub > ubest) {
+            ubest = ub;
+            ub_b = b;
+        }
+    }
+    warp_argmax(ubest, ub_b);
+    if (ub_b >= NB) ub_b = 0;  // every bound was NaN (invalid inputs): keep the block index in range
+    __syncwarp();
+
+    // exact best value of the block with the largest bound: a lower bound of the maximum, and its position
+    float lb;
+    int cstar;
+    {
+        const int c = 32 * ub_b + lane;
+        float l = -INFINITY;
+        if (c < D) l = fmaf(lam2, cs[c], log2_prior(pr, static_cast<float>(g.dmin + c)));
+        cstar = c < D ? c : 0x7fffffff;
+        warp_argmax(l, cstar);
+        lb = l;
+        if (cstar >= D) cstar = min(32 * ub_b, D - 1);
+    }
+    const float thr = lb - kPrune2;
+    int nsurv = 0, bfirst = NB, blast = -1;
+    for (int w0 = 0; w0 < NB; w0 += 32) {
+        const unsigned m = __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
+        if (m) {
+            nsurv += __popc(m);
+            bfirst = min(bfirst, w0 + __ffs(m) - 1);
+            blast = w0 + 31 - __clz(m);
+        }
+    }
+
+    // ---- linear-domain weights over the range of kept blocks ----
+    if ((blast - bfirst + 1) <= max(8, 2 * nsurv) && !(pr.minv < 1.5f)) {
+        float sref = pr.n > 0 ? -INFINITY : 0.f;
+#pragma unroll
+        for (int i = 0; i < kMaxComp; ++i)
+            if (i < pr.n) sref = fmaxf(sref, pr.ca[i]);
+        const float xref = lam2 * cmax;  // lambda log2(e) max_d C(d)
+        const int c_lo = 32 * bfirst, c_hi = min(32 * blast + 31, D - 1);
+        const int run = (c_hi - c_lo + 32) >> 5;
+        const int r0 = c_lo + lane * run, r1 = min(r0 + run, c_hi + 1);
+        float v[kMaxComp], q[kMaxComp], kk[kMaxComp];
+#pragma unroll
+        for (int i = 0; i < kMaxComp; ++i) {
+            v[i] = q[i] = 0.f;
+            kk[i] = i < pr.n ? ex2(-2.f * pr.ck[i]) : 0.f;
+        }
+        float best = -INFINITY;
+        int bidx = 0x7fffffff;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int c = r0; c < r1; ++c) {
+            const float d = static_cast<float>(g.dmin + c);
+            if (((c - r0) & (kRestart - 1)) == 0) {  // exact restart of every component
+#pragma unroll
+                for (int i = 0; i < kMaxComp; ++i)
+                    if (i < pr.n) {
+                        const float e = d - pr.cm[i];
+                        v[i] = ex2(pr.ca[i] - pr.ck[i] * e * e - sref);
+                        q[i] = ex2(fminf(-pr.ck[i] * (2.f * e + 1.f), 100.f));
+                    }
+            }
+            float m = pr.n == 0 ? 1.f : 0.f;
+#pragma unroll
+            for (int i = 0; i < kMaxComp; ++i)
+                if (i < pr.n) {
+                    m += v[i];
+                    v[i] *= q[i];
+                    q[i] *= kk[i];
+                }
+            const float w = ex2(fmaf(lam2, cs[c], -xref)) * m;
+            cs[c] = w;
+            if (w > best) {
+                best = w;
+                bidx = c;
+            }
+            const float dd = static_cast<float>(c - cstar);
+            s0 += w;
+            s1 = fmaf(w, dd, s1);
+            s2 = fmaf(w * dd, dd, s2);
+        }
+        warp_argmax(best, bidx);
+        __syncwarp();
+        if (best >= 0x1p-60f) {
+            s0 = warp_sum(s0);
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            float ctr = static_cast<float>(cstar);
+            float m1 = s1 / s0;
+            float var = s2 / s0 - m1 * m1;
+            if (m1 * m1 > 4.f * var + 1.f) {  // centre far from the mean: again about the rounded mean
+                const int cc = __float2int_rn(ctr + m1);
+                s0 = s1 = s2 = 0.f;
+                for (int c = r0; c < r1; ++c) {
+                    const float w = cs[c];
+                    const float dd = static_cast<float>(c - cc);
+                    s0 += w;
+                    s1 = fmaf(w, dd, s1);
+                    s2 = fmaf(w * dd, dd, s2);
+                }
+                s0 = warp_sum(s0);
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+                ctr = static_cast<float>(cc);
+                m1 = s1 / s0;
+                var = s2 / s0 - m1 * m1;
+            }
+            bidx_out = bidx;
+            mu_out = static_cast<float>(g.dmin) + ctr + m1;
+            var_out = fmaxf(var, 0.f);
+            return;
+        }
+        restore();  // the weights overwrote C on the kept range
+    }
+
+    // ---- exact log-domain ell on the kept blocks ----
+    float best = -INFINITY;
+    int bidx = 0x7fffffff;
+    for (int w0 = 0; w0 < NB; w0 += 32) {
+        unsigned m = __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
+        while (m) {
+            const int b = w0 + __ffs(m) - 1;
+            m &= m - 1;
+            const int c = 32 * b + lane;
+            float l = -INFINITY;
+            if (c < D) l = fmaf(lam2, cs[c], log2_prior(pr, static_cast<float>(g.dmin + c)));
+            cs[c] = l;
+            if (l > best || (l == best && c < bidx)) {
+                best = l;
+                bidx = c;
+            }
+        }
+    }
+    warp_argmax(best, bidx);
+    if (bidx == 0x7fffffff) bidx = 0;  // every ell was NaN (invalid inputs): keep indices in range
+    __syncwarp();
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int w0 = 0; w0 < NB; w0 += 32) {
+        unsigned m = __ballot_sync(0xffffffffu, (w0 + lane < NB && ubs[w0 + lane] >= thr) || w0 + lane == ub_b);
+        while (m) {
+            const int b = w0 + __ffs(m) - 1;
+            m &= m - 1;
+            const int c = 32 * b + lane;
+            const float w = ex2(cs[c] - best);  // 0 for lanes past D (ell = -inf)
+            const float dd = static_cast<float>(c - bidx);
+            s0 += w;
+            s1 = fmaf(w, dd, s1);
+            s2 = fmaf(w * dd, dd, s2);
+        }
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    const float m1 = s1 / s0;
+    bidx_out = bidx;
+    mu_out = static_cast<float>(g.dmin + bidx) + m1;
+    var_out = fmaxf(s2 / s0 - m1 * m1, 0.f);
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Background and reflectivity (Sec. II-E)
+// ------------------------------------------------------------------------------------------------------------
+
+// MLE of the signal fraction f of the two-component model "template a_t, uniform 1/T" (Eq. lik_bg with the
+// template placed on the window W), then r = f K / sum(h) and b = (1 - f) K / T. Lane items: zj[q] = photons
+// in a window bin whose normalised template value is aj[q] (items of all lanes together cover W once).
+// psi(f) = sum_W z (a - u) / (u + f (a - u)) - Kout / (1 - f), u = 1/T, is decreasing on [0, 1): safeguarded
+// Newton on psi with the bracket [lo, hi] kept around its root.
+template <int NQ>
+__device__ __forceinline__ void intensity_mle(const float* zj, const float* aj, float K, int L, int T, float hsum,
+                                              float& r, float& b) {
+    const float u = 1.f / static_cast<float>(T);
+    float kin = 0.f, za = 0.f, p1 = 0.f;
+    bool zero_tap = false;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        kin += zj[q];
+        za = fmaf(zj[q], aj[q], za);
+        if (zj[q] > 0.f) {
+            if (aj[q] > 0.f) p1 += zj[q] * __fdividef(aj[q] - u, aj[q]);
+            else zero_tap = true;
+        }
+    }
+    kin = warp_sum(kin);
+    za = warp_sum(za);
+    p1 = warp_sum(p1);
+    zero_tap = __any_sync(0xffffffffu, zero_tap);
+    const float kout = fmaxf(K - kin, 0.f);
+    const float psi0 = static_cast<float>(T) * za - K;
+    float f;
+    if (!(psi0 > 0.f)) {
+        f = 0.f;
+    } else if (!(kout > 0.f) && !zero_tap && p1 >= 0.f) {
+        f = 1.f;
+    } else {
+        float lo = 0.f, hi = 1.f;
+        // start from the box-template estimate (window excess over the flat background)
+        const float fr = static_cast<float>(L) * u;
+        f = fr < 1.f ? (kin - K * fr) / (K * (1.f - fr)) : 0.5f;
+        f = fminf(fmaxf(f, 0.02f), 0.98f);
+        for (int it = 0; it < 64; ++it) {
+            float gs = 0.f, gp = 0.f;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if (zj[q] > 0.f) {
+                    const float e = __fdividef(aj[q] - u, fmaf(f, aj[q] - u, u));
+                    gs = fmaf(zj[q], e, gs);
+                    gp = fmaf(zj[q] * e, e, gp);
+                }
+            }
+            gs = warp_sum(gs);
+            gp = warp_sum(gp);
+            const float rom = __fdividef(1.f, 1.f - f);
+            gs = fmaf(-kout, rom, gs);
+            gp = fmaf(kout * rom, rom, gp);
+            if (gs > 0.f) lo = f; else hi = f;
+            float fn = f + __fdividef(gs, gp);  // Newton step on psi (psi' = -gp)
+            if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
+            const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
+            f = fn;
+            if (conv) break;
+        }
+    }
+    r = f * K / hsum;
+    b = (1.f - f) * K * u;
+}
+
+}  // namespace px
+}  // namespace spl

@@ -52,6 +52,9 @@ struct Geometry {
 // Records a formatted message as this thread's last error.
 void set_error(const char* fmt, ...);
 
+// Host-side validation of one frame's parameters (need_filter adds sigma_rw2 and nu); sets the error message.
+spl_status check_params(const spl_params* q, bool need_filter);
+
 // Kernel launchers (estimate.cu / aux.cu). They return cudaSuccess or the launch error.
 cudaError_t launch_estimate(const EstimateArgs& a, bool cost_only, cudaStream_t s);
 cudaError_t launch_state_init(int P, float m, float v, float* mu, float* var, cudaStream_t s);

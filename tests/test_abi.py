@@ -106,3 +106,22 @@ def test_pi_and_init_argument_checks():
     assert lib.spl_pi_propagate(ct.byref(prm), 0x1000, None, 0x1000, None) == _abi.SPL_EINVAL
     assert lib.spl_state_init(ct.byref(prm), None, 0x1000, None) == _abi.SPL_EINVAL
     assert lib.spl_pi_propagate(None, 0x1000, None, 0x2000, None) == _abi.SPL_EINVAL
+
+
+def test_batch_argument_checks():
+    """Batch plans validate every sequence's parameters on the host before touching the device."""
+    lib = _abi.load()
+    good = make_params(4, 4, 64, 25, 12)
+    bad = make_params(4, 4, 64, 25, 12, beta=-1.0)
+    arr = (_abi.spl_params * 2)(good, bad)
+    h = ct.c_void_p()
+    assert lib.spl_batch_create(arr, 2, 1, ct.byref(h)) == _abi.SPL_EINVAL
+    assert "sequence 1" in lib.spl_last_error().decode()
+    assert lib.spl_batch_create(arr, 0, 1, ct.byref(h)) == _abi.SPL_EINVAL
+    assert lib.spl_batch_create(arr, 1, 0, ct.byref(h)) == _abi.SPL_EINVAL
+    assert lib.spl_batch_create(arr, 1, 1, None) == _abi.SPL_EINVAL
+    assert lib.spl_batch_step(None, 0, None) == _abi.SPL_EINVAL
+    assert lib.spl_batch_set(None, 0, None) == _abi.SPL_EINVAL
+    assert lib.spl_batch_tune(None, 0, None) == _abi.SPL_EINVAL
+    assert lib.spl_batch_info(None, None, None, None, None) == _abi.SPL_EINVAL
+    assert lib.spl_batch_status(None, None) == _abi.SPL_EINVAL
