@@ -28,9 +28,9 @@ constexpr int kNnzSparse = 320;  // zero-skip correlation up to this many non-em
 // Shared-memory slice of one warp (all offsets in 4-byte words; every array starts 16-byte aligned).
 struct Slice {
     int nch;     // 16-byte chunks per row
-    int raw;     // the next pixel's row as loaded (cp.async target), nch * 4 words
-    int zs;      // dense counts as float, nch * CB words + 16 zero words (read past the row by the dense sum)
-    int ent;     // non-empty bins (bin, count) as uint2, kNnzSparse entries
+    int rawsz;   // words per staging buffer: nch * 4 + 16 zero words (windows read up to 11 bins past T)
+    int raw;     // two staging buffers (cp.async targets): the current pixel's row and the next one's
+    int ent;     // non-empty bins packed as (bin << 16 | count), kNnzSparse entries
     int cps;     // photon-count prefix over chunks, nch + 1 words
     int cpe;     // non-empty-bin prefix over chunks, nch + 1 words
     int ubs;     // per-block upper bounds, NB words
@@ -44,10 +44,10 @@ __host__ __device__ __forceinline__ Slice make_slice(int T, int D, int cb) {
     Slice s;
     s.nch = (T + cb - 1) / cb;
     const int nb = (D + 31) / 32;
+    s.rawsz = s.nch * 4 + 16;
     s.raw = 0;
-    s.zs = s.nch * 4;
-    s.ent = s.zs + round4(s.nch * cb) + 16;
-    s.cps = s.ent + 2 * kNnzSparse;
+    s.ent = 2 * s.rawsz;
+    s.cps = s.ent + kNnzSparse;
     s.cpe = s.cps + round4(s.nch + 1);
     s.ubs = s.cpe + round4(s.nch + 1);
     s.cs = s.ubs + round4(nb);
@@ -104,6 +104,31 @@ __device__ __forceinline__ void convert_chunk(const float* raw, int i, int T, fl
         for (int k = 0; k < 8; ++k)
             if (i * 8 + k >= T) f[k] = 0.f;
     }
+}
+
+// Count in bin t of the staged row (t < T).
+template <int FMT>
+__device__ __forceinline__ float bin_value(const float* raw, int t) {
+    if (FMT == SPL_HIST_F32) return raw[t];
+    const unsigned short v = reinterpret_cast<const unsigned short*>(raw)[t];
+    if (FMT == SPL_HIST_U16) return __int_as_float(0x4B000000 | v) - 8388608.f;
+    return __half2float(__ushort_as_half(v));
+}
+
+// Counts of bins t .. t+3 of the staged row (t a multiple of 4).
+template <int FMT>
+__device__ __forceinline__ float4 bin4(const float* raw, int t) {
+    if (FMT == SPL_HIST_F32) return reinterpret_cast<const float4*>(raw)[t >> 2];
+    const uint2 v = reinterpret_cast<const uint2*>(raw)[t >> 2];
+    if (FMT == SPL_HIST_U16)
+        return make_float4(__int_as_float(0x4B000000 | (v.x & 0xffffu)) - 8388608.f,
+                           __int_as_float(0x4B000000 | (v.x >> 16)) - 8388608.f,
+                           __int_as_float(0x4B000000 | (v.y & 0xffffu)) - 8388608.f,
+                           __int_as_float(0x4B000000 | (v.y >> 16)) - 8388608.f);
+    return make_float4(__half2float(__ushort_as_half(static_cast<unsigned short>(v.x & 0xffffu))),
+                       __half2float(__ushort_as_half(static_cast<unsigned short>(v.x >> 16))),
+                       __half2float(__ushort_as_half(static_cast<unsigned short>(v.y & 0xffffu))),
+                       __half2float(__ushort_as_half(static_cast<unsigned short>(v.y >> 16))));
 }
 
 // One pixel's prior inputs, one stencil entry per lane (lanes 0-8; lane 0 for a per-pixel Gaussian prior).
@@ -189,19 +214,20 @@ __device__ __forceinline__ void warp_scan2(float* x, int* y, int n, int lane) {
 // candidate c of its run for every non-empty bin t whose taps reach the run (the bins come from the compacted
 // list, the chunk prefix gives the first and last relevant entries). No other lane writes the run, so the
 // accumulation needs no synchronisation.
-__device__ __forceinline__ float corr_runs(const float* __restrict__ gs, const uint2* ent, const int* cpe,
+__device__ __forceinline__ float corr_runs(const float* __restrict__ gs, const unsigned* ent, const int* cpe,
                                            float* cs, int D, int L, int u0, int cb, int lane) {
+    // cs holds 32 * ceil(D / 32) words, exactly the 32 runs of ceil(D / 32) candidates
     const int run = (D + 31) >> 5;
     const int r0 = lane * run, r1 = min(r0 + run, D);
-    for (int c = r0; c < r1; ++c) cs[c] = 0.f;
+    zero_words(cs, run * 8, lane);  // 32 * run candidates, 16-byte stores
     float mx = 0.f;
     if (r0 < r1) {
         const int e_lo = cpe[(u0 + r0) / cb];
         const int e_hi = cpe[(u0 + r1 - 1 + L - 1) / cb + 1];
         for (int e = e_lo; e < e_hi; ++e) {
-            const uint2 en = ent[e];
-            const float zc = __uint_as_float(en.y);
-            const int tc = static_cast<int>(en.x) - u0;  // candidate whose tap 0 falls on this bin
+            const unsigned en = ent[e];
+            const float zc = static_cast<float>(en & 0xffffu);
+            const int tc = static_cast<int>(en >> 16) - u0;  // candidate whose tap 0 falls on this bin
             const int lo = max(tc - L + 1, r0), hi = min(tc, r1 - 1);
             for (int c = lo; c <= hi; ++c) {
                 const float v = fmaf(zc, gs[tc - c], cs[c]);
@@ -215,22 +241,23 @@ __device__ __forceinline__ float corr_runs(const float* __restrict__ gs, const u
 }
 
 // Dense rows: a lane computes 8 consecutive candidates per 256-candidate super-block. Super-blocks start at
-// candidate -(u0 & 3) so every lane's window starts on a 16-byte boundary of zs (candidates < 0 are dropped).
-// Windows may read up to 11 words past the last bin of the row: zs carries 16 zero words there.
-__device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const float* zs, float* cs, int D, int L,
+// candidate -(u0 & 3) so every lane's window starts on a 4-bin boundary (candidates < 0 are dropped). Windows
+// may read up to 11 bins past the row: the staging buffer is zero there (bins T..pitch-1 are zeroed too).
+template <int FMT>
+__device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const float* raw, float* cs, int D, int L,
                                             int u0, int lane) {
     float mx = 0.f;
     for (int cb = -(u0 & 3); cb < D; cb += 256) {
         const int cl = cb + 8 * lane;
         if (cl < D && cl + 7 >= 0) {
-            const float4* z4 = reinterpret_cast<const float4*>(zs + u0 + cl);
+            const int t0 = u0 + cl;
             const float4* g4 = reinterpret_cast<const float4*>(gs);
             float acc[8];
 #pragma unroll
             for (int r = 0; r < 8; ++r) acc[r] = 0.f;
-            float4 c0 = z4[0], c1 = z4[1];
+            float4 c0 = bin4<FMT>(raw, t0), c1 = bin4<FMT>(raw, t0 + 4);
             for (int jg = 0; jg < L; jg += 4) {
-                const float4 nx = z4[jg / 4 + 2];
+                const float4 nx = bin4<FMT>(raw, t0 + jg + 8);
                 const float4 g = g4[jg / 4];
                 const float w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, nx.x, nx.y, nx.z, nx.w};
 #pragma unroll
@@ -255,29 +282,30 @@ __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const 
     return warp_max(mx);
 }
 
-// C(d) for all candidates of one pixel (row in zs, prefix sums in cps/cpe). Returns max C.
-template <int CB>
-__device__ __forceinline__ float correlate(const float* __restrict__ gs, const float* zs, uint2* ent,
-                                           const int* cpe, float* cs, int nch, bool empty, int nnz, int NB, int D,
-                                           int L, int u0, int lane) {
+// C(d) for all candidates of one pixel (staged row in raw, prefix sums in cps/cpe). Returns max C. Zero skip
+// needs every count below 2^16 (packed entries); `sparse_ok` says so.
+template <int FMT, int CB>
+__device__ __forceinline__ float correlate(const float* __restrict__ gs, const float* raw, unsigned* ent,
+                                           const int* cpe, float* cs, int nch, int T, bool empty, bool sparse,
+                                           int NB, int D, int L, int u0, int lane) {
     if (empty) {
         zero_words(cs, NB * 8, lane);
         return 0.f;
     }
-    if (nnz <= kNnzSparse) {
+    if (sparse) {
         for (int i = lane; i < nch; i += 32) {  // compact the non-empty bins, in bin order
             int o = cpe[i];
             if (cpe[i + 1] == o) continue;
+            float f[CB];
+            convert_chunk<FMT>(raw, i, T, f);
 #pragma unroll
-            for (int k = 0; k < CB; ++k) {
-                const float v = zs[i * CB + k];
-                if (v != 0.f) ent[o++] = make_uint2(static_cast<unsigned>(i * CB + k), __float_as_uint(v));
-            }
+            for (int k = 0; k < CB; ++k)
+                if (f[k] != 0.f) ent[o++] = (static_cast<unsigned>(i * CB + k) << 16) | static_cast<unsigned>(f[k]);
         }
         __syncwarp();
         return corr_runs(gs, ent, cpe, cs, D, L, u0, CB, lane);
     }
-    return corr_dense(gs, zs, cs, D, L, u0, lane);
+    return corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -321,9 +349,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     const int T = a.T, L = a.L, D = a.D, u0 = a.dmin - a.peak, NB = (D + 31) >> 5;
     const Slice sl = make_slice(T, D, CB);
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
-    float* raw = base + sl.raw;
-    float* zs = base + sl.zs;
-    uint2* ent = reinterpret_cast<uint2*>(base + sl.ent);
+    unsigned* ent = reinterpret_cast<unsigned*>(base + sl.ent);
     float* cps = base + sl.cps;
     int* cpe = reinterpret_cast<int*>(base + sl.cpe);
     float* ubs = base + sl.ubs;
@@ -331,21 +357,37 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     const long long P = static_cast<long long>(a.H) * a.W;
     const long long stride = static_cast<long long>(gridDim.x) * nwarps;
     constexpr int ESZ = FMT == SPL_HIST_F32 ? 4 : 2;
-    if (lane < 4) reinterpret_cast<float4*>(zs + sl.nch * CB)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < 8) {  // zero padding after each staging buffer (cp.async never writes it)
+        float* pad = base + sl.raw + (lane >> 2) * sl.rawsz + sl.nch * 4;
+        reinterpret_cast<float4*>(pad)[lane & 3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     long long p = static_cast<long long>(blockIdx.x) * nwarps + warp;
-    if (p < P) request_row(a, p, raw, sl.nch, ESZ, lane);
+    if (p < P) request_row(a, p, base + sl.raw, sl.nch, ESZ, lane);
     cp_async_commit();
     Nbr nb_next = request_nbr(a, p, P, lane);
 
-    for (; p < P; p += stride) {
+    for (int buf = 0; p < P; p += stride, buf ^= 1) {
         const Nbr nb = nb_next;
         const bool faulty = !COST_ONLY && __shfl_sync(0xffffffffu, nb.faulty, 0) != 0;
+        float* raw = base + sl.raw + buf * sl.rawsz;
         cp_async_wait_all();
         __syncwarp();
+        {  // stage the next pixel's row into the other buffer and its neighbour states into registers
+            const long long pn = p + stride;
+            if (pn < P) request_row(a, pn, base + sl.raw + (buf ^ 1) * sl.rawsz, sl.nch, ESZ, lane);
+            cp_async_commit();
+            nb_next = request_nbr(a, pn, P, lane);
+        }
+        if (FMT != SPL_HIST_U16) {  // bins T .. pitch-1 are not data: make them zero for the dense windows
+            for (int t = T + lane; t < sl.nch * CB; t += 32) {
+                if (FMT == SPL_HIST_F32) raw[t] = 0.f;
+                else reinterpret_cast<unsigned short*>(raw)[t] = 0;
+            }
+        }
 
-        // ---- 1. staged row -> floats in shared memory, per-chunk photon and non-empty-bin counts ----
-        float K = 0.f;
+        // ---- 1. per-chunk photon and non-empty-bin counts of the staged row ----
+        float K = 0.f, zmax = 0.f;
         int nnz = 0;
         if (!faulty) {
             for (int i = lane; i < sl.nch; i += 32) {
@@ -357,12 +399,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                 for (int k = 0; k < CB; ++k) {
                     s += f[k];
                     c += f[k] != 0.f;
-                }
-                if (CB == 8) {
-                    reinterpret_cast<float4*>(zs)[2 * i] = make_float4(f[0], f[1], f[2], f[3]);
-                    reinterpret_cast<float4*>(zs)[2 * i + 1] = make_float4(f[4 % CB], f[5 % CB], f[6 % CB], f[7 % CB]);
-                } else {
-                    reinterpret_cast<float4*>(zs)[i] = make_float4(f[0], f[1], f[2], f[3]);
+                    zmax = fmaxf(zmax, f[k]);
                 }
                 cps[i] = s;
                 cpe[i] = c;
@@ -371,19 +408,15 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             }
             K = warp_sum(K);
             nnz = static_cast<int>(warp_sum(static_cast<float>(nnz)));
+            zmax = warp_max(zmax);
+            __syncwarp();
+            warp_scan2(cps, cpe, sl.nch, lane);
         }
-        __syncwarp();  // the staged row is consumed: stage the next pixel's inputs behind this pixel's work
-        {
-            const long long pn = p + stride;
-            if (pn < P) request_row(a, pn, raw, sl.nch, ESZ, lane);
-            cp_async_commit();
-            nb_next = request_nbr(a, pn, P, lane);
-        }
-        if (!faulty) warp_scan2(cps, cpe, sl.nch, lane);
         const bool empty = faulty || nnz == 0;
+        const bool sparse = nnz <= kNnzSparse && zmax < 65536.f;
 
         // ---- 2. C(d) for every candidate ----
-        const float cmax = correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane);
+        const float cmax = correlate<FMT, CB>(gs, raw, ent, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane);
 
         if (COST_ONLY) {
             float best = -INFINITY;
@@ -435,8 +468,8 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         float mu, var;
         posterior(
             grid, pr, cmax, empty, cs, ubs, [&](int s_bin, int e_bin) { return cps[e_bin / CB + 1] - cps[s_bin / CB]; },
-            [&]() { correlate<CB>(gs, zs, ent, cpe, cs, sl.nch, empty, nnz, NB, D, L, u0, lane); }, lane, bidx, mu,
-            var);
+            [&]() { correlate<FMT, CB>(gs, raw, ent, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane); }, lane,
+            bidx, mu, var);
         if (lane == 0) {
             a.mu[p] = mu;
             a.var[p] = var;
@@ -458,7 +491,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
 #pragma unroll
                 for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
                     const int j = lane + 32 * q;
-                    zj[q] = j < L ? zs[t0 + j] : 0.f;
+                    zj[q] = j < L ? bin_value<FMT>(raw, t0 + j) : 0.f;
                     aj[q] = j < L ? as[j] : 0.f;
                 }
                 intensity_mle<SPL_MAX_TAPS / 32>(zj, aj, K, L, T, hsum, r, b);

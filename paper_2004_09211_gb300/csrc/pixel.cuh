@@ -34,7 +34,7 @@ namespace px {
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLog2TwoPi = 2.6514961294723187f;  // log2(2 pi)
-constexpr int kMaxComp = 10;                        // 9 stencil entries + 1 merged weakly informative one
+constexpr int kMaxComp = 9;                         // at most 9 distinct components (3x3 stencil)
 constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for dropping a block
 constexpr int kRestart = 16;                        // exact restart interval of the mixture recurrences
 

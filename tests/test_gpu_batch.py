@@ -45,11 +45,12 @@ def _make_frames(specs, N, seed):
     return out
 
 
-def _alloc_state(H, W):
+def _alloc_state(H, W, N):
+    """One state buffer per frame boundary (frame n reads state n, writes state n+1), so every frame's
+    output survives the whole run."""
     P = H * W
-    return dict(mu=[torch.empty(P, device=DEV) for _ in range(2)], var=[torch.empty(P, device=DEV) for _ in range(2)],
-                argmax=torch.empty(P, dtype=torch.int32, device=DEV), refl=torch.empty(P, device=DEV),
-                bg=torch.empty(P, device=DEV))
+    return dict(mu=[torch.empty(P, device=DEV) for _ in range(N + 1)],
+                var=[torch.empty(P, device=DEV) for _ in range(N + 1)])
 
 
 def _run(seqs, N, graph=False, tune=False):
@@ -59,7 +60,7 @@ def _run(seqs, N, graph=False, tune=False):
     plan = spl.spl_batch_create(prms, nslots=N)
     try:
         keep = []
-        states = [_alloc_state(q["H"], q["W"]) for q in seqs]
+        states = [_alloc_state(q["H"], q["W"], N) for q in seqs]
         outs = [[dict() for _ in seqs] for _ in range(N)]
         for n in range(N):
             frames = []
@@ -69,8 +70,8 @@ def _run(seqs, N, graph=False, tune=False):
                 d = dict(h=torch.from_numpy(q["h"]).to(DEV), offsets=torch.from_numpy(off).to(DEV),
                          bins=torch.from_numpy(bins).to(DEV) if bins.size else torch.zeros(1, dtype=torch.int32,
                                                                                            device=DEV),
-                         mu_in=st["mu"][n & 1], var_in=st["var"][n & 1], mu_out=st["mu"][(n + 1) & 1],
-                         var_out=st["var"][(n + 1) & 1])
+                         mu_in=st["mu"][n], var_in=st["var"][n], mu_out=st["mu"][n + 1],
+                         var_out=st["var"][n + 1])
                 # per-frame output buffers so every frame can be checked after the run
                 P = q["H"] * q["W"]
                 for k, dt in (("argmax", torch.int32), ("refl", torch.float32), ("bg", torch.float32)):
