@@ -220,6 +220,49 @@ SPL_API spl_status spl_batch_info(const spl_batch* b, int* tile, int* units, int
  * Synchronous. */
 SPL_API spl_status spl_batch_status(spl_batch* b, uint32_t* flags);
 
+/* ------------------------------------------------------------------------------------------------------------
+ * Allocation-free batched step
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate device memory
+ * themselves through CUDA -- for example a host application whose device memory is entirely handed out by
+ * another framework's pool allocator, or a real-time loop that must never enter cudaMalloc. Such callers
+ * cannot create a spl_batch plan (its tables are allocated), so this entry point takes everything from the
+ * caller's own memory and keeps its working memory in a fixed-size array compiled into the library.
+ * ------------------------------------------------------------------------------------------------------------ */
+
+/* One sequence for spl_batch_step_noalloc: its parameters and this frame's device pointers. */
+typedef struct {
+    spl_params prm;
+    spl_seq_frame f;
+} spl_seq_desc;
+
+/* Most sequences one spl_batch_step_noalloc call accepts (the capacity of its fixed working array). */
+#define SPL_NOALLOC_MAX_SEQ 4096
+
+/*
+ * spl_batch_step_noalloc -- one frame of every sequence, like spl_batch_step, without allocating anything.
+ *   descs_host : host array of nseq descriptors (validated on the host, as spl_batch_create and
+ *                spl_batch_set validate theirs).
+ *   descs_dev  : the same nseq descriptors in device memory the caller owns (for example copied there with
+ *                cudaMemcpy into memory the caller's pool provides).
+ *   tile       : pixels per work unit, 1..4096 (spl_batch_tune's choice of a plan is a good value; 32 is a
+ *                reasonable default). Units are processed in sequence order.
+ *   status     : nullable device uint32; SPL_BATCH_* condition flags are OR-ed into it.
+ * Results equal those of spl_batch_step on the same data.
+ * Working memory: a file-scope device array of (2 + SPL_NOALLOC_MAX_SEQ) 32-bit words (about 16 KB) that every
+ * GPU which loads the library keeps until the process exits; nseq above SPL_NOALLOC_MAX_SEQ is rejected with
+ * SPL_EINVAL. The call allocates no device or pinned memory (no cudaMalloc, no cudaFree, no allocating
+ * library routine): it launches a small set-up kernel that resets the array's work-queue head and writes its
+ * unit table, then the batch kernel, both on `stream`.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it; make that first call before any stream capture on the device.
+ * All calls on a device share the one array, and it keeps the last call's contents: calls whose kernels may
+ * overlap on the GPU (other streams, other host threads) race on it and must be serialised by the caller,
+ * for example by issuing them on one stream.
+ */
+SPL_API spl_status spl_batch_step_noalloc(const spl_seq_desc* descs_host, const spl_seq_desc* descs_dev, int nseq,
+                                          int tile, uint32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

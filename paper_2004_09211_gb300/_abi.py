@@ -35,6 +35,11 @@ class spl_seq_frame(ct.Structure):
                                            "present_now", "mu_out", "var_out", "argmax", "refl", "bg")]
 
 
+class spl_seq_desc(ct.Structure):
+    _fields_ = [("prm", spl_params), ("f", spl_seq_frame)]
+
+
+SPL_NOALLOC_MAX_SEQ = 4096
 SPL_BATCH_BAD_BIN = 1
 SPL_BATCH_TOO_MANY = 2
 SPL_MAX_PHOTONS = 1024
@@ -59,6 +64,7 @@ SIGNATURES = {
     "spl_batch_tune": (ct.c_int, [_vp, ct.c_int, _vp]),
     "spl_batch_info": (ct.c_int, [_vp] + [ct.POINTER(ct.c_int)] * 4),
     "spl_batch_status": (ct.c_int, [_vp, ct.POINTER(ct.c_uint32)]),
+    "spl_batch_step_noalloc": (ct.c_int, [ct.POINTER(spl_seq_desc), _vp, ct.c_int, ct.c_int, _vp, _vp]),
 }
 
 _lock = threading.Lock()
