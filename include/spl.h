@@ -221,6 +221,36 @@ SPL_API spl_status spl_batch_info(const spl_batch* b, int* tile, int* units, int
 SPL_API spl_status spl_batch_status(spl_batch* b, uint32_t* flags);
 
 /* ------------------------------------------------------------------------------------------------------------
+ * Differentiable filter: soft-argmax readout, loss to reference depths, gradients for calibration
+ *
+ * Over nframes frames of one sequence (all pixels present, none faulty) the forward pass runs the filter of
+ * spl_filter_step with every candidate evaluated exactly (no pruning) and, per pixel and frame, the soft-argmax
+ * readout s = sum_d d softmax(ell / tau)(d) (tau = 1 gives the pseudo-posterior mean of Sec. II-C). The loss is
+ * the mean over frames and pixels of (s - d_ref)^2. The backward pass gives d loss / d h (IRF taps), d beta and
+ * d nu (the 3x3 weights of Eq. predict) by a reverse sweep over the frames that recomputes each frame from the
+ * checkpointed states (mu_states, var_states) of the forward pass. Reductions have a fixed order: results are
+ * bitwise reproducible. Histograms: uint16, frame n of nframes at element n * P * pitch of z->data, pitch a
+ * multiple of 8. mu_states, var_states: [(nframes + 1)][P]; row 0 must hold the initial state (spl_state_init);
+ * the forward pass fills rows 1..nframes. scratch: device memory of spl_diff_scratch_size bytes owned by the
+ * caller (about 88 bytes per pixel plus a few hundred KB), used by both passes.
+ * ------------------------------------------------------------------------------------------------------------ */
+
+/* Bytes of scratch that spl_diff_forward / spl_diff_backward need for this frame size on the current device. */
+SPL_API spl_status spl_diff_scratch_size(const spl_params* prm, size_t* bytes);
+
+/* Forward pass. dsoft ([nframes][P], nullable) receives the readouts; loss (one float, nullable) the loss, which
+ * needs d_ref ([nframes][P]). tau > 0. */
+SPL_API spl_status spl_diff_forward(const spl_params* prm, int nframes, const spl_hist* z, const float* h, float tau,
+                                    const float* d_ref, float* mu_states, float* var_states, float* dsoft,
+                                    float* loss, void* scratch, size_t scratch_bytes, void* stream);
+
+/* Backward pass from the forward checkpoints: grad_h [L], grad_beta [1], grad_nu [9] (device). */
+SPL_API spl_status spl_diff_backward(const spl_params* prm, int nframes, const spl_hist* z, const float* h,
+                                     float tau, const float* d_ref, const float* mu_states, const float* var_states,
+                                     float* grad_h, float* grad_beta, float* grad_nu, void* scratch,
+                                     size_t scratch_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------------
  * Allocation-free batched step
  *
  * The paper has no counterpart to this call; it exists for callers that cannot allocate device memory

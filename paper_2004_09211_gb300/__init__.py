@@ -19,7 +19,8 @@ from ._abi import (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY, SPL_HIST_F16, SPL_HIST
 
 __all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate",
            "spl_filter_step", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
-           "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status", "SplError",
+           "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status",
+           "spl_diff_scratch_size", "spl_diff_forward", "spl_diff_backward", "FilterLoss", "SplError",
            "spl_params", "spl_hist", "spl_seq_frame", "load_library", "cross_weights"]
 
 _FMT = {torch.uint16: SPL_HIST_U16, torch.float16: SPL_HIST_F16, torch.float32: SPL_HIST_F32}
@@ -272,3 +273,94 @@ def spl_batch_status(handle) -> int:
     f = ct.c_uint32()
     _abi.check(_abi.load().spl_batch_status(handle, ct.byref(f)))
     return int(f.value)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# differentiable filter
+# ---------------------------------------------------------------------------------------------------------
+
+
+def spl_diff_scratch_size(prm: spl_params) -> int:
+    n = ct.c_size_t()
+    _abi.check(_abi.load().spl_diff_scratch_size(ct.byref(prm), ct.byref(n)))
+    return int(n.value)
+
+
+def _frames_hist(prm: spl_params, z: torch.Tensor, nframes: int) -> spl_hist:
+    if not isinstance(z, torch.Tensor) or z.device.type != "cuda" or z.dtype != torch.uint16 or not z.is_contiguous():
+        raise TypeError("z must be a contiguous CUDA uint16 tensor [nframes, P, pitch]")
+    if z.numel() != nframes * _P(prm) * z.shape[-1]:
+        raise ValueError("z must hold nframes * H * W rows")
+    hz = spl_hist()
+    hz.fmt = SPL_HIST_U16
+    hz.data = z.data_ptr()
+    hz.pitch = z.shape[-1]
+    return hz
+
+
+def spl_diff_forward(prm: spl_params, z: torch.Tensor, h: torch.Tensor, tau: float, d_ref=None, mu_states=None,
+                     var_states=None, scratch=None, stream=None) -> dict:
+    """Forward pass over the frames of z ([nframes, P, pitch] uint16). Returns dict(mu_states, var_states,
+    dsoft, loss, scratch); row 0 of the states is initialised here with spl_state_init when not given."""
+    nframes = z.shape[0]
+    P = _P(prm)
+    if mu_states is None:
+        mu_states = torch.empty(nframes + 1, P, device=z.device)
+        var_states = torch.empty(nframes + 1, P, device=z.device)
+        spl_state_init(prm, mu_states[0], var_states[0], stream=stream)
+    if scratch is None:
+        scratch = torch.empty(spl_diff_scratch_size(prm), dtype=torch.uint8, device=z.device)
+    dsoft = torch.empty(nframes, P, device=z.device)
+    loss = torch.empty(1, device=z.device) if d_ref is not None else None
+    hz = _frames_hist(prm, z, nframes)
+    _abi.check(_abi.load().spl_diff_forward(
+        ct.byref(prm), nframes, ct.byref(hz), _dev(h, "h", torch.float32, prm.L), float(tau),
+        _dev(d_ref, "d_ref", torch.float32, nframes * P), _dev(mu_states, "mu_states", torch.float32),
+        _dev(var_states, "var_states", torch.float32), _dev(dsoft, "dsoft", torch.float32),
+        _dev(loss, "loss", torch.float32, 1), scratch.data_ptr(), scratch.numel(), _stream(stream)))
+    return dict(mu_states=mu_states, var_states=var_states, dsoft=dsoft, loss=loss, scratch=scratch)
+
+
+def spl_diff_backward(prm: spl_params, z: torch.Tensor, h: torch.Tensor, tau: float, d_ref: torch.Tensor,
+                      mu_states: torch.Tensor, var_states: torch.Tensor, scratch=None, stream=None) -> dict:
+    """Gradients of the loss with respect to h, beta and nu. Returns dict(grad_h, grad_beta, grad_nu)."""
+    nframes = z.shape[0]
+    if scratch is None:
+        scratch = torch.empty(spl_diff_scratch_size(prm), dtype=torch.uint8, device=z.device)
+    gh = torch.empty(prm.L, device=z.device)
+    gb = torch.empty(1, device=z.device)
+    gn = torch.empty(9, device=z.device)
+    hz = _frames_hist(prm, z, nframes)
+    _abi.check(_abi.load().spl_diff_backward(
+        ct.byref(prm), nframes, ct.byref(hz), _dev(h, "h", torch.float32, prm.L), float(tau),
+        _dev(d_ref, "d_ref", torch.float32, nframes * _P(prm)), _dev(mu_states, "mu_states", torch.float32),
+        _dev(var_states, "var_states", torch.float32), gh.data_ptr(), gb.data_ptr(), gn.data_ptr(),
+        scratch.data_ptr(), scratch.numel(), _stream(stream)))
+    return dict(grad_h=gh, grad_beta=gb, grad_nu=gn)
+
+
+class FilterLoss(torch.autograd.Function):
+    """Loss of the differentiable filter as a torch autograd function of (h, beta, nu).
+
+    forward(h [L] float32 CUDA, beta 0-d tensor, nu [9] tensor, z [nframes, P, pitch] uint16, d_ref
+    [nframes, P] float32, geometry dict(H, W, T, peak, dmin, dmax, sigma_rw2), tau) -> loss (1-element tensor).
+    Both passes run in the library's kernels (spl_diff_forward / spl_diff_backward); the per-frame states are
+    the checkpoints the backward pass recomputes from."""
+
+    @staticmethod
+    def forward(ctx, h, beta, nu, z, d_ref, geom, tau):
+        prm = make_params(geom["H"], geom["W"], geom["T"], h.numel(), geom["peak"], geom.get("dmin"),
+                          geom.get("dmax"), beta=float(beta), sigma_rw2=geom.get("sigma_rw2", 3.0),
+                          nu=nu.detach().cpu().tolist())
+        hh = h.detach().contiguous().float()
+        out = spl_diff_forward(prm, z, hh, tau, d_ref=d_ref)
+        ctx.save_for_backward(hh, out["mu_states"], out["var_states"])
+        ctx.prm, ctx.z, ctx.d_ref, ctx.tau, ctx.scratch = prm, z, d_ref, tau, out["scratch"]
+        return out["loss"]
+
+    @staticmethod
+    def backward(ctx, gout):
+        hh, ms, vs = ctx.saved_tensors
+        g = spl_diff_backward(ctx.prm, ctx.z, hh, ctx.tau, ctx.d_ref, ms, vs, scratch=ctx.scratch)
+        s = gout.reshape(())
+        return g["grad_h"] * s, (g["grad_beta"] * s).reshape(()), g["grad_nu"] * s, None, None, None, None

@@ -455,3 +455,69 @@ def test_pi_propagation_fixed_points_and_symmetry(orc):
     fa = np.zeros((H, W), np.uint8)
     fa[2, 3] = 1
     assert orc.pi_propagate(nu, pi, faulty=fa)[2, 3] == 0.5
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Differentiable oracle (soft-argmax readout, gradients by autograd)
+# ------------------------------------------------------------------------------------------------------------
+
+
+def _diff_inputs(seed, H=4, W=5, T=90, N=3):
+    h, peak = synth.asymmetric_irf(L=16)
+    rng = _rng(seed)
+    zs, refs = [], []
+    for n in range(N):
+        z = _cube(seed * 10 + n, H, W, T, h, peak)
+        zs.append(z)
+        refs.append(rng.uniform(peak + 10, T - 16 + peak - 10, size=(H, W)))
+    return h, peak, zs, refs
+
+
+def test_diff_oracle_forward_equals_c_oracle(orc):
+    """The autograd oracle is an independent restatement: its filter states equal the C oracle's, and its
+    tau = 1 readout is the posterior mean (the paper's estimator)."""
+    from oracle import diff_oracle as dor
+    h, peak, zs, refs = _diff_inputs(31)
+    nu = NU_ASYM
+    T = zs[0].shape[-1]
+    out = dor.gradients(h, 0.6, nu, zs, refs, peak, sigma_rw2=2.5, tau=1.0)
+    q = orc.params(T, len(h), peak, beta=0.6, sigma_rw2=2.5, nu=nu)
+    mu, var = orc.state_init(q, *zs[0].shape[:2])
+    for n, z in enumerate(zs):
+        e = orc.filter_step(q, h, z, mu, var)
+        m2, v2, ds = out["frames"][n]
+        np.testing.assert_allclose(m2, e["mu"], rtol=1e-11)
+        np.testing.assert_allclose(v2, e["var"], rtol=1e-9)
+        np.testing.assert_allclose(ds, m2, rtol=1e-12)
+        mu, var = e["mu"], e["var"]
+
+
+def test_diff_oracle_gradient_matches_finite_differences():
+    """Central differences of the loss (float64, steps 1e-6 relative) agree with the autograd gradient for
+    every IRF tap, beta and every stencil weight (including weights that are zero)."""
+    from oracle import diff_oracle as dor
+    h, peak, zs, refs = _diff_inputs(32)
+    nu = NU_ASYM
+    beta, tau = 0.45, 0.5
+    g = dor.gradients(h, beta, nu, zs, refs, peak, sigma_rw2=3.0, tau=tau)
+    f = lambda hh, bb, nn: dor.loss_value(hh, bb, nn, zs, refs, peak, sigma_rw2=3.0, tau=tau)
+    hd = h.astype(np.float64)
+    for j in range(len(h)):
+        eps = 1e-6 * max(hd[j], 1e-3)
+        hp, hm = hd.copy(), hd.copy()
+        hp[j] += eps
+        hm[j] -= eps
+        fd = (f(hp, beta, nu) - f(hm, beta, nu)) / (2 * eps)
+        assert fd == pytest.approx(g["grad_h"][j], rel=1e-5, abs=1e-9 * max(1.0, abs(fd)))
+    eps = 1e-7
+    fd = (f(hd, beta + eps, nu) - f(hd, beta - eps, nu)) / (2 * eps)
+    assert fd == pytest.approx(g["grad_beta"], rel=1e-5)
+    for k in range(9):
+        up, dn = nu.copy(), nu.copy()
+        up[k] += 1e-7
+        if nu[k] > 0:   # central difference
+            dn[k] -= 1e-7
+            fd = (f(hd, beta, up) - f(hd, beta, dn)) / 2e-7
+        else:           # a zero weight must stay >= 0: forward difference
+            fd = (f(hd, beta, up) - f(hd, beta, nu)) / 1e-7
+        assert fd == pytest.approx(g["grad_nu"][k], rel=1e-4, abs=1e-8)
