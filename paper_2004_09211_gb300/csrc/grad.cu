@@ -266,12 +266,15 @@ __global__ void __launch_bounds__(256) k_diff_backward(const DiffArgs a, DSlice 
 #pragma unroll
         for (int k = 0; k < 9; ++k) mbar[k] = vbar[k] = 0.f;
         const float i0 = 1.f / f.S0, i0t = 1.f / f.S0t;
+        const float l0 = lg2(f.S0), l0t = lg2(f.S0t);
         for (int c = lane; c < D; c += 32) {
             const float d = static_cast<float>(a.dmin + c);
             const float e = ls[c] - f.M2;
             const float wn = ex2(e) * i0, wt = ex2(e * itau) * i0t;
             const float dm = d - f.mu;
-            const float lb = mub * wn * dm + varb * wn * (dm * dm - f.var) + sb * itau * wt * (d - f.s);
+            const float ca = mub * dm + varb * (dm * dm - f.var);  // coefficient of w
+            const float cb = sb * itau * (d - f.s);                // coefficient of w_tau
+            const float lb = ca * wn + cb * wt;
             const float C = cs[c];
             lbar = fmaf(lb, C, lbar);
             cs[c] = a.lam * lb;  // C_bar, for the tap gradient below
@@ -279,12 +282,19 @@ __global__ void __launch_bounds__(256) k_diff_backward(const DiffArgs a, DSlice 
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
                 const float de = d - em[k];
-                const float r = ex2(ec[k] - ek[k] * de * de - lp2);  // N_k(d) / sum_i nu_i N_i(d)
-                const float t = lb * r;
-                nubar[k] += t;
-                const float tw = t * ew[k];
-                mbar[k] = fmaf(tw, de / ev[k], mbar[k]);
-                vbar[k] = fmaf(tw, (de * de - ev[k]) / (2.f * ev[k] * ev[k]), vbar[k]);
+                const float lnk = ec[k] - ek[k] * de * de;  // log2 N_k(d)
+                if (ew[k] > 0.f) {
+                    // r = N_k / sum_i nu_i N_i <= 1 / nu_k: finite
+                    const float t = lb * ex2(lnk - lp2);
+                    nubar[k] += t;
+                    const float tw = t * ew[k];
+                    mbar[k] = fmaf(tw, de / ev[k], mbar[k]);
+                    vbar[k] = fmaf(tw, (de * de - ev[k]) / (2.f * ev[k] * ev[k]), vbar[k]);
+                } else {
+                    // zero weight: N_k / sum_i nu_i N_i is unbounded, its product with the weights is not; keep
+                    // the ratio inside one exponent
+                    nubar[k] += ca * ex2(e - l0 + lnk - lp2) + cb * ex2(e * itau - l0t + lnk - lp2);
+                }
             }
         }
         __syncwarp();

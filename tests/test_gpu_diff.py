@@ -83,6 +83,6 @@ def test_diff_backward_is_bitwise_reproducible_and_autograd_wired():
         loss = spl.FilterLoss.apply(ht, bt, nt, z, d_ref, geom, 0.5)
         loss.sum().backward()
         grads.append((ht.grad.clone(), bt.grad.clone(), nt.grad.clone(), loss.detach().clone()))
-    for a, b in zip(grads[0], grads[1]):
-        assert torch.equal(a, b)
+    for name, a, b in zip(("grad_h", "grad_beta", "grad_nu", "loss"), grads[0], grads[1]):
+        assert torch.equal(a, b), f"{name}: max |diff| {(a - b).abs().max().item():.3g}, run 1 {a[:4].tolist()}"
     assert torch.isfinite(grads[0][0]).all() and torch.isfinite(grads[0][2]).all()
