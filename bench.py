@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per sequence (default 50)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff"],
+                    help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
+                         "frame; diff: differentiable filter forward + backward")
     return ap.parse_args()
 
 
@@ -379,10 +382,188 @@ def reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------------------------------------
+# secondary workloads (one JSON line each; the default run prints the video line only)
+# ---------------------------------------------------------------------------------------------------------
+
+BATCH_SEQS = 64
+BATCH_FRAMES = 10
+
+
+def batched(args):
+    """64 independent sequences, sides {32..512} (square or 2:1), T in {512..4096}, per-sequence Gaussian
+    (sigma 2-6 bins, taps +-4 sigma) or 48-tap asymmetric IRF and beta in [0.1, 1]; photon lists (0-30 photons
+    per pixel: Poisson(3) signal + Poisson(10) background, truncated); 10 frames per step, captured in one CUDA
+    graph of 10 persistent launches. Also timed: the same sequences stepped one plan (one launch) per sequence."""
+    import paper_2004_09211_gb300 as spl
+    from paper_2004_09211_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    rng = np.random.default_rng(4)
+    gen = torch.Generator(device=dev).manual_seed(4)
+    seqs = []
+    for s in range(BATCH_SEQS):
+        side = int(rng.choice([32, 64, 128, 256, 512]))
+        Hs, Ws = side, side * (2 if rng.random() < 0.5 else 1)
+        T = int(rng.choice([512, 1024, 2048, 4096]))
+        if rng.random() < 0.5:
+            sig = rng.uniform(2.0, 6.0)
+            h, peak = synth.gaussian_irf(sig, int(math.ceil(4 * sig)))
+        else:
+            h, peak = synth.asymmetric_irf(L=48)
+        beta = float(rng.uniform(0.1, 1.0))
+        L = len(h)
+        sc = synth.moving_scene(Hs, Ws, BATCH_FRAMES, peak + 8, T - L + peak - 8, 400 + s)
+        hd = torch.from_numpy(h).to(dev)
+        frames = [synth.toa_lists_torch(torch.from_numpy(sc.depth[n]).to(dev), torch.tensor(3.0, device=dev), 10.0,
+                                        hd, peak, T, gen) for n in range(BATCH_FRAMES)]
+        prm = spl.make_params(Hs, Ws, T, L, peak, beta=beta, sigma_rw2=SIGMA_RW2)
+        P = Hs * Ws
+        st_mu = [torch.empty(P, device=dev) for _ in range(BATCH_FRAMES + 1)]
+        st_var = [torch.empty(P, device=dev) for _ in range(BATCH_FRAMES + 1)]
+        outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                    bg=torch.empty(P, device=dev))
+        seqs.append(dict(prm=prm, h=hd, frames=frames, mu=st_mu, var=st_var, outs=outs, P=P))
+    units = sum(q["P"] for q in seqs) * BATCH_FRAMES
+    photons = sum(int(f[1].numel()) for q in seqs for f in q["frames"])
+
+    def frame_dicts(n):
+        return [dict(h=q["h"], offsets=q["frames"][n][0], bins=q["frames"][n][1], mu_in=q["mu"][n],
+                     var_in=q["var"][n], mu_out=q["mu"][n + 1], var_out=q["var"][n + 1], **q["outs"]) for q in seqs]
+
+    def init_states():
+        for q in seqs:
+            spl.spl_state_init(q["prm"], q["mu"][0], q["var"][0])
+
+    plan = spl.spl_batch_create([q["prm"] for q in seqs], nslots=BATCH_FRAMES)
+    for n in range(BATCH_FRAMES):
+        spl.spl_batch_set(plan, n, frame_dicts(n))
+    init_states()
+    spl.spl_batch_tune(plan, 0)
+    info = spl.spl_batch_info(plan)
+    init_states()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        for n in range(BATCH_FRAMES):
+            spl.spl_batch_step(plan, n, stream=s)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.graph(g):
+        for n in range(BATCH_FRAMES):
+            spl.spl_batch_step(plan, n)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    flags = spl.spl_batch_status(plan)
+    # baseline: one single-sequence plan per sequence, stepped one after the other
+    plans = [spl.spl_batch_create([q["prm"]], nslots=BATCH_FRAMES) for q in seqs]
+    for i, q in enumerate(seqs):
+        for n in range(BATCH_FRAMES):
+            spl.spl_batch_set(plans[i], n, [frame_dicts(n)[i]])
+    for _ in range(2):
+        for n in range(BATCH_FRAMES):
+            for pl in plans:
+                spl.spl_batch_step(pl, n)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for n in range(BATCH_FRAMES):
+        for pl in plans:
+            spl.spl_batch_step(pl, n)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_unbatched = e0.elapsed_time(e1)
+    for pl in plans:
+        spl.spl_batch_destroy(pl)
+    spl.spl_batch_destroy(plan)
+    line = {"metric": "pixel-frames/s", "value": units / (ms / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: 64 photon-list sequences x 10 frames, sides 32-512, T 512-4096",
+                       "pixels": units // BATCH_FRAMES, "frames": BATCH_FRAMES, "photons_per_step": photons,
+                       "tile": info["tile"], "ctas": info["ctas"], "warps_per_cta": info["warps_per_cta"],
+                       "graph": "10 persistent launches captured in one CUDA graph"},
+            "unbatched": {"value": units / (ms_unbatched / 1e3), "ms_per_step": ms_unbatched,
+                          "note": "same sequences, one single-sequence plan per sequence, 640 launches"},
+            "status_flags": flags, "gpu_launches": 2 * BATCH_FRAMES * args.steps, "clocks": clk.summary(),
+            "roofline": None}
+    print(json.dumps(line), flush=True)
+
+
+def diff(args):
+    """Differentiable filter: 128 x 128 pixels x 20 frames, T = 1024, 48-tap asymmetric IRF, soft-argmax readout
+    (tau = 0.5), loss = MSE to the ground-truth depth, gradients for h, beta and the 3x3 weights. One step =
+    forward (states, readouts, loss) + backward (gradients)."""
+    import paper_2004_09211_gb300 as spl
+    from paper_2004_09211_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    Hd = Wd = 128
+    N, Td, Ld = 20, 1024, 48
+    h, peak = synth.asymmetric_irf(L=Ld)
+    sc = synth.moving_scene(Hd, Wd, N, peak + 8, Td - Ld + peak - 8, 5)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    hd = torch.from_numpy(h).to(dev)
+    pitch = synth.pad_pitch(Td)
+    zs = []
+    for n in range(N):
+        mean = synth.expected_counts(torch.from_numpy(sc.depth[n]).to(dev), torch.from_numpy(sc.signal[n]).to(dev),
+                                     float(sc.signal[n].mean()) / (0.1 * Td), hd, peak, Td)
+        zs.append(synth.pitched(synth.poisson_histograms(mean, gen).reshape(-1, Td), pitch))
+    z = torch.stack(zs).contiguous()
+    d_ref = torch.from_numpy(sc.depth.reshape(N, -1).astype(np.float32)).to(dev)
+    prm = spl.make_params(Hd, Wd, Td, Ld, peak, beta=0.5, sigma_rw2=SIGMA_RW2)
+    P = Hd * Wd
+    mu_s = torch.empty(N + 1, P, device=dev)
+    var_s = torch.empty(N + 1, P, device=dev)
+    scratch = torch.empty(spl.spl_diff_scratch_size(prm), dtype=torch.uint8, device=dev)
+
+    def step():
+        spl.spl_state_init(prm, mu_s[0], var_s[0])
+        fw = spl.spl_diff_forward(prm, z, hd, 0.5, d_ref=d_ref, mu_states=mu_s, var_states=var_s, scratch=scratch)
+        bw = spl.spl_diff_backward(prm, z, hd, 0.5, d_ref, mu_s, var_s, scratch=scratch)
+        return fw, bw
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            fw, bw = step()
+        e1.record()
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "pixel-frames/s", "value": P * N / (ms / 1e3), "unit": "pixel-frames/s (forward+backward)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "differentiable 128x128x20 frames, T=1024, L=48, tau=0.5", "pixels": P,
+                       "frames": N},
+            "loss": float(fw["loss"].item()), "grad_beta": float(bw["grad_beta"].item()),
+            "gpu_launches": (1 + N + 1 + 2 * N + 1) * args.steps, "clocks": clk.summary(), "roofline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference(args)
+    elif args.workload == "batched":
+        batched(args)
+    elif args.workload == "diff":
+        diff(args)
     else:
         native(args)
 

@@ -248,3 +248,45 @@ def cross_weights(nu0: float = 0.5) -> np.ndarray:
 SIGMA_RW2 = 3.0  # sigma_RW = sqrt(3) bins
 
 __all__ = [n for n in dir() if not n.startswith("_") and n not in ("dataclasses", "math", "np", "torch")]
+
+
+def toa_lists_torch(depth: torch.Tensor, signal: torch.Tensor, bg_total: float, h: torch.Tensor, peak: int, T: int,
+                    gen: torch.Generator, max_photons: int = 30):
+    """Vectorised photon lists on depth's device: per pixel K_sig ~ Poisson(signal) photons at d - peak + j with
+    j drawn from h, K_bg ~ Poisson(bg_total) uniform photons, at most max_photons kept (a uniformly random
+    subset), sorted by bin. Returns (offsets int32 [P+1], bins int32 [nnz])."""
+    dev = depth.device
+    d = depth.reshape(-1).to(torch.int64)
+    P = d.numel()
+    ks = torch.poisson(signal.reshape(-1).to(torch.float32).expand(P).contiguous(), generator=gen).to(torch.int64)
+    kb = torch.poisson(torch.full((P,), float(bg_total), device=dev), generator=gen).to(torch.int64)
+    k = ks + kb
+    n = int(k.sum())
+    pix = torch.repeat_interleave(torch.arange(P, device=dev), k)
+    start = torch.cumsum(k, 0) - k
+    rank = torch.arange(n, device=dev) - start[pix]
+    is_sig = rank < ks[pix]
+    cdf = torch.cumsum(h.to(torch.float64), 0)
+    cdf = (cdf / cdf[-1]).to(dev)
+    u = torch.rand(n, generator=gen, device=dev, dtype=torch.float64)
+    tap = torch.searchsorted(cdf, u, right=True).clamp(max=h.numel() - 1)
+    sig_bin = d[pix] - peak + tap
+    bg_bin = torch.randint(0, T, (n,), generator=gen, device=dev)
+    bins = torch.where(is_sig, sig_bin, bg_bin)
+    keep = (bins >= 0) & (bins < T)
+    pix, bins = pix[keep], bins[keep]
+    # random subset of at most max_photons per pixel: order by (pixel, random key), keep the first ones
+    key = torch.rand(pix.numel(), generator=gen, device=dev, dtype=torch.float64)
+    order = torch.argsort(pix.to(torch.float64) + key)
+    pix, bins = pix[order], bins[order]
+    cnt = torch.bincount(pix, minlength=P)
+    st = torch.cumsum(cnt, 0) - cnt
+    r = torch.arange(pix.numel(), device=dev) - st[pix]
+    sel = r < max_photons
+    pix, bins = pix[sel], bins[sel]
+    order = torch.argsort(pix * T + bins)
+    bins = bins[order]
+    cnt = torch.bincount(pix, minlength=P)
+    offsets = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    offsets[1:] = torch.cumsum(cnt, 0)
+    return offsets.to(torch.int32), bins.to(torch.int32)
