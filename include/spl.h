@@ -98,6 +98,21 @@ SPL_API spl_status spl_depth_cost(const spl_params* prm, const spl_hist* z, cons
                           int32_t* argmax, void* stream);
 
 /*
+ * spl_depth_cost_tc -- the robust data term of spl_depth_cost on the tensor cores (mixed precision).
+ *   Same outputs as spl_depth_cost (cost [P][D] = C(dmin + k), argmax nullable), from FP16 histograms
+ *   (SPL_HIST_F16; integer counts up to 2048 are exact in FP16). C is computed as a banded-Toeplitz matrix
+ *   product (128 pixels x 64 candidates per tile) with FP16 operands and FP32 accumulation: the powered IRF
+ *   g = h^beta is scaled by 2^15 and split into an FP16 high part and an FP16 low part whose products both
+ *   accumulate, so each tap carries about 22 significant bits (relative cost error ~1e-6 against FP64).
+ *   Requires L <= SPL_MAX_TAPS. A bounded internal wait that runs out sets flag 1 of spl_tc_status.
+ */
+SPL_API spl_status spl_depth_cost_tc(const spl_params* prm, const spl_hist* z, const float* h, float* cost,
+                                     int32_t* argmax, void* stream);
+
+/* Reads and clears the tensor-core kernels' device condition flags (synchronous). */
+SPL_API spl_status spl_tc_status(uint32_t* flags);
+
+/*
  * spl_depth_estimate -- single-frame pseudo-Bayesian depth estimate (Sec. II-C, Eq. approx_post).
  *   log pseudo-posterior ell(d) = lambda C(d) + log f(d), lambda = (beta + 1) / beta (Eq. beta_CE), on the
  *   integer grid dmin..dmax. f(d) = N(d; prior_mu[p], prior_var[p]) when prior_mu != NULL, else uniform

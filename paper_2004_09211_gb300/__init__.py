@@ -20,7 +20,8 @@ from ._abi import (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY, SPL_HIST_F16, SPL_HIST
 __all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate",
            "spl_filter_step", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
            "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status",
-           "spl_diff_scratch_size", "spl_diff_forward", "spl_diff_backward", "FilterLoss", "SplError",
+           "spl_diff_scratch_size", "spl_diff_forward", "spl_diff_backward", "FilterLoss", "spl_depth_cost_tc",
+           "spl_tc_status", "SplError",
            "spl_params", "spl_hist", "spl_seq_frame", "load_library", "cross_weights"]
 
 _FMT = {torch.uint16: SPL_HIST_U16, torch.float16: SPL_HIST_F16, torch.float32: SPL_HIST_F32}
@@ -141,6 +142,28 @@ def spl_depth_cost(prm: spl_params, z: torch.Tensor, h: torch.Tensor, cost: torc
                                   _dev(cost, "cost", torch.float32, P * D), _dev(argmax, "argmax", torch.int32, P),
                                   _stream(stream)))
     return cost, argmax
+
+
+def spl_depth_cost_tc(prm: spl_params, z: torch.Tensor, h: torch.Tensor, cost: torch.Tensor | None = None,
+                      argmax: torch.Tensor | None = None, want_cost: bool = True, stream=None):
+    """C(d) on the tensor cores from FP16 histograms (hi/lo split FP16 operands, FP32 accumulation)."""
+    P, D = _P(prm), _D(prm)
+    if cost is None and want_cost:
+        cost = _empty((P, D), torch.float32, z)
+    if argmax is None:
+        argmax = _empty((P,), torch.int32, z)
+    lib = _abi.load()
+    hz = _hist(prm, z)
+    _abi.check(lib.spl_depth_cost_tc(ct.byref(prm), ct.byref(hz), _dev(h, "h", torch.float32, prm.L),
+                                     _dev(cost, "cost", torch.float32, P * D),
+                                     _dev(argmax, "argmax", torch.int32, P), _stream(stream)))
+    return cost, argmax
+
+
+def spl_tc_status() -> int:
+    f = ct.c_uint32()
+    _abi.check(_abi.load().spl_tc_status(ct.byref(f)))
+    return int(f.value)
 
 
 def spl_depth_estimate(prm: spl_params, z: torch.Tensor, h: torch.Tensor, prior_mu=None, prior_var=None,

@@ -53,6 +53,8 @@ SIGNATURES = {
     "spl_version": (ct.c_char_p, []),
     "spl_last_error": (ct.c_char_p, []),
     "spl_depth_cost": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp]),
+    "spl_depth_cost_tc": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp]),
+    "spl_tc_status": (ct.c_int, [ct.POINTER(ct.c_uint32)]),
     "spl_depth_estimate": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_filter_step": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_state_init": (ct.c_int, [_P, _vp, _vp, _vp]),

@@ -136,6 +136,31 @@ spl_status spl_depth_cost(const spl_params* prm, const spl_hist* z, const float*
     return cuda_status(launch_estimate(a, true, static_cast<cudaStream_t>(stream)), "spl_depth_cost launch");
 }
 
+spl_status spl_depth_cost_tc(const spl_params* prm, const spl_hist* z, const float* h, float* cost,
+                             int32_t* argmax, void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, false);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(z->fmt == SPL_HIST_F16, "spl_depth_cost_tc takes FP16 histograms (SPL_HIST_F16)");
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(cost != nullptr || argmax != nullptr, "both cost and argmax are NULL: nothing to compute");
+    unsigned* status = tc_status_ptr();
+    SPL_REQUIRE(status != nullptr, "no device status word (no CUDA device?)");
+    return cuda_status(launch_cost_tc(prm, z->data, z->pitch, h, cost, argmax, status,
+                                      static_cast<cudaStream_t>(stream)),
+                       "spl_depth_cost_tc launch");
+}
+
+spl_status spl_tc_status(uint32_t* flags) {
+    g_err[0] = 0;
+    SPL_REQUIRE(flags != nullptr, "flags is NULL");
+    unsigned v = 0;
+    spl_status st = cuda_status(tc_status_read(&v), "spl_tc_status");
+    if (st == SPL_OK) *flags = v;
+    return st;
+}
+
 spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, const float* h, const float* prior_mu,
                               const float* prior_var, const uint8_t* present, int32_t* argmax, float* mu,
                               float* var, float* refl, float* bg, void* stream) {

@@ -61,4 +61,10 @@ cudaError_t launch_state_init(int P, float m, float v, float* mu, float* var, cu
 cudaError_t launch_pi_propagate(int H, int W, const float* nu, const float* pi_in, const uint8_t* faulty,
                                 float* pi_out, cudaStream_t s);
 
+// Tensor-core correlation (tc.cu).
+cudaError_t launch_cost_tc(const spl_params* q, const void* z, long long pitch, const float* h, float* cost,
+                           int* argmax, unsigned* status, cudaStream_t s);
+unsigned* tc_status_ptr();
+cudaError_t tc_status_read(unsigned* out);
+
 }  // namespace spl
