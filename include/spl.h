@@ -164,6 +164,21 @@ SPL_API spl_status spl_state_init(const spl_params* prm, float* mu, float* var, 
 SPL_API spl_status spl_pi_propagate(const spl_params* prm, const float* pi_in, const uint8_t* faulty, float* pi_out,
                             void* stream);
 
+/*
+ * spl_filter_step_tc -- spl_filter_step (one outer iteration of Algorithm 1) with the data term on the tensor
+ *   cores, for FP16 histograms (SPL_HIST_F16; integer counts up to 2048 are exact). Same arguments, outputs and
+ *   rules as spl_filter_step. C(d) (Eq. beta_div2) is formed as in spl_depth_cost_tc (FP16 operands, the taps
+ *   h^beta scaled by 2^15 and split into high and low FP16 parts, FP32 accumulation: about 22 significant bits
+ *   per tap) and consumed on chip: no per-candidate value is written to memory. The photon count K of each
+ *   pixel is accumulated by the tensor cores from the same tiles. Candidates whose pseudo-posterior weight is
+ *   provably below 2^-64 of the largest are skipped, as in spl_filter_step. A bounded internal wait that runs
+ *   out sets flag 1 of spl_tc_status (the outputs of that launch are then incomplete).
+ */
+SPL_API spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                                      const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                                      const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
+                                      float* refl, float* bg, void* stream);
+
 /* ------------------------------------------------------------------------------------------------------------
  * Batched filtering of many independent sequences from photon time-of-arrival lists
  *

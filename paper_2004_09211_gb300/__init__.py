@@ -18,7 +18,7 @@ from ._abi import (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY, SPL_HIST_F16, SPL_HIST
                    SPL_MAX_BINS, SPL_MAX_PHOTONS, SPL_MAX_TAPS, SplError, spl_hist, spl_params, spl_seq_frame)
 
 __all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate",
-           "spl_filter_step", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
+           "spl_filter_step", "spl_filter_step_tc", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
            "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status",
            "spl_diff_scratch_size", "spl_diff_forward", "spl_diff_backward", "FilterLoss", "spl_depth_cost_tc",
            "spl_tc_status", "SplError",
@@ -191,7 +191,7 @@ def spl_depth_estimate(prm: spl_params, z: torch.Tensor, h: torch.Tensor, prior_
 
 def spl_filter_step(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor, var_in: torch.Tensor,
                     present_in=None, faulty=None, present_now=None, intensity: bool = True,
-                    out: dict | None = None, stream=None) -> dict:
+                    out: dict | None = None, stream=None, _entry: str = "spl_filter_step") -> dict:
     """One frame of the online filter (Algorithm 1). Returns dict(mu, var, argmax[, refl, bg])."""
     P = _P(prm)
     o = dict(out or {})
@@ -203,7 +203,7 @@ def spl_filter_step(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: to
         o.setdefault("bg", _empty((P,), torch.float32, z))
     lib = _abi.load()
     hz = _hist(prm, z)
-    _abi.check(lib.spl_filter_step(
+    _abi.check(getattr(lib, _entry)(
         ct.byref(prm), ct.byref(hz), _dev(h, "h", torch.float32, prm.L),
         _dev(mu_in, "mu_in", torch.float32, P), _dev(var_in, "var_in", torch.float32, P),
         _dev(present_in, "present_in", torch.uint8, P), _dev(faulty, "faulty", torch.uint8, P),
@@ -213,6 +213,14 @@ def spl_filter_step(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: to
         _dev(o.get("refl"), "refl", torch.float32, P), _dev(o.get("bg"), "bg", torch.float32, P),
         _stream(stream)))
     return o
+
+
+def spl_filter_step_tc(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor, var_in: torch.Tensor,
+                       present_in=None, faulty=None, present_now=None, intensity: bool = True,
+                       out: dict | None = None, stream=None) -> dict:
+    """spl_filter_step with the data term on the tensor cores; z must be FP16 histograms."""
+    return spl_filter_step(prm, z, h, mu_in, var_in, present_in, faulty, present_now, intensity, out, stream,
+                           _entry="spl_filter_step_tc")
 
 
 def spl_state_init(prm: spl_params, mu: torch.Tensor | None = None, var: torch.Tensor | None = None,

@@ -213,6 +213,37 @@ spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float
     return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_filter_step launch");
 }
 
+spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                              const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                              const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
+                              float* refl, float* bg, void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, true);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(z->fmt == SPL_HIST_F16, "spl_filter_step_tc takes FP16 histograms (SPL_HIST_F16)");
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(mu_in && var_in && mu_out && var_out, "mu_in, var_in, mu_out and var_out are required");
+    SPL_REQUIRE(mu_out != mu_in && var_out != var_in && mu_out != var_in && var_out != mu_in,
+                "outputs must not alias the previous-frame state");
+    SPL_REQUIRE((refl == nullptr) == (bg == nullptr), "give both refl and bg or neither");
+    unsigned* status = tc_status_ptr();
+    SPL_REQUIRE(status != nullptr, "no device status word (no CUDA device?)");
+    EstimateArgs a = base_args(prm, z, h);
+    a.prior_mode = PRIOR_STENCIL;
+    a.pmu = mu_in;
+    a.pvar = var_in;
+    a.present_in = present_in;
+    a.faulty = faulty;
+    a.present_now = present_now;
+    a.argmax = argmax;
+    a.mu = mu_out;
+    a.var = var_out;
+    a.refl = refl;
+    a.bg = bg;
+    return cuda_status(launch_filter_tc(a, status, static_cast<cudaStream_t>(stream)), "spl_filter_step_tc launch");
+}
+
 spl_status spl_state_init(const spl_params* prm, float* mu, float* var, void* stream) {
     g_err[0] = 0;
     SPL_REQUIRE(prm != nullptr, "prm is NULL");

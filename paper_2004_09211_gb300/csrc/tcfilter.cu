@@ -1,0 +1,721 @@
+// One frame of the online filter (Algorithm 1) with the data term on the tensor cores: FP16 histograms in, the
+// same outputs as spl_filter_step out, nothing per candidate written to memory.
+//
+// Data term. C(d) = sum_j g_j z[d - peak + j] (Eq. beta_div2) for 128 pixels x 64 candidates per tile, as the
+// banded-Toeplitz product of tc.cu: C[p, 64 t + n] = sum_k Z[p, a0 + 64 t + k] G[k, n] with G[k, n] =
+// g[k - n - delta] * 2^15 split into FP16 high and low parts, accumulated in FP32 in tensor memory.
+// The photon count K of every pixel (Sec. II-E) comes from the same slabs: one extra N = 16 MMA per 64-bin slab
+// against a column of ones, accumulated over all slabs that cover [0, T) (exact in FP32 below 2^24 photons).
+//
+// Pipeline (persistent CTAs, 6 warps each, one or two CTAs per SM):
+//   warp 4  TMA producer: the 64-bin slabs of a 128-pixel block, origin x0 <= 0 so that every bin of [0, T) and
+//           every candidate window is covered, into a ring of R slabs (128-byte swizzled; zero fill outside).
+//   warp 5  MMA issuer: per slab the count MMA; once a tile's last slab has landed, the tile's MMAs into one of
+//           two accumulators; each slab goes back to the producer as soon as no later tile reads it.
+//   warps 0-3 epilogue, thread = pixel = TMEM lane:
+//     prior   Eq. predict from the 3x3 neighbour states, equal Gaussians merged (as the warp kernel does);
+//     tiles   ell(d) = lambda log2(e) C(d) + log2 f(d) in log2 units. A lower bound of max ell is the prior at its
+//             mode (C >= 0). A tile, then each 16-candidate chunk of it, is evaluated only if its upper bound
+//             lambda log2(e) max C + max log2 f reaches the running maximum minus 64: a dropped chunk weighs less
+//             than 2^-64 of the maximum. Evaluated chunks update the argmax (smallest maximiser) and are merged
+//             into running (weight, mean, second central moment) with a shared exponent reference, the chunk's
+//             own moments taken about its best candidate (the pairwise update of Chan, Golub and LeVeque), so
+//             no step subtracts large nearly equal numbers.
+//     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax, and the intensity MLE of Sec. II-E
+//             on the template at round-half-even(mu) with K from the count MMA.
+// All mbarrier waits are bounded (status bit 0 on time-out; the roles then stop, in-flight copies and MMAs are
+// waited for, tensor memory is released).
+#include <math.h>
+#include <stdint.h>
+
+#include "pixel.cuh"
+#include "spl_internal.h"
+#include "tc_common.cuh"
+
+namespace spl {
+namespace {
+
+using namespace tc;
+using px::ex2;
+using px::lg2;
+using px::Prior;
+
+constexpr int kM = 128;                          // pixels per block
+constexpr int kN = 64;                           // candidates per tile
+constexpr int kSlab = 64;                        // bins per slab
+constexpr int kMaxRing = 8;
+constexpr int kThreads = 192;
+constexpr unsigned kTmemCols = 256;              // acc 0 | acc 1 | count 0 | count 1 (64 + 64 + 16 + 16 used)
+constexpr unsigned kCntCol = 128;
+constexpr unsigned kWinCol = 160;                // intensity window staging: up to 4 x 17 columns
+constexpr float kScale = 32768.f;
+constexpr unsigned kSlabBytes = kM * kSlab * 2;  // 16 KB
+constexpr unsigned kBSlabBytes = kN * kSlab * 2; // 8 KB
+constexpr unsigned kOnesBytes = 16 * kSlab * 2;  // 2 KB
+constexpr uint32_t kIdescTile = idesc_f16(kM, kN);
+constexpr uint32_t kIdescCnt = idesc_f16(kM, 16);
+constexpr float kPrune = px::kPrune2;            // log2 margin below the running maximum
+
+struct TcGeom {
+    int a0, delta, kw, ntiles, nslab, mlead, S, npt, ring, nbs;
+    float lam2s;  // lambda log2(e) 2^-15 (the accumulators hold C * 2^15)
+};
+
+// Eq. predict for one pixel, one thread: stencil entry k contributes N(mu_in, var_in + sigma_rw2) when the
+// neighbour is inside the frame, present and not faulty, else the weakly informative Gaussian; entries with
+// nu_k = 0 are unused. Entries with bitwise equal (mean, variance) are merged by adding their weights in stencil
+// order, then the used ones are packed to the front in stencil order.
+__device__ __forceinline__ void prior_thread(const EstimateArgs& a, long long p, Prior& pr, bool& faulty) {
+    const int y = static_cast<int>(p / a.W), x = static_cast<int>(p - static_cast<long long>(y) * a.W);
+    float w[9], m[9], v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int yy = y + k / 3 - 1, xx = x + k % 3 - 1;
+        bool info = false;
+        float mk = 0.f, vk = 0.f;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+            const long long i = static_cast<long long>(yy) * a.W + xx;
+            mk = a.pmu[i];
+            vk = a.pvar[i];
+            const int pres = a.present_in ? a.present_in[i] : 1;
+            const int fl = a.faulty ? a.faulty[i] : 0;
+            info = pres != 0 && fl == 0;
+        }
+        w[k] = a.nu[k];
+        m[k] = info ? mk : a.flat_m;
+        v[k] = (info ? vk : a.flat_v) + a.sigma_rw2;
+    }
+    faulty = a.faulty ? a.faulty[p] != 0 : false;
+    // an entry equal to an earlier used one joins it (the earlier one is then the only used entry with that
+    // Gaussian, so the first match is the representative)
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+#pragma unroll
+        for (int i = 0; i < k; ++i) {
+            const bool same = w[i] > 0.f && w[k] > 0.f && __float_as_uint(m[i]) == __float_as_uint(m[k]) &&
+                              __float_as_uint(v[i]) == __float_as_uint(v[k]);
+            w[i] = same ? w[i] + w[k] : w[i];
+            w[k] = same ? 0.f : w[k];
+        }
+    }
+    // pack the used entries to the front, keeping their order (adjacent exchanges)
+#pragma unroll
+    for (int pass = 0; pass < 8; ++pass) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool sw = !(w[j] > 0.f) && w[j + 1] > 0.f;
+            const float tw = w[j], tm = m[j], tv = v[j];
+            w[j] = sw ? w[j + 1] : w[j];
+            m[j] = sw ? m[j + 1] : m[j];
+            v[j] = sw ? v[j + 1] : v[j];
+            w[j + 1] = sw ? tw : w[j + 1];
+            m[j + 1] = sw ? tm : m[j + 1];
+            v[j + 1] = sw ? tv : v[j + 1];
+        }
+    }
+    pr.n = 0;
+    pr.minv = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const bool act = w[i] > 0.f;
+        pr.n += act ? 1 : 0;
+        const float vi = act ? v[i] : 1.f;
+        pr.ca[i] = act ? lg2(w[i]) - 0.5f * (px::kLog2TwoPi + lg2(vi)) : -INFINITY;
+        pr.ck[i] = px::kLog2e / (2.f * vi);
+        pr.cm[i] = act ? m[i] : 0.f;
+        if (act) pr.minv = fminf(pr.minv, vi);
+    }
+}
+
+// Running pseudo-posterior summary of one pixel. Weights are 2^(ell - ref) with the reference kept as a pair,
+// ref = l2s cref + pref (l2s = lambda log2(e) 2^-15, cref a raw accumulator value, pref a log2 prior value), so
+// every exponent is formed as l2s (c - c') + (p - p'): differences of nearby numbers and one FMA, never the
+// difference of two large log values. The reference is any value that keeps the weights in range (it may lie
+// above the maximum); the pruning threshold uses `top`, a value of ell actually reached (or the lower bound
+// from the prior's mode).
+struct Moments {
+    float cref, pref;
+    float W;      // sum of weights
+    float mu;     // weighted mean, candidate index units
+    float M2;     // sum of w (d - mu)^2
+    float top;    // max(lower bound, largest ell evaluated), absolute log2 units
+    float best;   // largest ell evaluated
+    int bidx;     // its candidate index (smallest on ties)
+};
+
+// Merges one chunk's sums (s0 = sum u, s1 = sum u x, s2 = sum u x^2 with x = candidate - ctr, weights u
+// relative to the chunk reference (cr, pr_)) into the running summary: the pairwise update of Chan, Golub and
+// LeVeque after bringing both to the larger reference.
+__device__ __forceinline__ void merge(Moments& s, float l2s, float cr, float pr_, float s0, float s1, float s2,
+                                      float ctr) {
+    const float r0 = 1.f / s0;
+    const float cmu = ctr + s1 * r0;
+    float cm2 = fmaxf(fmaf(-s1 * r0, s1, s2), 0.f);
+    if (!(s.W > 0.f)) {
+        s.cref = cr;
+        s.pref = pr_;
+        s.W = s0;
+        s.mu = cmu;
+        s.M2 = cm2;
+        return;
+    }
+    const float diff = fmaf(l2s, cr - s.cref, pr_ - s.pref);  // chunk reference - running reference (bits)
+    if (diff > 0.f) {
+        const float sc = ex2(-diff);
+        s.W *= sc;
+        s.M2 *= sc;
+        s.cref = cr;
+        s.pref = pr_;
+    } else {
+        const float sc = ex2(diff);
+        s0 *= sc;
+        cm2 *= sc;
+    }
+    const float Wn = s.W + s0;
+    const float dl = cmu - s.mu;
+    const float f = s0 / Wn;
+    s.mu = fmaf(dl, f, s.mu);
+    s.M2 += cm2 + dl * dl * s.W * f;
+    s.W = Wn;
+}
+
+// Exact log-domain chunk: raw accumulators c[0..15] of candidates c0 .. c0 + 15 (those >= D excluded).
+__device__ __forceinline__ void chunk_log(const float* c, int c0, int D, int dmin, float l2s, const Prior& pr,
+                                          Moments& s) {
+    float lp[16], l[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const bool in = c0 + i < D;
+        lp[i] = in ? px::log2_prior(pr, static_cast<float>(dmin + c0 + i)) : -INFINITY;
+        l[i] = in ? fmaf(l2s, c[i], lp[i]) : -INFINITY;
+    }
+    float lm = l[0];
+#pragma unroll
+    for (int i = 1; i < 16; ++i) lm = fmaxf(lm, l[i]);
+    int ib = 0;
+    float cb = c[0], pb = lp[0];
+#pragma unroll
+    for (int i = 15; i >= 0; --i) {
+        const bool hit = l[i] == lm;
+        ib = hit ? i : ib;
+        cb = hit ? c[i] : cb;
+        pb = hit ? lp[i] : pb;
+    }
+    if (lm > s.best) {
+        s.best = lm;
+        s.bidx = c0 + ib;
+    }
+    s.top = fmaxf(s.top, lm);
+    if (!(lm >= s.top - kPrune)) return;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float w = ex2(fmaf(l2s, c[i] - cb, lp[i] - pb));
+        const float x = static_cast<float>(i - ib);
+        s0 += w;
+        s1 = fmaf(w, x, s1);
+        s2 = fmaf(w * x, x, s2);
+    }
+    merge(s, l2s, cb, pb, s0, s1, s2, static_cast<float>(c0 + ib));
+}
+
+// Linear-domain chunk. The weight of candidate i relative to the chunk's bound (cq = max c, lpb = the prior's
+// bound on the chunk) is 2^(l2s (c_i - cq)) * sum_k 2^(ca_k - ck_k (d_i - m_k)^2 - lpb): one exp2 for the data
+// factor and, per mixture component, the exact two-multiply recurrence of a Gaussian on a unit grid (value
+// ratio, then ratio of ratios) started from exact exponentials at the chunk's first candidate. No value
+// exceeds n; a component that underflows on the chunk is below 2^-126 of the bound. Returns false (nothing
+// merged, nothing updated) when the chunk's largest weight is below 2^-60 of its bound, which the exact
+// log-domain chunk then handles; requires component variances >= 1.5 bins^2, so that 15 steps from the start
+// cannot take a component from below the float range up to its peak.
+__device__ __forceinline__ bool chunk_lin(const float* c, int c0, int D, int dmin, float l2s, const Prior& pr,
+                                         float cq, float lpb, Moments& s) {
+    float v[px::kMaxComp], q[px::kMaxComp], rho[px::kMaxComp];
+    const float d0 = static_cast<float>(dmin + c0);
+#pragma unroll
+    for (int k = 0; k < px::kMaxComp; ++k) {
+        if (k < pr.n) {
+            const float e = d0 - pr.cm[k];
+            v[k] = ex2(pr.ca[k] - pr.ck[k] * e * e - lpb);
+            q[k] = ex2(fminf(-pr.ck[k] * (2.f * e + 1.f), 100.f));
+            rho[k] = ex2(-2.f * pr.ck[k]);
+        } else {
+            v[k] = q[k] = rho[k] = 0.f;
+        }
+    }
+    float u[16];
+    float um = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        float pv = 0.f;
+#pragma unroll
+        for (int k = 0; k < px::kMaxComp; ++k) {
+            if (k < pr.n) {
+                pv += v[k];
+                v[k] *= q[k];
+                q[k] *= rho[k];
+            }
+        }
+        u[i] = c0 + i < D ? ex2(l2s * (c[i] - cq)) * pv : 0.f;
+        um = fmaxf(um, u[i]);
+    }
+    if (!(um >= 0x1p-60f)) return false;
+    int ib = 0;
+#pragma unroll
+    for (int i = 15; i >= 0; --i) ib = u[i] == um ? i : ib;
+    const float lm = fmaf(l2s, cq, lpb) + lg2(um);
+    if (lm > s.best) {
+        s.best = lm;
+        s.bidx = c0 + ib;
+    }
+    s.top = fmaxf(s.top, lm);
+    if (!(lm >= s.top - kPrune)) return true;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float x = static_cast<float>(i - ib);
+        s0 += u[i];
+        s1 = fmaf(u[i], x, s1);
+        s2 = fmaf(u[i] * x, x, s2);
+    }
+    merge(s, l2s, cq, lpb, s0, s1, s2, static_cast<float>(c0 + ib));
+    return true;
+}
+
+__device__ __forceinline__ float half_at(uint4 w, int h) {
+    const unsigned word = h < 2 ? w.x : h < 4 ? w.y : h < 6 ? w.z : w.w;
+    return __half2float(__ushort_as_half(static_cast<unsigned short>((h & 1) ? word >> 16 : word)));
+}
+
+// Intensity MLE of Sec. II-E for one pixel per thread (the per-warp version is px::intensity_mle). The window
+// bins t0 .. t0 + L - 1 of this lane's pixel are staged in its tensor-memory lane as packed FP16 (LCH 16-byte
+// groups starting at bin t0 - sh, columns win .. win + 4 LCH - 1); the normalised template is in shared memory.
+// Warp-collective: every lane runs the loops (the tensor-memory loads are warp-wide); lanes with need == false
+// only take part. psi(f) = sum_W z (a - u) / (u + f (a - u)) - Kout / (1 - f), u = 1/T, is decreasing on
+// [0, 1): safeguarded Newton on psi with the bracket [lo, hi] kept around its root; r = f K / sum(h),
+// b = (1 - f) K / T.
+template <int LCH>
+__device__ __forceinline__ void intensity_lanes(uint32_t win, int sh, bool need, float K, int L, int T, float hsum,
+                                                const float* s_a, float& r, float& b) {
+    const float u = 1.f / static_cast<float>(T);
+    float kin = 0.f, za = 0.f, p1 = 0.f;
+    bool zero_tap = false;
+#pragma unroll 1
+    for (int grp = 0; grp < LCH; ++grp) {
+        const uint4 w = tmem_ld4(win + 4 * grp);
+        tmem_wait_ld();
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const float z = half_at(w, h);
+            const int j = 8 * grp + h - sh;
+            if (static_cast<unsigned>(j) < static_cast<unsigned>(L)) {
+                const float aj = s_a[j];
+                kin += z;
+                za = fmaf(z, aj, za);
+                if (z > 0.f) {
+                    if (aj > 0.f) p1 += z * __fdividef(aj - u, aj);
+                    else zero_tap = true;
+                }
+            }
+        }
+    }
+    const float kout = fmaxf(K - kin, 0.f);
+    const float psi0 = static_cast<float>(T) * za - K;
+    float f = 0.f, lo = 0.f, hi = 1.f;
+    bool active = false;
+    if (!(psi0 > 0.f)) {
+        f = 0.f;
+    } else if (!(kout > 0.f) && !zero_tap && p1 >= 0.f) {
+        f = 1.f;
+    } else {
+        const float fr = static_cast<float>(L) * u;
+        f = fr < 1.f ? (kin - K * fr) / (K * (1.f - fr)) : 0.5f;
+        f = fminf(fmaxf(f, 0.02f), 0.98f);
+        active = need;
+    }
+    for (int it = 0; it < 64; ++it) {
+        if (!__any_sync(0xffffffffu, active)) break;
+        float gs = 0.f, gp = 0.f;
+#pragma unroll 1
+        for (int grp = 0; grp < LCH; ++grp) {
+            const uint4 w = tmem_ld4(win + 4 * grp);
+            tmem_wait_ld();
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const float z = half_at(w, h);
+                const int j = 8 * grp + h - sh;
+                if (static_cast<unsigned>(j) < static_cast<unsigned>(L) && z > 0.f) {
+                    const float aj = s_a[j];
+                    const float e = __fdividef(aj - u, fmaf(f, aj - u, u));
+                    gs = fmaf(z, e, gs);
+                    gp = fmaf(z * e, e, gp);
+                }
+            }
+        }
+        if (active) {
+            const float rom = __fdividef(1.f, 1.f - f);
+            gs = fmaf(-kout, rom, gs);
+            gp = fmaf(kout * rom, rom, gp);
+            if (gs > 0.f) lo = f; else hi = f;
+            float fn = f + __fdividef(gs, gp);
+            if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
+            const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
+            f = fn;
+            if (conv) active = false;
+        }
+    }
+    r = f * K / hsum;
+    b = (1.f - f) * K * u;
+}
+
+template <int LCH>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_filter_tc(const __grid_constant__ CUtensorMap zmap, const EstimateArgs a, const TcGeom g, unsigned* status) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar[2 * kMaxRing + 9];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ float s_g[SPL_MAX_TAPS];
+    __shared__ float s_a[SPL_MAX_TAPS];
+    __shared__ float s_hsum;
+
+    const unsigned base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - smem_u32(smem_raw));
+    const unsigned ring = static_cast<unsigned>(g.ring);
+    const unsigned ringA = base;
+    const unsigned Bhi = base + ring * kSlabBytes;
+    const unsigned Blo = Bhi + g.nbs * kBSlabBytes;
+    const unsigned Bone = Blo + g.nbs * kBSlabBytes;
+    const unsigned full0 = smem_u32(&bar[0]), empty0 = smem_u32(&bar[kMaxRing]);
+    const unsigned accf0 = smem_u32(&bar[2 * kMaxRing]), acce0 = smem_u32(&bar[2 * kMaxRing + 2]);
+    const unsigned cntf0 = smem_u32(&bar[2 * kMaxRing + 4]), cnte0 = smem_u32(&bar[2 * kMaxRing + 6]);
+    const unsigned drain = smem_u32(&bar[2 * kMaxRing + 8]);
+    volatile int* stop = &abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // ---- set-up ----
+    if (warp == 5) tmem_alloc(smem_u32(&tmem_base), kTmemCols);
+    for (int j = tid; j < SPL_MAX_TAPS; j += kThreads) {
+        const float hj = j < a.L ? a.h[j] : 0.f;
+        s_g[j] = hj > 0.f ? powf(hj, a.beta) : 0.f;
+        s_a[j] = hj > 0.f ? hj : 0.f;
+    }
+    if (tid == 0) {
+        for (unsigned i = 0; i < ring; ++i) {
+            mbar_init(full0 + 8 * i, 1);
+            mbar_init(empty0 + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(accf0 + 8 * i, 1);
+            mbar_init(acce0 + 8 * i, 4);
+            mbar_init(cntf0 + 8 * i, 1);
+            mbar_init(cnte0 + 8 * i, 4);
+        }
+        mbar_init(drain, 1);
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (warp == 0) {  // normalised template for the intensity step
+        float sum = 0.f;
+        for (int j = lane; j < a.L; j += 32) sum += s_a[j];
+        sum = px::warp_sum(sum);
+        if (lane == 0) s_hsum = sum;
+        if (sum > 0.f)
+            for (int j = lane; j < a.L; j += 32) s_a[j] /= sum;
+    }
+    for (int e = tid; e < g.nbs * kSlab * kN; e += kThreads) {  // Toeplitz operand, high and low parts
+        const int k = e / kN, n = e - k * kN;
+        const int j = k - n - g.delta;
+        const float gv = (k < g.kw && j >= 0 && j < a.L) ? s_g[j] * kScale : 0.f;
+        const __half hi = __float2half_rn(gv);
+        const __half lo = __float2half_rn(gv - __half2float(hi));
+        const unsigned off = (k / kSlab) * kBSlabBytes + swz_offset(n, k % kSlab);
+        *reinterpret_cast<__half*>(gbase + (Bhi - base) + off) = hi;
+        *reinterpret_cast<__half*>(gbase + (Blo - base) + off) = lo;
+    }
+    for (int e = tid; e < 16 * kSlab; e += kThreads)  // ones operand of the count MMA
+        *reinterpret_cast<__half*>(gbase + (Bone - base) + swz_offset(e / kSlab, e % kSlab)) = __float2half_rn(1.f);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 4) {
+        // ================= TMA producer =================
+        if (lane == 0) {
+            const int x0 = g.a0 - kSlab * g.mlead;
+            unsigned cnt = 0, slot = 0, phase = 0;
+            bool ok = true;
+            for (int pt = blockIdx.x; pt < g.npt && ok && !*stop; pt += gridDim.x) {
+                for (int s = 0; s < g.S; ++s) {
+                    if (cnt >= ring && !(ok = wait_bounded(empty0 + 8 * slot, phase ^ 1u, stop, status))) break;
+                    mbar_expect_tx(full0 + 8 * slot, kSlabBytes);
+                    tma_load_2d(ringA + slot * kSlabBytes, &zmap, x0 + kSlab * s, pt * kM, full0 + 8 * slot);
+                    ++cnt;
+                    if (++slot == ring) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            for (unsigned i = cnt > ring ? cnt - ring : 0; i < cnt; ++i) wait_quiet(full0 + 8 * (i % ring), (i / ring) & 1u);
+        }
+    } else if (warp == 5) {
+        // ================= MMA issuer =================
+        if (lane == 0) {
+            unsigned gs = 0, rel = 0, tcount = 0, blk = 0;
+            bool ok = true;
+            for (int pt = blockIdx.x; pt < g.npt && ok; pt += gridDim.x, ++blk) {
+                const unsigned base_s = gs;
+                const uint32_t dcnt = tmem + kCntCol + 16u * (blk & 1u);
+                if (blk >= 2 && !(ok = wait_bounded(cnte0 + 8 * (blk & 1u), ((blk >> 1) - 1) & 1u, stop, status)))
+                    break;
+                fence_after();
+                for (int s = 0; s < g.S; ++s, ++gs) {
+                    if (!(ok = wait_bounded(full0 + 8 * (gs % ring), (gs / ring) & 1u, stop, status))) break;
+                    fence_after();
+                    const unsigned aslab = ringA + (gs % ring) * kSlabBytes;
+#pragma unroll
+                    for (int kk = 0; kk < kSlab; kk += 16)
+                        mma_f16<kIdescCnt>(dcnt, desc_sw128(aslab + 2 * kk), desc_sw128(Bone + 2 * kk),
+                                           (s > 0 || kk > 0) ? 1u : 0u);
+                    const int t = s - g.mlead - g.nslab + 1;
+                    if (t >= 0 && t < g.ntiles) {
+                        const unsigned acc = tcount & 1u, use = tcount >> 1;
+                        if (use > 0 && !(ok = wait_bounded(acce0 + 8 * acc, (use - 1) & 1u, stop, status))) break;
+                        fence_after();
+                        const uint32_t d = tmem + acc * kN;
+                        for (int j = 0; j < g.nslab; ++j) {
+                            const unsigned sj = base_s + g.mlead + t + j;
+                            const unsigned sl = ringA + (sj % ring) * kSlabBytes;
+                            const int k_end = min(kSlab * (j + 1), g.kw);
+                            for (int k = kSlab * j; k < k_end; k += 16) {
+                                const unsigned koff = (k - kSlab * j) * 2;
+                                const uint64_t ad = desc_sw128(sl + koff);
+                                mma_f16<kIdescTile>(d, ad, desc_sw128(Bhi + j * kBSlabBytes + koff), k > 0 ? 1u : 0u);
+                                mma_f16<kIdescTile>(d, ad, desc_sw128(Blo + j * kBSlabBytes + koff), 1u);
+                            }
+                        }
+                        mma_commit(accf0 + 8 * acc);
+                        ++tcount;
+                    }
+                    // slabs that no later tile of the block reads go back to the producer
+                    const int tn = max(0, s - g.mlead - g.nslab + 2);
+                    const unsigned need = tn < g.ntiles ? base_s + g.mlead + tn : gs + 1;
+                    const unsigned lim = min(need, gs + 1);
+                    for (; rel < lim; ++rel) mma_commit(empty0 + 8 * (rel % ring));
+                }
+                if (!ok) break;
+                mma_commit(cntf0 + 8 * (blk & 1u));
+            }
+            mma_commit(drain);
+            wait_quiet(drain, 0);
+        }
+    } else {
+        // ================= epilogue: thread = pixel = TMEM lane =================
+        const long long P = static_cast<long long>(a.H) * a.W;
+        const int D = a.D, T = a.T, L = a.L, dmin = a.dmin;
+        const float hsum = s_hsum;
+        const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+        unsigned tcount = 0, blk = 0;
+        bool ok = true;
+        for (int pt = blockIdx.x; pt < g.npt && ok; pt += gridDim.x, ++blk) {
+            const long long p = static_cast<long long>(pt) * kM + tid;
+            const bool valid = p < P;
+            Prior pr;
+            bool faulty = false;
+            if (valid) {
+                prior_thread(a, p, pr, faulty);
+            } else {
+                pr.n = 0;
+                pr.minv = 1.f;
+#pragma unroll
+                for (int i = 0; i < px::kMaxComp; ++i) pr.ca[i] = pr.ck[i] = pr.cm[i] = 0.f;
+            }
+            const float l2s = faulty ? 0.f : g.lam2s;
+            Moments st;
+            {  // lower bound of max ell: the prior at the mode of its tallest component (C >= 0)
+                float top = -INFINITY, tm = 0.f;
+#pragma unroll
+                for (int i = 0; i < px::kMaxComp; ++i)
+                    if (i < pr.n && pr.ca[i] > top) {
+                        top = pr.ca[i];
+                        tm = pr.cm[i];
+                    }
+                const float d0 = fminf(fmaxf(rintf(tm), static_cast<float>(dmin)), static_cast<float>(dmin + D - 1));
+                st.top = px::log2_prior(pr, d0);
+            }
+            st.cref = st.pref = 0.f;
+            st.W = st.mu = st.M2 = 0.f;
+            st.best = -INFINITY;
+            st.bidx = 0;
+            const bool lin_ok = !(pr.minv < 1.5f);
+            for (int t = 0; t < g.ntiles; ++t, ++tcount) {
+                const unsigned acc = tcount & 1u, use = tcount >> 1;
+                ok = __all_sync(0xffffffffu, wait_bounded(accf0 + 8 * acc, use & 1u, stop, status));
+                if (!ok) break;
+                fence_after();
+                // tile bound from the largest accumulator, then chunk by chunk, re-read from tensor memory (the
+                // loads are warp-collective: every lane issues them, the decisions are per lane)
+                const uint32_t tacc = lane_base + acc * kN;
+                const int c0t = kN * t;
+                const int nval = min(kN, D - c0t);
+                float cm = 0.f;
+#pragma unroll
+                for (int q = 0; q < kN / 16; ++q) {
+                    float c[16];
+                    tmem_ld16(tacc + 16 * q, c);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) cm = fmaxf(cm, c[i]);
+                }
+                const bool alive =
+                    valid && fmaf(l2s, cm,
+                                  px::log2_prior_bound(pr, static_cast<float>(dmin + c0t),
+                                                       static_cast<float>(dmin + c0t + nval - 1))) >=
+                                 st.top - kPrune;
+                if (__any_sync(0xffffffffu, alive)) {
+#pragma unroll 1
+                    for (int q = 0; q < kN / 16 && c0t + 16 * q < D; ++q) {
+                        const int cq0 = c0t + 16 * q;
+                        float c[16];
+                        tmem_ld16(tacc + 16 * q, c);
+                        tmem_wait_ld();
+                        if (alive) {
+                            float cq = c[0];
+#pragma unroll
+                            for (int i = 1; i < 16; ++i) cq = fmaxf(cq, c[i]);
+                            const float lpb = px::log2_prior_bound(pr, static_cast<float>(dmin + cq0),
+                                                                   static_cast<float>(dmin + min(cq0 + 15, D - 1)));
+                            if (fmaf(l2s, cq, lpb) >= st.top - kPrune) {
+                                if (!(lin_ok && chunk_lin(c, cq0, D, dmin, l2s, pr, cq, lpb, st)))
+                                    chunk_log(c, cq0, D, dmin, l2s, pr, st);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8 * acc);
+            }
+            if (!ok) break;
+            // photon count of the block's pixels
+            ok = __all_sync(0xffffffffu,
+                            wait_bounded(cntf0 + 8 * (blk & 1u), (blk >> 1) & 1u, stop, status));
+            if (!ok) break;
+            fence_after();
+            const float K = tmem_ld1(lane_base + kCntCol + 16u * (blk & 1u));
+            tmem_wait_ld();
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(cnte0 + 8 * (blk & 1u));
+            // outputs (stores by valid lanes; the intensity step is warp-collective)
+            const float mu = static_cast<float>(dmin) + st.mu;
+            if (valid) {
+                a.mu[p] = mu;
+                a.var[p] = st.M2 / st.W;
+                if (a.argmax) a.argmax[p] = dmin + st.bidx;
+            }
+            if (a.refl) {
+                const bool present = valid && (a.present_now ? a.present_now[p] != 0 : true);
+                const bool need = valid && !faulty && present && K > 0.f && hsum > 0.f;
+                float r = 0.f, b = 0.f;
+                if (__any_sync(0xffffffffu, need)) {
+                    int t0 = 0;
+                    if (need) {
+                        const int rm = __float2int_rn(fminf(fmaxf(mu, 0.f), static_cast<float>(T)));
+                        t0 = min(max(rm - a.peak, 0), T - L);  // template at round-half-even(mu)
+                    }
+                    const int t0a = t0 & ~7;
+                    const uint4* row = reinterpret_cast<const uint4*>(static_cast<const __half*>(a.z) +
+                                                                      (valid ? p : 0) * a.pitch + t0a);
+                    const uint32_t win = lane_base + kWinCol;
+#pragma unroll 1
+                    for (int ch = 0; ch < LCH; ++ch) {
+                        const uint4 v = need && t0a + 8 * ch < T ? __ldg(row + ch) : make_uint4(0u, 0u, 0u, 0u);
+                        tmem_st4(win + 4 * ch, v);
+                    }
+                    tmem_wait_st();
+                    intensity_lanes<LCH>(win, t0 - t0a, need, K, L, T, hsum, s_a, r, b);
+                }
+                if (valid) {
+                    if (faulty) {
+                        r = b = 0.f;
+                    } else if (!need) {
+                        r = 0.f;
+                        b = K / static_cast<float>(T);
+                    }
+                    a.refl[p] = r;
+                    a.bg[p] = b;
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream_t s) {
+    TcGeom g;
+    const long long P = static_cast<long long>(a.H) * a.W;
+    const int u0 = a.dmin - a.peak;  // >= 0 (checked on the host)
+    g.a0 = u0 & ~7;
+    g.delta = u0 - g.a0;
+    g.kw = ((kN + a.L - 1 + g.delta) + 15) & ~15;
+    g.ntiles = (a.D + kN - 1) / kN;
+    g.nslab = (g.kw + kSlab - 1) / kSlab;
+    g.nbs = g.nslab;
+    g.mlead = (g.a0 + kSlab - 1) / kSlab;
+    const int x0 = g.a0 - kSlab * g.mlead;
+    g.S = max(g.mlead + g.ntiles + g.nslab - 1, (a.T - x0 + kSlab - 1) / kSlab);
+    g.npt = static_cast<int>((P + kM - 1) / kM);
+    g.lam2s = a.lam2 / kScale;
+
+    int dev = 0, nsm = 0, smem_sm = 0, smem_blk = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const size_t fixed = 1024 + 2 * static_cast<size_t>(g.nbs) * kBSlabBytes + kOnesBytes;
+    const size_t static_bytes = 4096;  // barriers, template tables and the per-CTA reservation, rounded up
+    // two CTAs per SM when a ring of at least nslab + 2 slabs still fits, else one CTA with a deeper ring
+    long long r2 = (static_cast<long long>(smem_sm) / 2 - static_cast<long long>(static_bytes) -
+                    static_cast<long long>(fixed)) / kSlabBytes;
+    int ring;
+    if (r2 >= g.nslab + 2) {
+        ring = static_cast<int>(r2 < kMaxRing ? r2 : kMaxRing);
+    } else {
+        long long r1 = (static_cast<long long>(smem_blk) - static_cast<long long>(static_bytes) -
+                        static_cast<long long>(fixed)) / kSlabBytes;
+        ring = static_cast<int>(r1 < kMaxRing ? r1 : kMaxRing);
+    }
+    if (ring < g.nslab) return cudaErrorInvalidConfiguration;
+    g.ring = ring;
+    const size_t smem = fixed + static_cast<size_t>(ring) * kSlabBytes;
+
+    CUtensorMap map;
+    if ((e = hist_map(&map, a.z, a.pitch, a.T, P)) != cudaSuccess) return e;
+    auto kern = a.L <= 64 ? k_filter_tc<9> : k_filter_tc<17>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
+        cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    per_sm = per_sm > 2 ? 2 : per_sm;  // tensor memory: 256 columns per CTA, 512 per SM
+    const long long want = static_cast<long long>(nsm) * per_sm;
+    const int grid = static_cast<int>(g.npt < want ? g.npt : want);
+    kern<<<grid, kThreads, smem, s>>>(map, a, g, status);
+    return cudaGetLastError();
+}
+
+}  // namespace spl

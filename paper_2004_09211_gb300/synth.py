@@ -171,6 +171,30 @@ def poisson_histograms(mean: torch.Tensor, gen: torch.Generator, dtype=torch.uin
     return z.to(dtype)
 
 
+def frame_histograms(depth: torch.Tensor, signal: torch.Tensor, bg_per_bin: float, h: torch.Tensor, peak: int,
+                     T: int, gen: torch.Generator, pitch: int, dtype=torch.float16, chunk: int = 1 << 15,
+                     max_count: int = 2048) -> torch.Tensor:
+    """Poisson histograms of one frame straight into a zero-padded [P, pitch] buffer on depth's device, a chunk
+    of pixels at a time (for frames too large for expected_counts): per bin Poisson(bg_per_bin) plus, at bins
+    d - peak + j, Poisson(signal * h_j) (the same law as poisson_histograms(expected_counts(...)): a sum of
+    independent Poisson counts). Counts above max_count are clipped."""
+    dev = depth.device
+    d = depth.reshape(-1).to(torch.int64)
+    r = signal.reshape(-1).to(device=dev, dtype=torch.float32)
+    hh = h.to(device=dev, dtype=torch.float32)
+    L = hh.numel()
+    P = d.numel()
+    out = torch.zeros(P, pitch, dtype=dtype, device=dev)
+    jj = torch.arange(L, device=dev)
+    for p0 in range(0, P, chunk):
+        p1 = min(P, p0 + chunk)
+        z = torch.poisson(torch.full((p1 - p0, T), float(bg_per_bin), device=dev), generator=gen)
+        sig = torch.poisson(r[p0:p1, None] * hh[None, :], generator=gen)
+        z.scatter_add_(1, d[p0:p1, None] - peak + jj[None, :], sig)
+        out[p0:p1, :T] = z.clamp_(max=max_count).to(dtype)
+    return out
+
+
 def pad_pitch(T: int, elem_bytes: int = 2, align: int = 16) -> int:
     """Row pitch (elements) rounding T up so each pixel's row starts on a 16-byte boundary."""
     per = align // elem_bytes

@@ -138,8 +138,10 @@ def test_estimate_gaussian_prior_and_presence(orc):
 # ------------------------------------------------------------------------------------------------------------
 
 
-def _run_filter(orc, q, prm, h, zs, T, present=None, faulty=None, present_now=None, dtype=torch.uint16):
+def _run_filter(orc, q, prm, h, zs, T, present=None, faulty=None, present_now=None, dtype=torch.uint16,
+                step=None, tie_rel=None):
     """Runs the GPU chain and the oracle chain independently and compares every frame."""
+    step = step or spl.spl_filter_step
     H, W = prm.H, prm.W
     hd = torch.from_numpy(h).to(DEV)
     mu_g, var_g = spl.spl_state_init(prm)
@@ -147,8 +149,8 @@ def _run_filter(orc, q, prm, h, zs, T, present=None, faulty=None, present_now=No
     dp = lambda a: None if a is None else torch.from_numpy(a).to(DEV).reshape(-1)
     ties = 0
     for n, z in enumerate(zs):
-        o = spl.spl_filter_step(prm, _gpu_hist(z, T, dtype), hd, mu_g, var_g, present_in=dp(present),
-                                faulty=dp(faulty), present_now=dp(present_now))
+        o = step(prm, _gpu_hist(z, T, dtype), hd, mu_g, var_g, present_in=dp(present), faulty=dp(faulty),
+                 present_now=dp(present_now))
         e = orc.filter_step(q, h, z, mu_o, var_o, present_in=present, faulty=faulty, want_ell=True)
         torch.cuda.synchronize()
         ties += check_argmax(_np(o["argmax"]), e["argmax"], e["ell"], q.dmin, f"argmax frame {n}")
