@@ -127,6 +127,41 @@ __device__ __forceinline__ void prior_thread(const EstimateArgs& a, long long p,
     }
 }
 
+// log2 of the prior density at d (up to a constant) over the first NC component slots; slots past the pixel's
+// own count have ca = -inf and contribute nothing. NC is the largest component count in the warp, so the loops
+// have fixed trip counts instead of per-lane predication over all 9 slots.
+template <int NC>
+__device__ __forceinline__ float lp_n(const Prior& pr, float d) {
+    if (NC == 1) {
+        const float e = d - pr.cm[0];
+        return pr.ca[0] - pr.ck[0] * e * e;
+    }
+    float t[NC];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const float e = d - pr.cm[k];
+        t[k] = pr.ca[k] - pr.ck[k] * e * e;
+        mx = fmaxf(mx, t[k]);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) sum += ex2(t[k] - mx);
+    return mx + lg2(sum);
+}
+
+// Upper bound of lp_n over depths [lo, hi] (the largest component's maximum there, plus log2 of the count).
+template <int NC>
+__device__ __forceinline__ float lpb_n(const Prior& pr, float lo, float hi) {
+    float mx = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const float e = fmaxf(fmaxf(lo - pr.cm[k], pr.cm[k] - hi), 0.f);
+        mx = fmaxf(mx, pr.ca[k] - pr.ck[k] * e * e);
+    }
+    return NC > 1 && pr.n > 1 ? mx + lg2(static_cast<float>(pr.n)) + 1e-3f : mx + 1e-3f;
+}
+
 // Running pseudo-posterior summary of one pixel. Weights are 2^(ell - ref) with the reference kept as a pair,
 // ref = l2s cref + pref (l2s = lambda log2(e) 2^-15, cref a raw accumulator value, pref a log2 prior value), so
 // every exponent is formed as l2s (c - c') + (p - p'): differences of nearby numbers and one FMA, never the
@@ -180,13 +215,14 @@ __device__ __forceinline__ void merge(Moments& s, float l2s, float cr, float pr_
 }
 
 // Exact log-domain chunk: raw accumulators c[0..15] of candidates c0 .. c0 + 15 (those >= D excluded).
+template <int NC>
 __device__ __forceinline__ void chunk_log(const float* c, int c0, int D, int dmin, float l2s, const Prior& pr,
                                           Moments& s) {
     float lp[16], l[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const bool in = c0 + i < D;
-        lp[i] = in ? px::log2_prior(pr, static_cast<float>(dmin + c0 + i)) : -INFINITY;
+        lp[i] = in ? lp_n<NC>(pr, static_cast<float>(dmin + c0 + i)) : -INFINITY;
         l[i] = in ? fmaf(l2s, c[i], lp[i]) : -INFINITY;
     }
     float lm = l[0];
@@ -227,20 +263,17 @@ __device__ __forceinline__ void chunk_log(const float* c, int c0, int D, int dmi
 // merged, nothing updated) when the chunk's largest weight is below 2^-60 of its bound, which the exact
 // log-domain chunk then handles; requires component variances >= 1.5 bins^2, so that 15 steps from the start
 // cannot take a component from below the float range up to its peak.
+template <int NC>
 __device__ __forceinline__ bool chunk_lin(const float* c, int c0, int D, int dmin, float l2s, const Prior& pr,
                                          float cq, float lpb, Moments& s) {
-    float v[px::kMaxComp], q[px::kMaxComp], rho[px::kMaxComp];
+    float v[NC], q[NC], rho[NC];
     const float d0 = static_cast<float>(dmin + c0);
 #pragma unroll
-    for (int k = 0; k < px::kMaxComp; ++k) {
-        if (k < pr.n) {
-            const float e = d0 - pr.cm[k];
-            v[k] = ex2(pr.ca[k] - pr.ck[k] * e * e - lpb);
-            q[k] = ex2(fminf(-pr.ck[k] * (2.f * e + 1.f), 100.f));
-            rho[k] = ex2(-2.f * pr.ck[k]);
-        } else {
-            v[k] = q[k] = rho[k] = 0.f;
-        }
+    for (int k = 0; k < NC; ++k) {
+        const float e = d0 - pr.cm[k];
+        v[k] = ex2(pr.ca[k] - pr.ck[k] * e * e - lpb);
+        q[k] = ex2(fminf(-pr.ck[k] * (2.f * e + 1.f), 100.f));
+        rho[k] = ex2(-2.f * pr.ck[k]);
     }
     float u[16];
     float um = 0.f;
@@ -248,12 +281,10 @@ __device__ __forceinline__ bool chunk_lin(const float* c, int c0, int D, int dmi
     for (int i = 0; i < 16; ++i) {
         float pv = 0.f;
 #pragma unroll
-        for (int k = 0; k < px::kMaxComp; ++k) {
-            if (k < pr.n) {
-                pv += v[k];
-                v[k] *= q[k];
-                q[k] *= rho[k];
-            }
+        for (int k = 0; k < NC; ++k) {
+            pv += v[k];
+            v[k] *= q[k];
+            q[k] *= rho[k];
         }
         u[i] = c0 + i < D ? ex2(l2s * (c[i] - cq)) * pv : 0.f;
         um = fmaxf(um, u[i]);
@@ -365,6 +396,47 @@ __device__ __forceinline__ void intensity_lanes(uint32_t win, int sh, bool need,
     }
     r = f * K / hsum;
     b = (1.f - f) * K * u;
+}
+
+// One candidate tile of one pixel (this lane): the bound of the whole tile from its largest accumulator, then
+// chunk by chunk. The tensor-memory loads are warp-collective: every lane issues them; the decisions are per
+// lane.
+template <int NC>
+__device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmin, float l2s, const Prior& pr,
+                                          bool valid, bool lin_ok, Moments& st) {
+    const int nval = min(kN, D - c0t);
+    float cm = 0.f;
+#pragma unroll
+    for (int q = 0; q < kN / 16; ++q) {
+        float c[16];
+        tmem_ld16(tacc + 16 * q, c);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) cm = fmaxf(cm, c[i]);
+    }
+    const bool alive = valid && fmaf(l2s, cm,
+                                     lpb_n<NC>(pr, static_cast<float>(dmin + c0t),
+                                               static_cast<float>(dmin + c0t + nval - 1))) >= st.top - kPrune;
+    if (!__any_sync(0xffffffffu, alive)) return;
+#pragma unroll 1
+    for (int q = 0; q < kN / 16 && c0t + 16 * q < D; ++q) {
+        const int cq0 = c0t + 16 * q;
+        float c[16];
+        tmem_ld16(tacc + 16 * q, c);
+        tmem_wait_ld();
+        if (alive) {
+            float cq = c[0];
+#pragma unroll
+            for (int i = 1; i < 16; ++i) cq = fmaxf(cq, c[i]);
+            const float lpb = lpb_n<NC>(pr, static_cast<float>(dmin + cq0),
+                                        static_cast<float>(dmin + min(cq0 + 15, D - 1)));
+            if (fmaf(l2s, cq, lpb) >= st.top - kPrune) {
+                if (!(lin_ok && chunk_lin<NC>(c, cq0, D, dmin, l2s, pr, cq, lpb, st)))
+                    chunk_log<NC>(c, cq0, D, dmin, l2s, pr, st);
+            }
+        }
+        __syncwarp();
+    }
 }
 
 template <int LCH>
@@ -527,12 +599,17 @@ __global__ void __launch_bounds__(kThreads, 2)
             bool faulty = false;
             if (valid) {
                 prior_thread(a, p, pr, faulty);
-            } else {
-                pr.n = 0;
+            } else {  // padding lane: one flat component, results discarded
+                pr.n = 1;
                 pr.minv = 1.f;
 #pragma unroll
-                for (int i = 0; i < px::kMaxComp; ++i) pr.ca[i] = pr.ck[i] = pr.cm[i] = 0.f;
+                for (int i = 0; i < px::kMaxComp; ++i) {
+                    pr.ca[i] = i == 0 ? 0.f : -INFINITY;
+                    pr.ck[i] = 0.f;
+                    pr.cm[i] = 0.f;
+                }
             }
+            const int nw = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(pr.n)));
             const float l2s = faulty ? 0.f : g.lam2s;
             Moments st;
             {  // lower bound of max ell: the prior at the mode of its tallest component (C >= 0)
@@ -556,45 +633,15 @@ __global__ void __launch_bounds__(kThreads, 2)
                 ok = __all_sync(0xffffffffu, wait_bounded(accf0 + 8 * acc, use & 1u, stop, status));
                 if (!ok) break;
                 fence_after();
-                // tile bound from the largest accumulator, then chunk by chunk, re-read from tensor memory (the
-                // loads are warp-collective: every lane issues them, the decisions are per lane)
                 const uint32_t tacc = lane_base + acc * kN;
                 const int c0t = kN * t;
-                const int nval = min(kN, D - c0t);
-                float cm = 0.f;
-#pragma unroll
-                for (int q = 0; q < kN / 16; ++q) {
-                    float c[16];
-                    tmem_ld16(tacc + 16 * q, c);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) cm = fmaxf(cm, c[i]);
-                }
-                const bool alive =
-                    valid && fmaf(l2s, cm,
-                                  px::log2_prior_bound(pr, static_cast<float>(dmin + c0t),
-                                                       static_cast<float>(dmin + c0t + nval - 1))) >=
-                                 st.top - kPrune;
-                if (__any_sync(0xffffffffu, alive)) {
-#pragma unroll 1
-                    for (int q = 0; q < kN / 16 && c0t + 16 * q < D; ++q) {
-                        const int cq0 = c0t + 16 * q;
-                        float c[16];
-                        tmem_ld16(tacc + 16 * q, c);
-                        tmem_wait_ld();
-                        if (alive) {
-                            float cq = c[0];
-#pragma unroll
-                            for (int i = 1; i < 16; ++i) cq = fmaxf(cq, c[i]);
-                            const float lpb = px::log2_prior_bound(pr, static_cast<float>(dmin + cq0),
-                                                                   static_cast<float>(dmin + min(cq0 + 15, D - 1)));
-                            if (fmaf(l2s, cq, lpb) >= st.top - kPrune) {
-                                if (!(lin_ok && chunk_lin(c, cq0, D, dmin, l2s, pr, cq, lpb, st)))
-                                    chunk_log(c, cq0, D, dmin, l2s, pr, st);
-                            }
-                        }
-                        __syncwarp();
-                    }
+                switch (nw) {  // warp-uniform
+                    case 1: tile_work<1>(tacc, c0t, D, dmin, l2s, pr, valid, lin_ok, st); break;
+                    case 2: tile_work<2>(tacc, c0t, D, dmin, l2s, pr, valid, lin_ok, st); break;
+                    case 3: tile_work<3>(tacc, c0t, D, dmin, l2s, pr, valid, lin_ok, st); break;
+                    case 4:
+                    case 5: tile_work<5>(tacc, c0t, D, dmin, l2s, pr, valid, lin_ok, st); break;
+                    default: tile_work<9>(tacc, c0t, D, dmin, l2s, pr, valid, lin_ok, st); break;
                 }
                 fence_before();
                 __syncwarp();
@@ -690,13 +737,15 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
     // two CTAs per SM when a ring of at least nslab + 2 slabs still fits, else one CTA with a deeper ring
     long long r2 = (static_cast<long long>(smem_sm) / 2 - static_cast<long long>(static_bytes) -
                     static_cast<long long>(fixed)) / kSlabBytes;
-    int ring;
+    int ring, per_sm;
     if (r2 >= g.nslab + 2) {
         ring = static_cast<int>(r2 < kMaxRing ? r2 : kMaxRing);
+        per_sm = 2;
     } else {
         long long r1 = (static_cast<long long>(smem_blk) - static_cast<long long>(static_bytes) -
                         static_cast<long long>(fixed)) / kSlabBytes;
         ring = static_cast<int>(r1 < kMaxRing ? r1 : kMaxRing);
+        per_sm = 1;
     }
     if (ring < g.nslab) return cudaErrorInvalidConfiguration;
     g.ring = ring;
@@ -708,10 +757,13 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
         cudaSuccess)
         return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    per_sm = per_sm > 2 ? 2 : per_sm;  // tensor memory: 256 columns per CTA, 512 per SM
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+        return e;
+    // two CTAs per SM when shared memory allows it (256 tensor-memory columns each; the registers of two
+    // 192-thread CTAs fit by the launch bounds); the occupancy query confirms at least one fits
+    int fits = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, kern, kThreads, smem)) != cudaSuccess) return e;
+    if (fits < 1) return cudaErrorInvalidConfiguration;
     const long long want = static_cast<long long>(nsm) * per_sm;
     const int grid = static_cast<int>(g.npt < want ? g.npt : want);
     kern<<<grid, kThreads, smem, s>>>(map, a, g, status);
