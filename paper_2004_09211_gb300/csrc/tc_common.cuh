@@ -168,15 +168,15 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 inline EncodeTiled encode_fn() {
-    static EncodeTiled fn = nullptr;
-    if (!fn) {
+    static const EncodeTiled fn = []() -> EncodeTiled {  // initialised once, thread-safe
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    }
+            return reinterpret_cast<EncodeTiled>(p);
+        return nullptr;
+    }();
     return fn;
 }
 

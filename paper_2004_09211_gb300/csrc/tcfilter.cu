@@ -28,6 +28,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "pixel.cuh"
 #include "spl_internal.h"
 #include "tc_common.cuh"
@@ -214,6 +216,37 @@ __device__ __forceinline__ void merge(Moments& s, float l2s, float cr, float pr_
     s.W = Wn;
 }
 
+// As merge, for a chunk whose weight s0, mean cmu (candidate index) and second central moment cm2 are known.
+__device__ __forceinline__ void merge_centred(Moments& s, float l2s, float cr, float pr_, float s0, float cmu,
+                                              float cm2) {
+    if (!(s.W > 0.f)) {
+        s.cref = cr;
+        s.pref = pr_;
+        s.W = s0;
+        s.mu = cmu;
+        s.M2 = cm2;
+        return;
+    }
+    const float diff = fmaf(l2s, cr - s.cref, pr_ - s.pref);  // chunk reference - running reference (bits)
+    if (diff > 0.f) {
+        const float sc = ex2(-diff);
+        s.W *= sc;
+        s.M2 *= sc;
+        s.cref = cr;
+        s.pref = pr_;
+    } else {
+        const float sc = ex2(diff);
+        s0 *= sc;
+        cm2 *= sc;
+    }
+    const float Wn = s.W + s0;
+    const float dl = cmu - s.mu;
+    const float f = s0 / Wn;
+    s.mu = fmaf(dl, f, s.mu);
+    s.M2 += cm2 + dl * dl * s.W * f;
+    s.W = Wn;
+}
+
 // Exact log-domain chunk: raw accumulators c[0..15] of candidates c0 .. c0 + 15 (those >= D excluded).
 template <int NC>
 __device__ __forceinline__ void chunk_log(const float* c, int c0, int D, int dmin, float l2s, const Prior& pr,
@@ -255,28 +288,32 @@ __device__ __forceinline__ void chunk_log(const float* c, int c0, int D, int dmi
     merge(s, l2s, cb, pb, s0, s1, s2, static_cast<float>(c0 + ib));
 }
 
-// Linear-domain chunk. The weight of candidate i relative to the chunk's bound (cq = max c, lpb = the prior's
-// bound on the chunk) is 2^(l2s (c_i - cq)) * sum_k 2^(ca_k - ck_k (d_i - m_k)^2 - lpb): one exp2 for the data
-// factor and, per mixture component, the exact two-multiply recurrence of a Gaussian on a unit grid (value
-// ratio, then ratio of ratios) started from exact exponentials at the chunk's first candidate. No value
-// exceeds n; a component that underflows on the chunk is below 2^-126 of the bound. Returns false (nothing
-// merged, nothing updated) when the chunk's largest weight is below 2^-60 of its bound, which the exact
-// log-domain chunk then handles; requires component variances >= 1.5 bins^2, so that 15 steps from the start
-// cannot take a component from below the float range up to its peak.
-template <int NC>
+// Linear-domain chunk. The weight of candidate i relative to the reference (cq = the chunk's largest
+// accumulator, pref = an upper bound of the prior on the chunk) is 2^(l2s (c_i - cq)) *
+// sum_k 2^(ca_k - ck_k (d_i - m_k)^2 - pref): one exp2 for the data factor and, per mixture component, the exact
+// two-multiply recurrence of a Gaussian on a unit grid (value ratio, then ratio of ratios) started from exact
+// exponentials at the chunk's first candidate. No value exceeds n; a component that underflows on the chunk is
+// below 2^-126 of the reference. Returns false (nothing merged, nothing updated) when the chunk's largest
+// weight is below 2^-60 of the reference; the caller then bounds the chunk exactly and, if it can matter, runs
+// the exact log-domain chunk. Requires component variances >= 1.5 bins^2, so that 15 steps from the start cannot
+// take a component from below the float range up to its peak. FULL: all 16 candidates are < D.
+// The chunk's moments are formed in two passes (sum u and sum u i, then sum u (i - mean)^2), so the chunk
+// variance is not a difference of large numbers and a mean at the chunk's first candidate keeps its relative
+// precision.
+template <int NC, bool FULL>
 __device__ __forceinline__ bool chunk_lin(const float* c, int c0, int D, int dmin, float l2s, const Prior& pr,
-                                         float cq, float lpb, Moments& s) {
+                                         float cq, float pref, Moments& s) {
     float v[NC], q[NC], rho[NC];
     const float d0 = static_cast<float>(dmin + c0);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
         const float e = d0 - pr.cm[k];
-        v[k] = ex2(pr.ca[k] - pr.ck[k] * e * e - lpb);
+        v[k] = ex2(pr.ca[k] - pr.ck[k] * e * e - pref);
         q[k] = ex2(fminf(-pr.ck[k] * (2.f * e + 1.f), 100.f));
         rho[k] = ex2(-2.f * pr.ck[k]);
     }
     float u[16];
-    float um = 0.f;
+    float um = 0.f, s0 = 0.f, s1 = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         float pv = 0.f;
@@ -286,29 +323,31 @@ __device__ __forceinline__ bool chunk_lin(const float* c, int c0, int D, int dmi
             v[k] *= q[k];
             q[k] *= rho[k];
         }
-        u[i] = c0 + i < D ? ex2(l2s * (c[i] - cq)) * pv : 0.f;
+        u[i] = ex2(l2s * (c[i] - cq)) * pv;
+        if (!FULL) u[i] = c0 + i < D ? u[i] : 0.f;
         um = fmaxf(um, u[i]);
+        s0 += u[i];
+        s1 = fmaf(u[i], static_cast<float>(i), s1);
     }
     if (!(um >= 0x1p-60f)) return false;
-    int ib = 0;
+    const float lm = fmaf(l2s, cq, pref) + lg2(um);
+    if (lm > s.best) {  // new best: its (smallest) index in the chunk
+        int ib = 0;
 #pragma unroll
-    for (int i = 15; i >= 0; --i) ib = u[i] == um ? i : ib;
-    const float lm = fmaf(l2s, cq, lpb) + lg2(um);
-    if (lm > s.best) {
+        for (int i = 15; i >= 0; --i) ib = u[i] == um ? i : ib;
         s.best = lm;
         s.bidx = c0 + ib;
     }
     s.top = fmaxf(s.top, lm);
     if (!(lm >= s.top - kPrune)) return true;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const float m1 = s1 / s0;
+    float s2 = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const float x = static_cast<float>(i - ib);
-        s0 += u[i];
-        s1 = fmaf(u[i], x, s1);
+        const float x = static_cast<float>(i) - m1;
         s2 = fmaf(u[i] * x, x, s2);
     }
-    merge(s, l2s, cq, lpb, s0, s1, s2, static_cast<float>(c0 + ib));
+    merge_centred(s, l2s, cq, pref, s0, static_cast<float>(c0) + m1, s2);
     return true;
 }
 
@@ -398,25 +437,28 @@ __device__ __forceinline__ void intensity_lanes(uint32_t win, int sh, bool need,
     b = (1.f - f) * K * u;
 }
 
-// One candidate tile of one pixel (this lane): the bound of the whole tile from its largest accumulator, then
-// chunk by chunk. The tensor-memory loads are warp-collective: every lane issues them; the decisions are per
-// lane.
+// One candidate tile of one pixel (this lane). A tile whose prior bound alone reaches the pruning threshold is
+// kept without looking at the data (C >= 0); otherwise its largest accumulator decides. Kept tiles are evaluated
+// chunk by chunk with the tile's prior bound as the reference. The tensor-memory loads are warp-collective:
+// every lane issues them; the decisions are per lane.
 template <int NC>
 __device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmin, float l2s, const Prior& pr,
                                           bool valid, bool lin_ok, Moments& st) {
     const int nval = min(kN, D - c0t);
-    float cm = 0.f;
+    const float lpt = lpb_n<NC>(pr, static_cast<float>(dmin + c0t), static_cast<float>(dmin + c0t + nval - 1));
+    bool alive = valid && lpt >= st.top - kPrune;
+    if (__any_sync(0xffffffffu, valid && !alive)) {
+        float cm = 0.f;
 #pragma unroll
-    for (int q = 0; q < kN / 16; ++q) {
-        float c[16];
-        tmem_ld16(tacc + 16 * q, c);
-        tmem_wait_ld();
+        for (int q = 0; q < kN / 16; ++q) {
+            float c[16];
+            tmem_ld16(tacc + 16 * q, c);
+            tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) cm = fmaxf(cm, c[i]);
+            for (int i = 0; i < 16; ++i) cm = fmaxf(cm, c[i]);
+        }
+        alive = valid && fmaf(l2s, cm, lpt) >= st.top - kPrune;
     }
-    const bool alive = valid && fmaf(l2s, cm,
-                                     lpb_n<NC>(pr, static_cast<float>(dmin + c0t),
-                                               static_cast<float>(dmin + c0t + nval - 1))) >= st.top - kPrune;
     if (!__any_sync(0xffffffffu, alive)) return;
 #pragma unroll 1
     for (int q = 0; q < kN / 16 && c0t + 16 * q < D; ++q) {
@@ -428,11 +470,16 @@ __device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmi
             float cq = c[0];
 #pragma unroll
             for (int i = 1; i < 16; ++i) cq = fmaxf(cq, c[i]);
-            const float lpb = lpb_n<NC>(pr, static_cast<float>(dmin + cq0),
-                                        static_cast<float>(dmin + min(cq0 + 15, D - 1)));
-            if (fmaf(l2s, cq, lpb) >= st.top - kPrune) {
-                if (!(lin_ok && chunk_lin<NC>(c, cq0, D, dmin, l2s, pr, cq, lpb, st)))
-                    chunk_log<NC>(c, cq0, D, dmin, l2s, pr, st);
+            if (fmaf(l2s, cq, lpt) >= st.top - kPrune) {
+                bool done = false;
+                if (lin_ok)
+                    done = cq0 + 16 <= D ? chunk_lin<NC, true>(c, cq0, D, dmin, l2s, pr, cq, lpt, st)
+                                         : chunk_lin<NC, false>(c, cq0, D, dmin, l2s, pr, cq, lpt, st);
+                if (!done) {
+                    const float lpq = lpb_n<NC>(pr, static_cast<float>(dmin + cq0),
+                                                static_cast<float>(dmin + min(cq0 + 15, D - 1)));
+                    if (fmaf(l2s, cq, lpq) >= st.top - kPrune) chunk_log<NC>(c, cq0, D, dmin, l2s, pr, st);
+                }
             }
         }
         __syncwarp();
@@ -710,6 +757,53 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 }  // namespace
 
+namespace {
+
+struct DevInfo {
+    int nsm, smem_sm, smem_blk;
+};
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+DevInfo g_info[kMaxDevices];
+bool g_have_info[kMaxDevices];
+size_t g_smem_set[kMaxDevices][2];  // dynamic shared memory last configured per kernel variant (0 = never)
+
+cudaError_t device_info(int dev, DevInfo& out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (dev >= 0 && dev < kMaxDevices && g_have_info[dev]) {
+        out = g_info[dev];
+        return cudaSuccess;
+    }
+    DevInfo d;
+    cudaError_t e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices) {
+        g_info[dev] = d;
+        g_have_info[dev] = true;
+    }
+    out = d;
+    return cudaSuccess;
+}
+
+// Sets the kernel's shared-memory attributes when the configuration changes and checks that one CTA fits.
+cudaError_t prepare_kernel(int dev, int variant, const void* kern, size_t smem) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (dev >= 0 && dev < kMaxDevices && g_smem_set[dev][variant] == smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int fits = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (fits < 1) return cudaErrorInvalidConfiguration;
+    if (dev >= 0 && dev < kMaxDevices) g_smem_set[dev][variant] = smem;
+    return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream_t s) {
     TcGeom g;
     const long long P = static_cast<long long>(a.H) * a.W;
@@ -726,12 +820,12 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
     g.npt = static_cast<int>((P + kM - 1) / kM);
     g.lam2s = a.lam2 / kScale;
 
-    int dev = 0, nsm = 0, smem_sm = 0, smem_blk = 0;
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
+    DevInfo info;
+    if ((e = device_info(dev, info)) != cudaSuccess) return e;
+    const int nsm = info.nsm, smem_sm = info.smem_sm, smem_blk = info.smem_blk;
     const size_t fixed = 1024 + 2 * static_cast<size_t>(g.nbs) * kBSlabBytes + kOnesBytes;
     const size_t static_bytes = 4096;  // barriers, template tables and the per-CTA reservation, rounded up
     // two CTAs per SM when a ring of at least nslab + 2 slabs still fits, else one CTA with a deeper ring
@@ -753,17 +847,9 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
 
     CUtensorMap map;
     if ((e = hist_map(&map, a.z, a.pitch, a.T, P)) != cudaSuccess) return e;
-    auto kern = a.L <= 64 ? k_filter_tc<9> : k_filter_tc<17>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
-        return e;
-    // two CTAs per SM when shared memory allows it (256 tensor-memory columns each; the registers of two
-    // 192-thread CTAs fit by the launch bounds); the occupancy query confirms at least one fits
-    int fits = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, kern, kThreads, smem)) != cudaSuccess) return e;
-    if (fits < 1) return cudaErrorInvalidConfiguration;
+    const int variant = a.L <= 64 ? 0 : 1;
+    auto kern = variant == 0 ? k_filter_tc<9> : k_filter_tc<17>;
+    if ((e = prepare_kernel(dev, variant, reinterpret_cast<const void*>(kern), smem)) != cudaSuccess) return e;
     const long long want = static_cast<long long>(nsm) * per_sm;
     const int grid = static_cast<int>(g.npt < want ? g.npt : want);
     kern<<<grid, kThreads, smem, s>>>(map, a, g, status);
