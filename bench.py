@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per sequence (default 50)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff"],
+    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed"],
                     help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
-                         "frame; diff: differentiable filter forward + backward")
+                         "frame; diff: differentiable filter forward + backward; mixed: 1024x1024 FP16 frames "
+                         "through the tensor-core filter step")
     return ap.parse_args()
 
 
@@ -556,6 +557,175 @@ def diff(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------------------------------------
+# mixed precision: the filter step with the data term on the tensor cores
+# ---------------------------------------------------------------------------------------------------------
+
+MIX_HW, MIX_FRAMES, MIX_T, MIX_L, MIX_SBR, MIX_SEED = 1024, 20, 4096, 64, 0.05, 3
+MIX_CROP, MIX_CROP_FRAMES = 48, 2
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def mixed(args):
+    """Mixed precision: 1024 x 1024 pixels x 20 frames, T = 4096, the asymmetric IRF stretched to 64 taps, the
+    video scene generator (1-5 signal photons per pixel-frame) at SBR 0.05 (about 60 background photons per
+    pixel-frame), beta = 0.5, FP16 counts (exact up to 2048). One step = the 20 frames through
+    spl_filter_step_tc. Every frame is generated on the device (seeded per frame) before its filter step; CUDA
+    events bracket each step and the step time is their sum, so generation is outside the timed region (each
+    frame is 8.6 GB, far larger than L2). Also measured: spl_filter_step (FP32 CUDA cores) on the same FP16
+    frames, the depth RMSE of both against the ground truth, the tensor-core data term against an FP64
+    evaluation of its definition on a crop, and (CPU baseline leg) the FP64 oracle on crops with the
+    tensor-core filter's depths compared to it."""
+    import paper_2004_09211_gb300 as spl
+    from paper_2004_09211_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    Hm = Wm = MIX_HW
+    N, Tm, Lm = MIX_FRAMES, MIX_T, MIX_L
+    P = Hm * Wm
+    h, peak = synth.stretched_irf(synth.asymmetric_irf(L=48)[0], Lm)
+    sc = synth.moving_scene(Hm, Wm, N, peak + 8, Tm - Lm + peak - 8, MIX_SEED)
+    hd = torch.from_numpy(h).to(dev)
+    pitch = synth.pad_pitch(Tm)
+    prm = spl.make_params(Hm, Wm, Tm, Lm, peak, beta=0.5, sigma_rw2=SIGMA_RW2)
+    depth = [torch.from_numpy(sc.depth[n]).to(dev) for n in range(N)]
+    signal = [torch.from_numpy(sc.signal[n]).to(dev) for n in range(N)]
+    bgs = [float(sc.signal[n].mean()) / (MIX_SBR * Tm) for n in range(N)]
+    gen = torch.Generator(device=dev)
+    zbuf = torch.zeros(P, pitch, dtype=torch.float16, device=dev)
+
+    def gen_frame(n):
+        gen.manual_seed(MIX_SEED * 1000 + n)
+        synth.frame_histograms(depth[n], signal[n], bgs[n], hd, peak, Tm, gen, pitch, out=zbuf)
+
+    mu = [torch.empty(P, device=dev) for _ in range(2)]
+    var = [torch.empty(P, device=dev) for _ in range(2)]
+    outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                bg=torch.empty(P, device=dev))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(step_fn):
+        """The 20-frame sequence; returns (summed step ms, per-frame depth RMSE against the ground truth)."""
+        spl.spl_state_init(prm, mu[0], var[0])
+        total, rmse = 0.0, []
+        for n in range(N):
+            gen_frame(n)
+            src, dst = n & 1, (n + 1) & 1
+            e0.record()
+            step_fn(prm, zbuf, hd, mu[src], var[src], out=dict(mu=mu[dst], var=var[dst], **outs))
+            e1.record()
+            torch.cuda.synchronize(dev)
+            total += e0.elapsed_time(e1)
+            rmse.append(float(((mu[dst] - depth[n].reshape(-1).float()) ** 2).mean().sqrt()))
+        return total, rmse
+
+    for _ in range(args.warmup):
+        run(spl.spl_filter_step_tc)
+    with ClockSampler(0) as clk:
+        runs = [run(spl.spl_filter_step_tc) for _ in range(args.steps)]
+    ms = statistics.mean(r[0] for r in runs)
+    rmse_tc = runs[-1][1]
+    flags = spl.spl_tc_status()
+    ms_fp32, rmse_fp32 = run(spl.spl_filter_step)
+
+    # data term against an FP64 evaluation of its definition (C(d) = sum_j h_j^beta z[d - peak + j]) on a crop
+    gen_frame(0)
+    cz = 32
+    crop = zbuf.reshape(Hm, Wm, pitch)[:cz, :cz, :].contiguous().reshape(cz * cz, pitch)
+    pc = spl.make_params(cz, cz, Tm, Lm, peak, beta=0.5, sigma_rw2=SIGMA_RW2)
+    ctc, _ = spl.spl_depth_cost_tc(pc, crop, hd)
+    g64 = torch.where(hd > 0, hd.double().clamp(min=1e-300) ** 0.5, torch.zeros_like(hd, dtype=torch.float64))
+    win = crop[:, :Tm].double().unfold(1, Lm, 1)[:, pc.dmin - peak:pc.dmax - peak + 1, :]
+    cref = win @ g64
+    cerr = (ctc.double() - cref).abs()
+    cost_error = {"max_abs_over_max_C": float(cerr.max() / cref.max()),
+                  "rms_rel": float(((cerr / cref.clamp(min=1e-30)) ** 2).mean().sqrt()),
+                  "crop": f"{cz}x{cz} pixels of frame 0, all {pc.dmax - pc.dmin + 1} candidates"}
+
+    # roofline of the fused kernel: algorithmic bytes = FP16 row + previous state + outputs per pixel-frame;
+    # tensor work = the issued MMAs (hi and lo Toeplitz tiles, count MMAs)
+    peaks = _peaks()
+    kw = ((64 + Lm - 1) + 15) & ~15
+    ntiles = (prm.dmax - prm.dmin + 1 + 63) // 64
+    npt = (P + 127) // 128
+    slabs = max(ntiles + (kw + 63) // 64 - 1, (Tm + 63) // 64)
+    flops = npt * (ntiles * 2 * (2 * 128 * 64 * kw) + slabs * 2 * 128 * 16 * 64)
+    frame_s = ms / N / 1e3
+    alg_bytes = P * (2 * Tm + 8 + 20)
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    roofline = {"bound": "hbm", "achieved": alg_bytes / frame_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": alg_bytes / frame_s / 1e9 / hbm_peak, "traffic": None, "kernel": "k_filter_tc",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": frame_s * 1e3,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+                "tensor": {"achieved": flops / frame_s / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                           "frac": flops / frame_s / 1e12 / tc_peak, "flops_per_launch": flops,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops (FP16 runs at the BF16 rate)"},
+                "note": "epilogue-bound on this workload: broad posteriors leave nothing to prune, so every "
+                        "candidate's mixture prior is evaluated"}
+
+    cpu = None
+    if not args.no_cpu:
+        cpu = mixed_cpu_baseline(spl, synth, h, hd, peak, sc, dev)
+
+    rt, rf = statistics.mean(rmse_tc), statistics.mean(rmse_fp32)
+    line = {"metric": "pixel-frames/s", "value": P * N / (ms / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 x f16 -> f32 (tensor), f32 epilogue",
+            "data": "synthetic",
+            "config": {"workload": "mixed precision 1024x1024x20 frames, T=4096, 64-tap IRF, SBR 0.05, FP16 counts",
+                       "pixels": P, "frames": N, "T": Tm, "L": Lm, "beta": 0.5,
+                       "l2": "inputs larger than L2 (8.6 GB per frame), generated between timed steps"},
+            "fp32_path": {"value": P * N / (ms_fp32 / 1e3), "ms_per_step": ms_fp32,
+                          "speedup_tc_over_fp32": ms_fp32 / ms},
+            "depth_rmse_bins": {"tc_mean_over_frames": rt, "fp32_mean_over_frames": rf,
+                                "tc_last_frame": rmse_tc[-1], "fp32_last_frame": rmse_fp32[-1],
+                                "equal": abs(rt - rf) <= max(0.01, 0.01 * rf)},
+            "cost_error_vs_fp64": cost_error, "status_flags": flags, "roofline": roofline,
+            "gpu_launches": N * args.steps, "clocks": clk.summary(), "cpu_baseline": cpu, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
+def mixed_cpu_baseline(spl, synth, h, hd, peak, sc, dev):
+    """The FP64 oracle on a MIX_CROP x MIX_CROP crop of the mixed workload for MIX_CROP_FRAMES frames (host
+    cores, timed), and the tensor-core filter on the same crop as its own image, compared with it."""
+    from oracle import oracle as orc
+    c = MIX_CROP
+    pitch = synth.pad_pitch(MIX_T)
+    gen = torch.Generator(device=dev)
+    zs = []
+    for n in range(MIX_CROP_FRAMES):
+        gen.manual_seed(MIX_SEED * 7000 + n)
+        zs.append(synth.frame_histograms(torch.from_numpy(sc.depth[n][:c, :c].copy()).to(dev),
+                                         torch.from_numpy(sc.signal[n][:c, :c].copy()).to(dev),
+                                         float(sc.signal[n].mean()) / (MIX_SBR * MIX_T), hd, peak, MIX_T, gen, pitch))
+    q = orc.params(MIX_T, MIX_L, peak, beta=0.5, sigma_rw2=SIGMA_RW2, nu=synth.cross_weights(0.5))
+    threads = orc.set_threads(os.cpu_count() or 1)
+    m, v = orc.state_init(q, c, c)
+    t0 = time.perf_counter()
+    for z in zs:
+        e = orc.filter_step(q, h, z[:, :MIX_T].double().cpu().numpy().reshape(c, c, MIX_T), m, v)
+        m, v = e["mu"], e["var"]
+    dt = time.perf_counter() - t0
+    prm = spl.make_params(c, c, MIX_T, MIX_L, peak, beta=0.5, sigma_rw2=SIGMA_RW2)
+    mu, var = spl.spl_state_init(prm)
+    for z in zs:
+        o = spl.spl_filter_step_tc(prm, z, hd, mu, var)
+        mu, var = o["mu"], o["var"]
+    d = mu.double().cpu().numpy().reshape(c, c) - m
+    return {"value": c * c * MIX_CROP_FRAMES / dt, "unit": "pixel-frames/s", "cores": threads, "kind": "oracle",
+            "sample": f"{c}x{c} crop x {MIX_CROP_FRAMES} frames of the mixed workload (T={MIX_T}, L={MIX_L})",
+            "tc_vs_fp64_depth": {"rms_bins": float(np.sqrt((d ** 2).mean())), "max_abs_bins": float(np.abs(d).max()),
+                                 "max_rel": float((np.abs(d) / np.abs(m)).max())}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -564,6 +734,8 @@ def main():
         batched(args)
     elif args.workload == "diff":
         diff(args)
+    elif args.workload == "mixed":
+        mixed(args)
     else:
         native(args)
 

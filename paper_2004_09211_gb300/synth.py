@@ -173,18 +173,22 @@ def poisson_histograms(mean: torch.Tensor, gen: torch.Generator, dtype=torch.uin
 
 def frame_histograms(depth: torch.Tensor, signal: torch.Tensor, bg_per_bin: float, h: torch.Tensor, peak: int,
                      T: int, gen: torch.Generator, pitch: int, dtype=torch.float16, chunk: int = 1 << 15,
-                     max_count: int = 2048) -> torch.Tensor:
+                     max_count: int = 2048, out: torch.Tensor | None = None) -> torch.Tensor:
     """Poisson histograms of one frame straight into a zero-padded [P, pitch] buffer on depth's device, a chunk
     of pixels at a time (for frames too large for expected_counts): per bin Poisson(bg_per_bin) plus, at bins
     d - peak + j, Poisson(signal * h_j) (the same law as poisson_histograms(expected_counts(...)): a sum of
-    independent Poisson counts). Counts above max_count are clipped."""
+    independent Poisson counts). Counts above max_count are clipped. `out` ([P, pitch] of dtype) is filled in
+    place when given."""
     dev = depth.device
     d = depth.reshape(-1).to(torch.int64)
     r = signal.reshape(-1).to(device=dev, dtype=torch.float32)
     hh = h.to(device=dev, dtype=torch.float32)
     L = hh.numel()
     P = d.numel()
-    out = torch.zeros(P, pitch, dtype=dtype, device=dev)
+    if out is None:
+        out = torch.zeros(P, pitch, dtype=dtype, device=dev)
+    elif pitch > T:
+        out[:, T:].zero_()
     jj = torch.arange(L, device=dev)
     for p0 in range(0, P, chunk):
         p1 = min(P, p0 + chunk)
