@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per sequence (default 50)")
+    ap.add_argument("--side", type=int, default=None,
+                    help="mixed workload only: image side (default 1024; smaller sides for profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed"],
@@ -587,8 +589,9 @@ def mixed(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     spl.load_library()
-    Hm = Wm = MIX_HW
-    N, Tm, Lm = MIX_FRAMES, MIX_T, MIX_L
+    Hm = Wm = args.side or MIX_HW
+    N = args.frames if args.frames != N_FRAMES else MIX_FRAMES
+    Tm, Lm = MIX_T, MIX_L
     P = Hm * Wm
     h, peak = synth.stretched_irf(synth.asymmetric_irf(L=48)[0], Lm)
     sc = synth.moving_scene(Hm, Wm, N, peak + 8, Tm - Lm + peak - 8, MIX_SEED)
@@ -680,7 +683,7 @@ def mixed(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 x f16 -> f32 (tensor), f32 epilogue",
             "data": "synthetic",
-            "config": {"workload": "mixed precision 1024x1024x20 frames, T=4096, 64-tap IRF, SBR 0.05, FP16 counts",
+            "config": {"workload": f"mixed precision {Hm}x{Wm}x{N} frames, T=4096, 64-tap IRF, SBR 0.05, FP16 counts",
                        "pixels": P, "frames": N, "T": Tm, "L": Lm, "beta": 0.5,
                        "l2": "inputs larger than L2 (8.6 GB per frame), generated between timed steps"},
             "fp32_path": {"value": P * N / (ms_fp32 / 1e3), "ms_per_step": ms_fp32,
