@@ -170,6 +170,49 @@ struct Grid {
     float lam2, gmax;        // lambda log2(e), max_j g_j
 };
 
+// One lane's run of candidates r0 .. r1 - 1 in the linear domain (see above), with the mixture loops sized to
+// NC >= pr.n component slots; slots past pr.n start at 0 and stay 0. Writes the weights into cs and accumulates
+// the lane's best weight and moments about cstar.
+template <int NC>
+__device__ __forceinline__ void lin_run(const Grid& g, const Prior& pr, float* cs, int r0, int r1, float sref,
+                                        float xref, int cstar, float& best, int& bidx, float& s0, float& s1,
+                                        float& s2) {
+    float v[NC > 0 ? NC : 1], q[NC > 0 ? NC : 1], kk[NC > 0 ? NC : 1];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        v[i] = q[i] = 0.f;
+        kk[i] = i < pr.n ? ex2(-2.f * pr.ck[i]) : 0.f;
+    }
+    for (int c = r0; c < r1; ++c) {
+        const float d = static_cast<float>(g.dmin + c);
+        if (((c - r0) & (kRestart - 1)) == 0) {  // exact restart of every component
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const float e = d - pr.cm[i];
+                v[i] = i < pr.n ? ex2(pr.ca[i] - pr.ck[i] * e * e - sref) : 0.f;
+                q[i] = i < pr.n ? ex2(fminf(-pr.ck[i] * (2.f * e + 1.f), 100.f)) : 0.f;
+            }
+        }
+        float m = NC == 0 ? 1.f : 0.f;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            m += v[i];
+            v[i] *= q[i];
+            q[i] *= kk[i];
+        }
+        const float w = ex2(fmaf(g.lam2, cs[c], -xref)) * m;
+        cs[c] = w;
+        if (w > best) {
+            best = w;
+            bidx = c;
+        }
+        const float dd = static_cast<float>(c - cstar);
+        s0 += w;
+        s1 = fmaf(w, dd, s1);
+        s2 = fmaf(w * dd, dd, s2);
+    }
+}
+
 // cs[0 .. D) holds C(d) on entry; cs[0 .. 32 NB) and ubs[0 .. NB) are scratch. count(s, e) returns an upper
 // bound of the photons in bins [s, e] (evaluated per lane). restore() writes C back into cs (needed only on
 // the rare fallback from the linear path). Outputs: index of the smallest maximiser, mean depth and variance.
@@ -230,44 +273,17 @@ __device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float 
         const int c_lo = 32 * bfirst, c_hi = min(32 * blast + 31, D - 1);
         const int run = (c_hi - c_lo + 32) >> 5;
         const int r0 = c_lo + lane * run, r1 = min(r0 + run, c_hi + 1);
-        float v[kMaxComp], q[kMaxComp], kk[kMaxComp];
-#pragma unroll
-        for (int i = 0; i < kMaxComp; ++i) {
-            v[i] = q[i] = 0.f;
-            kk[i] = i < pr.n ? ex2(-2.f * pr.ck[i]) : 0.f;
-        }
         float best = -INFINITY;
         int bidx = 0x7fffffff;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int c = r0; c < r1; ++c) {
-            const float d = static_cast<float>(g.dmin + c);
-            if (((c - r0) & (kRestart - 1)) == 0) {  // exact restart of every component
-#pragma unroll
-                for (int i = 0; i < kMaxComp; ++i)
-                    if (i < pr.n) {
-                        const float e = d - pr.cm[i];
-                        v[i] = ex2(pr.ca[i] - pr.ck[i] * e * e - sref);
-                        q[i] = ex2(fminf(-pr.ck[i] * (2.f * e + 1.f), 100.f));
-                    }
-            }
-            float m = pr.n == 0 ? 1.f : 0.f;
-#pragma unroll
-            for (int i = 0; i < kMaxComp; ++i)
-                if (i < pr.n) {
-                    m += v[i];
-                    v[i] *= q[i];
-                    q[i] *= kk[i];
-                }
-            const float w = ex2(fmaf(lam2, cs[c], -xref)) * m;
-            cs[c] = w;
-            if (w > best) {
-                best = w;
-                bidx = c;
-            }
-            const float dd = static_cast<float>(c - cstar);
-            s0 += w;
-            s1 = fmaf(w, dd, s1);
-            s2 = fmaf(w * dd, dd, s2);
+        switch (pr.n) {  // warp-uniform: loops sized to the component count
+            case 0: lin_run<0>(g, pr, cs, r0, r1, sref, xref, cstar, best, bidx, s0, s1, s2); break;
+            case 1: lin_run<1>(g, pr, cs, r0, r1, sref, xref, cstar, best, bidx, s0, s1, s2); break;
+            case 2: lin_run<2>(g, pr, cs, r0, r1, sref, xref, cstar, best, bidx, s0, s1, s2); break;
+            case 3: lin_run<3>(g, pr, cs, r0, r1, sref, xref, cstar, best, bidx, s0, s1, s2); break;
+            case 4:
+            case 5: lin_run<5>(g, pr, cs, r0, r1, sref, xref, cstar, best, bidx, s0, s1, s2); break;
+            default: lin_run<kMaxComp>(g, pr, cs, r0, r1, sref, xref, cstar, best, bidx, s0, s1, s2); break;
         }
         warp_argmax(best, bidx);
         __syncwarp();
