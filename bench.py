@@ -42,6 +42,31 @@ SEED = 2
 WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.1,1} x beta {0.2,0.5,1}"
 
 
+# DRAM bytes (read + write) per launch of each workload's dominant kernel, from one ncu capture of that kernel
+# (the full-size launch, or a smaller launch scaled by the pixels processed where the full one is too large to
+# capture), valid only for the exact kernel sources it was taken on: the bench reports null for "traffic" when
+# the sources' hash differs.
+TRAFFIC_CAPTURES = {
+    "k_estimate": {"sources": ("estimate.cu", "pixel.cuh"),
+                   "sha256": "888f9f473175fa6f8e3b4435a7effafebc6dc9a999a316e8f9711e0e18300dd9",
+                   "bytes_per_pixel": 201.55e6 / 65536},
+    "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh"),
+                    "sha256": "e28bd2fec48f8c9d9720055e3eb9797d42510f1116a5f3384f11662c9b41c1a2",
+                    "bytes_per_pixel": 555.17e6 / 65536},
+}
+
+
+def capture_traffic(kernel: str, pixels: int):
+    """Traffic per launch of `kernel` over `pixels` pixels from its capture, or None if the sources changed."""
+    import hashlib
+    cap = TRAFFIC_CAPTURES[kernel]
+    h = hashlib.sha256()
+    for f in cap["sources"]:
+        with open(os.path.join(ROOT, "paper_2004_09211_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return cap["bytes_per_pixel"] * pixels if h.hexdigest() == cap["sha256"] else None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,7 +243,7 @@ def native(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / avg_kernel_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
+                "frac": achieved / hbm_peak, "traffic": capture_traffic("k_estimate", P),
                 "kernel": "k_estimate<u16> (spl_filter_step)", "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": avg_kernel_s * 1e3,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
@@ -665,7 +690,8 @@ def mixed(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
     roofline = {"bound": "hbm", "achieved": alg_bytes / frame_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "frac": alg_bytes / frame_s / 1e9 / hbm_peak, "traffic": None, "kernel": "k_filter_tc",
+                "frac": alg_bytes / frame_s / 1e9 / hbm_peak, "traffic": capture_traffic("k_filter_tc", P),
+                "kernel": "k_filter_tc",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": frame_s * 1e3,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
                 "tensor": {"achieved": flops / frame_s / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
