@@ -78,10 +78,11 @@ def parse():
                     help="mixed workload only: image side (default 1024; smaller sides for profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed"],
+    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc"],
                     help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
                          "frame; diff: differentiable filter forward + backward; mixed: 1024x1024 FP16 frames "
-                         "through the tensor-core filter step")
+                         "through the tensor-core filter step; video_tc: the video job through the tensor-core "
+                         "filter step on FP16 copies of its frames, beside the FP32 path")
     return ap.parse_args()
 
 
@@ -159,8 +160,9 @@ def make_sequences(frames: int, device):
     return h, peak, hd, sc, videos
 
 
-def run_job(spl, prms, hd, videos, states, outs, stream, ev=None):
+def run_job(spl, prms, hd, videos, states, outs, stream, ev=None, step=None):
     """One step: every (SBR, beta) run over all frames. Returns the number of kernel launches."""
+    step = step or spl.spl_filter_step
     launches = 0
     for vi, frames_z in enumerate(videos):
         for bi in range(len(BETAS)):
@@ -173,8 +175,7 @@ def run_job(spl, prms, hd, videos, states, outs, stream, ev=None):
                 if ev is not None:
                     ev[0].append(torch.cuda.Event(enable_timing=True))
                     ev[0][-1].record(stream)
-                spl.spl_filter_step(prm, z, hd, mu[src], var[src], out=dict(mu=mu[dst], var=var[dst], **outs),
-                                    stream=stream)
+                step(prm, z, hd, mu[src], var[src], out=dict(mu=mu[dst], var=var[dst], **outs), stream=stream)
                 if ev is not None:
                     ev[1].append(torch.cuda.Event(enable_timing=True))
                     ev[1][-1].record(stream)
@@ -584,6 +585,60 @@ def diff(args):
     print(json.dumps(line), flush=True)
 
 
+def video_tc(args):
+    """The video job (the headline workload) through spl_filter_step_tc on FP16 copies of its uint16 frames (the
+    counts are small integers, exact in FP16), timed like the headline, beside spl_filter_step on the original
+    frames. Also reported: the depth RMSE of both paths against the ground truth at every run's last frame."""
+    import paper_2004_09211_gb300 as spl
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    frames = args.frames
+    h, peak, hd, sc, videos = make_sequences(frames, dev)
+    videos16 = [[z.to(torch.int32).to(torch.float16) for z in v] for v in videos]
+    P = H * W
+    prms = [spl.make_params(H, W, T, L, peak, beta=b, sigma_rw2=SIGMA_RW2) for b in BETAS]
+    states = [[([torch.empty(P, device=dev) for _ in range(2)], [torch.empty(P, device=dev) for _ in range(2)])
+               for _ in BETAS] for _ in SBRS]
+    outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                bg=torch.empty(P, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    units = len(SBRS) * len(BETAS) * frames * P
+    truth = torch.from_numpy(sc.depth[frames - 1].reshape(-1)).to(dev).float()
+
+    def timed(step, vids):
+        for _ in range(args.warmup):
+            run_job(spl, prms, hd, vids, states, outs, stream, step=step)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            run_job(spl, prms, hd, vids, states, outs, stream, step=step)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        last = frames & 1  # the buffer holding each run's final state
+        rmse = [float(((states[vi][bi][0][last] - truth) ** 2).mean().sqrt()) for vi in range(len(SBRS))
+                for bi in range(len(BETAS))]
+        return e0.elapsed_time(e1) / args.steps, rmse
+
+    with ClockSampler(0) as clk:
+        ms_tc, rmse_tc = timed(spl.spl_filter_step_tc, videos16)
+    flags = spl.spl_tc_status()
+    ms_32, rmse_32 = timed(spl.spl_filter_step, videos)
+    runs = [f"SBR {sb} beta {b}" for sb in SBRS for b in BETAS]
+    line = {"metric": "pixel-frames/s", "value": units / (ms_tc / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_tc, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 x f16 -> f32 (tensor), f32 epilogue",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + ", FP16 copies of the counts", "pixels": P, "frames": frames,
+                       "pixel_frames_per_step": units},
+            "fp32_path": {"value": units / (ms_32 / 1e3), "ms_per_step": ms_32, "speedup_tc_over_fp32": ms_32 / ms_tc},
+            "depth_rmse_bins_last_frame": {r: {"tc": a, "fp32": b} for r, a, b in zip(runs, rmse_tc, rmse_32)},
+            "status_flags": flags, "gpu_launches": len(SBRS) * len(BETAS) * (frames + 1) * args.steps,
+            "clocks": clk.summary(), "roofline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------------------------------------
 # mixed precision: the filter step with the data term on the tensor cores
 # ---------------------------------------------------------------------------------------------------------
@@ -765,6 +820,8 @@ def main():
         diff(args)
     elif args.workload == "mixed":
         mixed(args)
+    elif args.workload == "video_tc":
+        video_tc(args)
     else:
         native(args)
 
