@@ -183,6 +183,19 @@ def run_job(spl, prms, hd, videos, states, outs, stream, ev=None, step=None):
     return launches
 
 
+def replica_throughput(ms_local: float, units_per_rank: int, steps: int, world: int, device=None):
+    """Whole-job figures of N independent replicas (the path has no data-path collective): the slowest rank's
+    time bounds the job (max over ranks, all_reduce on `device` when a process group is initialised), and the
+    value counts the units of every rank. Returns (ms_max, units per second)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch.distributed as td
+        t = torch.tensor([ms], device=device if device is not None else "cpu", dtype=torch.float64)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * world * steps / (ms / 1e3)
+
+
 def native(args):
     import paper_2004_09211_gb300 as spl
     rank = int(os.environ.get("RANK", "0"))
@@ -226,11 +239,7 @@ def native(args):
         barrier()
     ms = start.elapsed_time(stop)
     kern_ms = [a.elapsed_time(b) for a, b in zip(*ev)]
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
-    value = units * world * args.steps / (ms / 1e3)
+    ms, value = replica_throughput(ms, units, args.steps, world, dev if dist else None)
 
     # roofline of the dominant kernel (the fused filter step): algorithmic bytes per pixel-frame =
     # histogram row (2 T) + previous state (mu, var) + outputs (mu, var, argmax, refl, bg)

@@ -125,3 +125,30 @@ def test_batch_argument_checks():
     assert lib.spl_batch_tune(None, 0, None) == _abi.SPL_EINVAL
     assert lib.spl_batch_info(None, None, None, None, None) == _abi.SPL_EINVAL
     assert lib.spl_batch_status(None, None) == _abi.SPL_EINVAL
+
+
+def test_tensor_core_argument_checks():
+    """spl_depth_cost_tc / spl_filter_step_tc take FP16 histograms only and check the filter arguments like
+    spl_filter_step, all on the host."""
+    lib = _abi.load()
+    prm = make_params(4, 4, 64, 25, 12)
+    hz_u16 = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 64)
+    hz_f16 = _abi.spl_hist(_abi.SPL_HIST_F16, 0x1000, 64)
+    st = lib.spl_depth_cost_tc(ct.byref(prm), ct.byref(hz_u16), 0x2000, 0x3000, None, None)
+    assert st == _abi.SPL_EINVAL and "FP16" in lib.spl_last_error().decode()
+    st = lib.spl_depth_cost_tc(ct.byref(prm), ct.byref(hz_f16), 0x2000, None, None, None)
+    assert st == _abi.SPL_EINVAL and "nothing to compute" in lib.spl_last_error().decode()
+    st = lib.spl_filter_step_tc(ct.byref(prm), ct.byref(hz_u16), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                                0x6000, None, None, None, None)
+    assert st == _abi.SPL_EINVAL and "FP16" in lib.spl_last_error().decode()
+    st = lib.spl_filter_step_tc(ct.byref(prm), ct.byref(hz_f16), 0x2000, 0x3000, 0x4000, None, None, None, 0x3000,
+                                0x6000, None, None, None, None)
+    assert st == _abi.SPL_EINVAL and "alias" in lib.spl_last_error().decode()
+    st = lib.spl_filter_step_tc(ct.byref(prm), ct.byref(hz_f16), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                                0x6000, None, 0x7000, None, None)
+    assert st == _abi.SPL_EINVAL and "refl and bg" in lib.spl_last_error().decode()
+    bad = make_params(4, 4, 64, 25, 12, sigma_rw2=0.0)
+    st = lib.spl_filter_step_tc(ct.byref(bad), ct.byref(hz_f16), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                                0x6000, None, None, None, None)
+    assert st == _abi.SPL_EINVAL and "sigma_rw2" in lib.spl_last_error().decode()
+    assert lib.spl_tc_status(None) == _abi.SPL_EINVAL
