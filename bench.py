@@ -48,7 +48,7 @@ WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.
 # the sources' hash differs.
 TRAFFIC_CAPTURES = {
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh"),
-                   "sha256": "888f9f473175fa6f8e3b4435a7effafebc6dc9a999a316e8f9711e0e18300dd9",
+                   "sha256": "7fba7a62574d59a268ff7304a1393940b778a0f5ff4684dd304eed1d999b2a91",
                    "bytes_per_pixel": 201.55e6 / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh"),
                     "sha256": "e28bd2fec48f8c9d9720055e3eb9797d42510f1116a5f3384f11662c9b41c1a2",

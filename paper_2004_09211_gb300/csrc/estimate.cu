@@ -15,6 +15,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <atomic>
+
 #include "pixel.cuh"
 #include "spl_internal.h"
 
@@ -521,11 +523,11 @@ cudaError_t launch_t(const EstimateArgs& a, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    static int configured[64] = {0};
-    if (dev < 64 && !configured[dev]) {
+    static std::atomic<int> configured[64];  // per device: the shared-memory limit has been raised
+    if (dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return e;
-        configured[dev] = 1;
+        if (dev < 64) configured[dev].store(1, std::memory_order_release);
     }
     int nsm = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
