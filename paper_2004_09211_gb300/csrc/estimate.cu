@@ -284,6 +284,45 @@ __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const 
     return warp_max(mx);
 }
 
+constexpr int kLaneNnz = 128;  // rows with at most this many non-empty bins: lane-per-candidate correlation
+
+// Rows with few non-empty bins: lane = candidate, four 32-candidate blocks per pass over the packed bins whose
+// chunks meet the four blocks' window. Every lane runs the same photon loop (no divergence) with four
+// independent accumulators; a tap index outside 0 .. L-1 reads gs[L] = 0. Returns max C.
+__device__ __forceinline__ float corr_lanes(const float* __restrict__ gs, const unsigned* ent, const int* cpe,
+                                           float* cs, int NB, int D, int L, int u0, int cb, int nch, int lane) {
+    float mx = 0.f;
+    for (int b0 = 0; b0 < NB; b0 += 4) {
+        const int nblk = min(4, NB - b0);
+        const int c0 = 32 * b0 + lane;
+        const int ch_lo = (u0 + 32 * b0) / cb;
+        const int ch_hi = min((u0 + 32 * (b0 + nblk) - 1 + L - 1) / cb + 1, nch);
+        const int e_lo = cpe[ch_lo], e_hi = cpe[ch_hi];
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int e = e_lo; e < e_hi; ++e) {
+            const unsigned en = ent[e];
+            const int base = static_cast<int>(en >> 16) - u0 - c0;
+            const float z = static_cast<float>(en & 0xffffu);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = base - 32 * k;
+                acc[k] = fmaf(z, gs[static_cast<unsigned>(j) < static_cast<unsigned>(L) ? j : L], acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < nblk) {
+                const int c = c0 + 32 * k;
+                const float v = c < D ? acc[k] : 0.f;
+                cs[c] = v;
+                mx = fmaxf(mx, v);
+            }
+        }
+    }
+    __syncwarp();
+    return warp_max(mx);
+}
+
 // C(d) for all candidates of one pixel (staged row in raw, prefix sums in cps/cpe). Returns max C. Zero skip
 // needs every count below 2^16 (packed entries); `sparse_ok` says so.
 template <int FMT, int CB>
@@ -305,6 +344,7 @@ __device__ __forceinline__ float correlate(const float* __restrict__ gs, const f
                 if (f[k] != 0.f) ent[o++] = (static_cast<unsigned>(i * CB + k) << 16) | static_cast<unsigned>(f[k]);
         }
         __syncwarp();
+        if (cpe[nch] <= kLaneNnz) return corr_lanes(gs, ent, cpe, cs, NB, D, L, u0, CB, nch, lane);
         return corr_runs(gs, ent, cpe, cs, D, L, u0, CB, lane);
     }
     return corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
