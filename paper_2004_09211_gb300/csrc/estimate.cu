@@ -212,36 +212,6 @@ __device__ __forceinline__ void warp_scan2(float* x, int* y, int n, int lane) {
 // Correlation C(d) for every candidate into cs[0 .. 32 NB); each routine returns max_d C(d) (warp-uniform)
 // ------------------------------------------------------------------------------------------------------------
 
-// Sparse rows: lane l owns the contiguous run [r0, r1) of candidates and adds z_t g_{t-u0-c} into each
-// candidate c of its run for every non-empty bin t whose taps reach the run (the bins come from the compacted
-// list, the chunk prefix gives the first and last relevant entries). No other lane writes the run, so the
-// accumulation needs no synchronisation.
-__device__ __forceinline__ float corr_runs(const float* __restrict__ gs, const unsigned* ent, const int* cpe,
-                                           float* cs, int D, int L, int u0, int cb, int lane) {
-    // cs holds 32 * ceil(D / 32) words, exactly the 32 runs of ceil(D / 32) candidates
-    const int run = (D + 31) >> 5;
-    const int r0 = lane * run, r1 = min(r0 + run, D);
-    zero_words(cs, run * 8, lane);  // 32 * run candidates, 16-byte stores
-    float mx = 0.f;
-    if (r0 < r1) {
-        const int e_lo = cpe[(u0 + r0) / cb];
-        const int e_hi = cpe[(u0 + r1 - 1 + L - 1) / cb + 1];
-        for (int e = e_lo; e < e_hi; ++e) {
-            const unsigned en = ent[e];
-            const float zc = static_cast<float>(en & 0xffffu);
-            const int tc = static_cast<int>(en >> 16) - u0;  // candidate whose tap 0 falls on this bin
-            const int lo = max(tc - L + 1, r0), hi = min(tc, r1 - 1);
-            for (int c = lo; c <= hi; ++c) {
-                const float v = fmaf(zc, gs[tc - c], cs[c]);
-                cs[c] = v;
-                mx = fmaxf(mx, v);
-            }
-        }
-    }
-    __syncwarp();
-    return warp_max(mx);
-}
-
 // Dense rows: a lane computes 8 consecutive candidates per 256-candidate super-block. Super-blocks start at
 // candidate -(u0 & 3) so every lane's window starts on a 4-bin boundary (candidates < 0 are dropped). Windows
 // may read up to 11 bins past the row: the staging buffer is zero there (bins T..pitch-1 are zeroed too).
@@ -284,9 +254,7 @@ __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const 
     return warp_max(mx);
 }
 
-constexpr int kLaneNnz = 128;  // rows with at most this many non-empty bins: lane-per-candidate correlation
-
-// Rows with few non-empty bins: lane = candidate, four 32-candidate blocks per pass over the packed bins whose
+// Sparse rows (at most kNnzSparse non-empty bins): lane = candidate, four 32-candidate blocks per pass over the packed bins whose
 // chunks meet the four blocks' window. Every lane runs the same photon loop (no divergence) with four
 // independent accumulators; a tap index outside 0 .. L-1 reads gs[L] = 0. Returns max C.
 __device__ __forceinline__ float corr_lanes(const float* __restrict__ gs, const unsigned* ent, const int* cpe,
@@ -344,8 +312,7 @@ __device__ __forceinline__ float correlate(const float* __restrict__ gs, const f
                 if (f[k] != 0.f) ent[o++] = (static_cast<unsigned>(i * CB + k) << 16) | static_cast<unsigned>(f[k]);
         }
         __syncwarp();
-        if (cpe[nch] <= kLaneNnz) return corr_lanes(gs, ent, cpe, cs, NB, D, L, u0, CB, nch, lane);
-        return corr_runs(gs, ent, cpe, cs, D, L, u0, CB, lane);
+        return corr_lanes(gs, ent, cpe, cs, NB, D, L, u0, CB, nch, lane);
     }
     return corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
 }
