@@ -25,7 +25,8 @@ namespace {
 
 using namespace px;
 
-constexpr int kNnzSparse = 320;  // zero-skip correlation up to this many non-empty bins
+constexpr int kNnzSparse = 320;  // capacity of the packed non-empty-bin list
+constexpr int kLaneNnz = 64;     // zero-skip correlation up to this many non-empty bins, dense tap sum above
 
 // Shared-memory slice of one warp (all offsets in 4-byte words; every array starts 16-byte aligned).
 struct Slice {
@@ -254,9 +255,9 @@ __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const 
     return warp_max(mx);
 }
 
-// Sparse rows (at most kNnzSparse non-empty bins): lane = candidate, four 32-candidate blocks per pass over the packed bins whose
-// chunks meet the four blocks' window. Every lane runs the same photon loop (no divergence) with four
-// independent accumulators; a tap index outside 0 .. L-1 reads gs[L] = 0. Returns max C.
+// Sparse rows (at most kLaneNnz non-empty bins): lane = candidate, four 32-candidate blocks per pass over the
+// packed bins whose chunks meet the four blocks' window. Every lane runs the same photon loop (no divergence) with
+// four independent accumulators; a tap index outside 0 .. L-1 reads gs[L] = 0. Returns max C.
 __device__ __forceinline__ float corr_lanes(const float* __restrict__ gs, const unsigned* ent, const int* cpe,
                                            float* cs, int NB, int D, int L, int u0, int cb, int nch, int lane) {
     float mx = 0.f;
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             warp_scan2(cps, cpe, sl.nch, lane);
         }
         const bool empty = faulty || nnz == 0;
-        const bool sparse = nnz <= kNnzSparse && zmax < 65536.f;
+        const bool sparse = nnz <= kLaneNnz && zmax < 65536.f;
 
         // ---- 2. C(d) for every candidate ----
         const float cmax = correlate<FMT, CB>(gs, raw, ent, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane);
