@@ -21,8 +21,9 @@
 //             into running (weight, mean, second central moment) with a shared exponent reference, the chunk's
 //             own moments taken about its best candidate (the pairwise update of Chan, Golub and LeVeque), so
 //             no step subtracts large nearly equal numbers.
-//     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax, and the intensity MLE of Sec. II-E
-//             on the template at round-half-even(mu) with K from the count MMA.
+//     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax; the photon count K goes to bg.
+// A second kernel, k_intensity_tc (one warp per pixel), then runs the intensity MLE of Sec. II-E on the template at
+// round-half-even(mu) with that K and writes refl and bg.
 // All mbarrier waits are bounded (status bit 0 on time-out; the roles then stop, in-flight copies and MMAs are
 // waited for, tensor memory is released).
 #include <math.h>
@@ -49,7 +50,6 @@ constexpr int kMaxRing = 8;
 constexpr int kThreads = 192;
 constexpr unsigned kTmemCols = 256;              // acc 0 | acc 1 | count 0 | count 1 (64 + 64 + 16 + 16 used)
 constexpr unsigned kCntCol = 128;
-constexpr unsigned kWinCol = 160;                // intensity window staging: up to 4 x 17 columns
 constexpr float kScale = 32768.f;
 constexpr unsigned kSlabBytes = kM * kSlab * 2;  // 16 KB
 constexpr unsigned kBSlabBytes = kN * kSlab * 2; // 8 KB
@@ -351,92 +351,6 @@ __device__ __forceinline__ bool chunk_lin(const float* c, int c0, int D, int dmi
     return true;
 }
 
-__device__ __forceinline__ float half_at(uint4 w, int h) {
-    const unsigned word = h < 2 ? w.x : h < 4 ? w.y : h < 6 ? w.z : w.w;
-    return __half2float(__ushort_as_half(static_cast<unsigned short>((h & 1) ? word >> 16 : word)));
-}
-
-// Intensity MLE of Sec. II-E for one pixel per thread (the per-warp version is px::intensity_mle). The window
-// bins t0 .. t0 + L - 1 of this lane's pixel are staged in its tensor-memory lane as packed FP16 (LCH 16-byte
-// groups starting at bin t0 - sh, columns win .. win + 4 LCH - 1); the normalised template is in shared memory.
-// Warp-collective: every lane runs the loops (the tensor-memory loads are warp-wide); lanes with need == false
-// only take part. psi(f) = sum_W z (a - u) / (u + f (a - u)) - Kout / (1 - f), u = 1/T, is decreasing on
-// [0, 1): safeguarded Newton on psi with the bracket [lo, hi] kept around its root; r = f K / sum(h),
-// b = (1 - f) K / T.
-template <int LCH>
-__device__ __forceinline__ void intensity_lanes(uint32_t win, int sh, bool need, float K, int L, int T, float hsum,
-                                                const float* s_a, float& r, float& b) {
-    const float u = 1.f / static_cast<float>(T);
-    float kin = 0.f, za = 0.f, p1 = 0.f;
-    bool zero_tap = false;
-#pragma unroll 1
-    for (int grp = 0; grp < LCH; ++grp) {
-        const uint4 w = tmem_ld4(win + 4 * grp);
-        tmem_wait_ld();
-#pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            const float z = half_at(w, h);
-            const int j = 8 * grp + h - sh;
-            if (static_cast<unsigned>(j) < static_cast<unsigned>(L)) {
-                const float aj = s_a[j];
-                kin += z;
-                za = fmaf(z, aj, za);
-                if (z > 0.f) {
-                    if (aj > 0.f) p1 += z * __fdividef(aj - u, aj);
-                    else zero_tap = true;
-                }
-            }
-        }
-    }
-    const float kout = fmaxf(K - kin, 0.f);
-    const float psi0 = static_cast<float>(T) * za - K;
-    float f = 0.f, lo = 0.f, hi = 1.f;
-    bool active = false;
-    if (!(psi0 > 0.f)) {
-        f = 0.f;
-    } else if (!(kout > 0.f) && !zero_tap && p1 >= 0.f) {
-        f = 1.f;
-    } else {
-        const float fr = static_cast<float>(L) * u;
-        f = fr < 1.f ? (kin - K * fr) / (K * (1.f - fr)) : 0.5f;
-        f = fminf(fmaxf(f, 0.02f), 0.98f);
-        active = need;
-    }
-    for (int it = 0; it < 64; ++it) {
-        if (!__any_sync(0xffffffffu, active)) break;
-        float gs = 0.f, gp = 0.f;
-#pragma unroll 1
-        for (int grp = 0; grp < LCH; ++grp) {
-            const uint4 w = tmem_ld4(win + 4 * grp);
-            tmem_wait_ld();
-#pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                const float z = half_at(w, h);
-                const int j = 8 * grp + h - sh;
-                if (static_cast<unsigned>(j) < static_cast<unsigned>(L) && z > 0.f) {
-                    const float aj = s_a[j];
-                    const float e = __fdividef(aj - u, fmaf(f, aj - u, u));
-                    gs = fmaf(z, e, gs);
-                    gp = fmaf(z * e, e, gp);
-                }
-            }
-        }
-        if (active) {
-            const float rom = __fdividef(1.f, 1.f - f);
-            gs = fmaf(-kout, rom, gs);
-            gp = fmaf(kout * rom, rom, gp);
-            if (gs > 0.f) lo = f; else hi = f;
-            float fn = f + __fdividef(gs, gp);
-            if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
-            const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
-            f = fn;
-            if (conv) active = false;
-        }
-    }
-    r = f * K / hsum;
-    b = (1.f - f) * K * u;
-}
-
 // One candidate tile of one pixel (this lane). A tile whose prior bound alone reaches the pruning threshold is
 // kept without looking at the data (C >= 0); otherwise its largest accumulator decides. Kept tiles are evaluated
 // chunk by chunk with the tile's prior bound as the reference. The tensor-memory loads are warp-collective:
@@ -486,7 +400,6 @@ __device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmi
     }
 }
 
-template <int LCH>
 __global__ void __launch_bounds__(kThreads, 2)
     k_filter_tc(const __grid_constant__ CUtensorMap zmap, const EstimateArgs a, const TcGeom g, unsigned* status) {
     extern __shared__ unsigned char smem_raw[];
@@ -494,8 +407,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float s_g[SPL_MAX_TAPS];
-    __shared__ float s_a[SPL_MAX_TAPS];
-    __shared__ float s_hsum;
 
     const unsigned base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - smem_u32(smem_raw));
@@ -516,7 +427,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int j = tid; j < SPL_MAX_TAPS; j += kThreads) {
         const float hj = j < a.L ? a.h[j] : 0.f;
         s_g[j] = hj > 0.f ? powf(hj, a.beta) : 0.f;
-        s_a[j] = hj > 0.f ? hj : 0.f;
     }
     if (tid == 0) {
         for (unsigned i = 0; i < ring; ++i) {
@@ -533,14 +443,6 @@ __global__ void __launch_bounds__(kThreads, 2)
         abort_flag = 0;
     }
     __syncthreads();
-    if (warp == 0) {  // normalised template for the intensity step
-        float sum = 0.f;
-        for (int j = lane; j < a.L; j += 32) sum += s_a[j];
-        sum = px::warp_sum(sum);
-        if (lane == 0) s_hsum = sum;
-        if (sum > 0.f)
-            for (int j = lane; j < a.L; j += 32) s_a[j] /= sum;
-    }
     for (int e = tid; e < g.nbs * kSlab * kN; e += kThreads) {  // Toeplitz operand, high and low parts
         const int k = e / kN, n = e - k * kN;
         const int j = k - n - g.delta;
@@ -635,7 +537,6 @@ __global__ void __launch_bounds__(kThreads, 2)
         // ================= epilogue: thread = pixel = TMEM lane =================
         const long long P = static_cast<long long>(a.H) * a.W;
         const int D = a.D, T = a.T, L = a.L, dmin = a.dmin;
-        const float hsum = s_hsum;
         const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
         unsigned tcount = 0, blk = 0;
         bool ok = true;
@@ -705,45 +606,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(cnte0 + 8 * (blk & 1u));
-            // outputs (stores by valid lanes; the intensity step is warp-collective)
-            const float mu = static_cast<float>(dmin) + st.mu;
+            // outputs; the photon count goes to bg, where k_intensity_tc reads it for the intensity step
             if (valid) {
-                a.mu[p] = mu;
+                a.mu[p] = static_cast<float>(dmin) + st.mu;
                 a.var[p] = st.M2 / st.W;
                 if (a.argmax) a.argmax[p] = dmin + st.bidx;
-            }
-            if (a.refl) {
-                const bool present = valid && (a.present_now ? a.present_now[p] != 0 : true);
-                const bool need = valid && !faulty && present && K > 0.f && hsum > 0.f;
-                float r = 0.f, b = 0.f;
-                if (__any_sync(0xffffffffu, need)) {
-                    int t0 = 0;
-                    if (need) {
-                        const int rm = __float2int_rn(fminf(fmaxf(mu, 0.f), static_cast<float>(T)));
-                        t0 = min(max(rm - a.peak, 0), T - L);  // template at round-half-even(mu)
-                    }
-                    const int t0a = t0 & ~7;
-                    const uint4* row = reinterpret_cast<const uint4*>(static_cast<const __half*>(a.z) +
-                                                                      (valid ? p : 0) * a.pitch + t0a);
-                    const uint32_t win = lane_base + kWinCol;
-#pragma unroll 1
-                    for (int ch = 0; ch < LCH; ++ch) {
-                        const uint4 v = need && t0a + 8 * ch < T ? __ldg(row + ch) : make_uint4(0u, 0u, 0u, 0u);
-                        tmem_st4(win + 4 * ch, v);
-                    }
-                    tmem_wait_st();
-                    intensity_lanes<LCH>(win, t0 - t0a, need, K, L, T, hsum, s_a, r, b);
-                }
-                if (valid) {
-                    if (faulty) {
-                        r = b = 0.f;
-                    } else if (!need) {
-                        r = 0.f;
-                        b = K / static_cast<float>(T);
-                    }
-                    a.refl[p] = r;
-                    a.bg[p] = b;
-                }
+                if (a.refl) a.bg[p] = K;
             }
         }
     }
@@ -752,6 +620,66 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (warp == 5) {
         fence_after();
         tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// Intensity step of Sec. II-E after k_filter_tc, one warp per pixel: b = K / T and r = 0 for a pixel that is
+// not present, r = b = 0 for a faulty one, else the MLE of (r, b) under Eq. lik_bg_poisson with the template at
+// round-half-even(mu) (px::intensity_mle over the L-bin window, read from the FP16 row). K, the photon count
+// that the tensor cores accumulated, arrives in bg and is replaced by b. Kept out of the fused kernel: a solve
+// there holds the whole 128-pixel block and stalls the MMA pipeline until its slowest pixel converges.
+__global__ void __launch_bounds__(256) k_intensity_tc(const EstimateArgs a) {
+    __shared__ float as[SPL_MAX_TAPS];
+    __shared__ float s_hsum;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < SPL_MAX_TAPS; j += blockDim.x) {
+        const float hj = j < a.L ? a.h[j] : 0.f;
+        as[j] = hj > 0.f ? hj : 0.f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float sum = 0.f;
+        for (int j = lane; j < a.L; j += 32) sum += as[j];
+        sum = px::warp_sum(sum);
+        if (lane == 0) s_hsum = sum;
+    }
+    __syncthreads();
+    const float hsum = s_hsum;
+    if (hsum > 0.f)
+        for (int j = threadIdx.x; j < a.L; j += blockDim.x) as[j] /= hsum;
+    __syncthreads();
+    const long long P = static_cast<long long>(a.H) * a.W;
+    const long long stride = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
+    const int T = a.T, L = a.L;
+    const __half* z = static_cast<const __half*>(a.z);
+    for (long long p = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + warp; p < P; p += stride) {
+        const float K = a.bg[p];
+        const float mu = a.mu[p];
+        const bool faulty = a.faulty ? a.faulty[p] != 0 : false;
+        const bool present = a.present_now ? a.present_now[p] != 0 : true;
+        float r = 0.f, b = 0.f;
+        if (faulty) {
+            r = b = 0.f;
+        } else if (!present || !(K > 0.f) || !(hsum > 0.f)) {
+            r = 0.f;
+            b = K / static_cast<float>(T);
+        } else {
+            const int rm = __float2int_rn(fminf(fmaxf(mu, 0.f), static_cast<float>(T)));
+            const int t0 = min(max(rm - a.peak, 0), T - L);  // template at round-half-even(mu)
+            float zj[SPL_MAX_TAPS / 32], aj[SPL_MAX_TAPS / 32];
+#pragma unroll
+            for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
+                const int j = lane + 32 * q;
+                zj[q] = j < L ? __half2float(z[p * a.pitch + t0 + j]) : 0.f;
+                aj[q] = j < L ? as[j] : 0.f;
+            }
+            px::intensity_mle<SPL_MAX_TAPS / 32>(zj, aj, K, L, T, hsum, r, b);
+        }
+        if (lane == 0) {
+            a.refl[p] = r;
+            a.bg[p] = b;
+        }
+        __syncwarp();
     }
 }
 
@@ -847,12 +775,14 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
 
     CUtensorMap map;
     if ((e = hist_map(&map, a.z, a.pitch, a.T, P)) != cudaSuccess) return e;
-    const int variant = a.L <= 64 ? 0 : 1;
-    auto kern = variant == 0 ? k_filter_tc<9> : k_filter_tc<17>;
-    if ((e = prepare_kernel(dev, variant, reinterpret_cast<const void*>(kern), smem)) != cudaSuccess) return e;
+    if ((e = prepare_kernel(dev, 0, reinterpret_cast<const void*>(k_filter_tc), smem)) != cudaSuccess) return e;
     const long long want = static_cast<long long>(nsm) * per_sm;
     const int grid = static_cast<int>(g.npt < want ? g.npt : want);
-    kern<<<grid, kThreads, smem, s>>>(map, a, g, status);
+    k_filter_tc<<<grid, kThreads, smem, s>>>(map, a, g, status);
+    if ((e = cudaGetLastError()) != cudaSuccess || !a.refl) return e;
+    const long long blocks = (P + 7) / 8;  // one warp per pixel, 8 warps per block, at most 8 blocks per SM
+    const long long cap = static_cast<long long>(nsm) * 8;
+    k_intensity_tc<<<static_cast<unsigned>(blocks < cap ? blocks : cap), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
