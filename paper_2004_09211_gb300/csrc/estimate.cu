@@ -1,6 +1,7 @@
 // Fused per-pixel kernel over photon-count histograms: robust data term (Eq. beta_div2), pseudo-posterior on the
-// depth grid (Eq. approx_post) with the spatio-temporal Gaussian-mixture prior (Eq. predict), moment matching
-// (Eq. KL_div), and the background/reflectivity estimate (Sec. II-E).
+// depth grid (Eq. approx_post) with the spatio-temporal Gaussian-mixture prior (Eq. predict) and moment matching
+// (Eq. KL_div). It leaves each pixel's photon count in bg; the background/reflectivity estimate (Sec. II-E) is a
+// separate launch (intensity.cu).
 //
 // Mapping. One warp owns one pixel at a time (persistent grid-stride loop over pixels). While a pixel is
 // processed, the next pixel's histogram row is copied into the warp's shared-memory slice with cp.async and its
@@ -8,10 +9,10 @@
 //
 // Correlation. C(d) = sum_j g_j z[d - peak + j] (g = h^beta) for every candidate, into shared memory. A row
 // with few non-empty bins (photon-starved data) is correlated from a compacted list of those bins (exact zero
-// skip: each lane accumulates a contiguous run of candidates from the bins that reach it); a denser row uses
+// skip: lane = candidate, four 32-candidate blocks per pass over the bins that reach them); a denser row uses
 // a register-blocked direct sum (8 candidates per lane, taps in groups of 4).
 //
-// The pseudo-posterior moments and the intensity MLE are in pixel.cuh (shared with the photon-list kernel).
+// The pseudo-posterior moments are in pixel.cuh (shared with the photon-list kernel).
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -326,35 +327,23 @@ template <int FMT, bool COST_ONLY>
 __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     extern __shared__ __align__(16) float dyn[];
     __shared__ __align__(16) float gs[SPL_MAX_TAPS + 4];  // g_j = h_j^beta (0 for taps <= 0 and for j >= L)
-    __shared__ float as[SPL_MAX_TAPS];                     // h_j / sum(h): normalised template (intensity)
-    __shared__ float s_hsum, s_gmax;
+    __shared__ float s_gmax;
     constexpr int CB = FMT == SPL_HIST_F32 ? 4 : 8;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int j = threadIdx.x; j < SPL_MAX_TAPS + 4; j += blockDim.x) {
         const float hj = j < a.L ? a.h[j] : 0.f;
         gs[j] = hj > 0.f ? powf(hj, a.beta) : 0.f;
-        if (j < SPL_MAX_TAPS) as[j] = hj > 0.f ? hj : 0.f;
     }
     __syncthreads();
     if (warp == 0) {
-        float s = 0.f, g = 0.f;
-        for (int j = lane; j < a.L; j += 32) {
-            s += as[j];
-            g = fmaxf(g, gs[j]);
-        }
-        s = warp_sum(s);
+        float g = 0.f;
+        for (int j = lane; j < a.L; j += 32) g = fmaxf(g, gs[j]);
         g = warp_max(g);
-        if (lane == 0) {
-            s_hsum = s;
-            s_gmax = g;
-        }
+        if (lane == 0) s_gmax = g;
     }
     __syncthreads();
-    const float hsum = s_hsum, gmax = s_gmax;
-    if (hsum > 0.f)
-        for (int j = threadIdx.x; j < a.L; j += blockDim.x) as[j] /= hsum;
-    __syncthreads();
+    const float gmax = s_gmax;
 
     const int T = a.T, L = a.L, D = a.D, u0 = a.dmin - a.peak, NB = (D + 31) >> 5;
     const Slice sl = make_slice(T, D, CB);
@@ -486,31 +475,9 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             if (a.argmax) a.argmax[p] = a.dmin + bidx;
         }
 
-        // ---- 5. background b and reflectivity r (Sec. II-E) ----
-        if (a.refl) {
-            float r = 0.f, b = 0.f;
-            const bool present = a.present_now ? a.present_now[p] != 0 : true;
-            if (faulty) {
-                r = b = 0.f;
-            } else if (!present || !(K > 0.f) || !(hsum > 0.f)) {
-                r = 0.f;
-                b = K / static_cast<float>(T);
-            } else {
-                const int t0 = min(max(__float2int_rn(mu) - a.peak, 0), T - L);  // template at round(mu)
-                float zj[SPL_MAX_TAPS / 32], aj[SPL_MAX_TAPS / 32];
-#pragma unroll
-                for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
-                    const int j = lane + 32 * q;
-                    zj[q] = j < L ? bin_value<FMT>(raw, t0 + j) : 0.f;
-                    aj[q] = j < L ? as[j] : 0.f;
-                }
-                intensity_mle<SPL_MAX_TAPS / 32>(zj, aj, K, L, T, hsum, r, b);
-            }
-            if (lane == 0) {
-                a.refl[p] = r;
-                a.bg[p] = b;
-            }
-        }
+        // ---- 5. background b and reflectivity r (Sec. II-E): a separate launch (intensity.cu) solves them; the
+        // photon count goes to bg for it ----
+        if (a.refl && lane == 0) a.bg[p] = K;
         __syncwarp();
     }
     cp_async_wait_all();  // no copy may still target this CTA's shared memory when it exits
@@ -566,16 +533,22 @@ cudaError_t launch_t(const EstimateArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_estimate(const EstimateArgs& a, bool cost_only, cudaStream_t s) {
+    cudaError_t e;
     switch (a.fmt) {
         case SPL_HIST_U16:
-            return cost_only ? launch_t<SPL_HIST_U16, true>(a, s) : launch_t<SPL_HIST_U16, false>(a, s);
+            e = cost_only ? launch_t<SPL_HIST_U16, true>(a, s) : launch_t<SPL_HIST_U16, false>(a, s);
+            break;
         case SPL_HIST_F16:
-            return cost_only ? launch_t<SPL_HIST_F16, true>(a, s) : launch_t<SPL_HIST_F16, false>(a, s);
+            e = cost_only ? launch_t<SPL_HIST_F16, true>(a, s) : launch_t<SPL_HIST_F16, false>(a, s);
+            break;
         case SPL_HIST_F32:
-            return cost_only ? launch_t<SPL_HIST_F32, true>(a, s) : launch_t<SPL_HIST_F32, false>(a, s);
+            e = cost_only ? launch_t<SPL_HIST_F32, true>(a, s) : launch_t<SPL_HIST_F32, false>(a, s);
+            break;
         default:
             return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess || cost_only || !a.refl) return e;
+    return launch_intensity(a, s);  // reads K from bg, writes refl and bg
 }
 
 }  // namespace spl

@@ -64,6 +64,8 @@ cudaError_t launch_pi_propagate(int H, int W, const float* nu, const float* pi_i
 // Tensor-core correlation (tc.cu).
 cudaError_t launch_cost_tc(const spl_params* q, const void* z, long long pitch, const float* h, float* cost,
                            int* argmax, unsigned* status, cudaStream_t s);
+// Intensity step of Sec. II-E after a depth kernel that left each pixel's photon count in a.bg (intensity.cu).
+cudaError_t launch_intensity(const EstimateArgs& a, cudaStream_t s);
 // Filter step with the data term on the tensor cores (tcfilter.cu); a.z holds FP16 histograms.
 cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream_t s);
 unsigned* tc_status_ptr();

@@ -22,8 +22,8 @@
 //             own moments taken about its best candidate (the pairwise update of Chan, Golub and LeVeque), so
 //             no step subtracts large nearly equal numbers.
 //     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax; the photon count K goes to bg.
-// A second kernel, k_intensity_tc (one warp per pixel), then runs the intensity MLE of Sec. II-E on the template at
-// round-half-even(mu) with that K and writes refl and bg.
+// A second launch (intensity.cu) then runs the intensity MLE of Sec. II-E on the template at round-half-even(mu)
+// with that K and writes refl and bg.
 // All mbarrier waits are bounded (status bit 0 on time-out; the roles then stop, in-flight copies and MMAs are
 // waited for, tensor memory is released).
 #include <math.h>
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(cnte0 + 8 * (blk & 1u));
-            // outputs; the photon count goes to bg, where k_intensity_tc reads it for the intensity step
+            // outputs; the photon count goes to bg, where the intensity launch reads it
             if (valid) {
                 a.mu[p] = static_cast<float>(dmin) + st.mu;
                 a.var[p] = st.M2 / st.W;
@@ -620,198 +620,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (warp == 5) {
         fence_after();
         tmem_dealloc(tmem, kTmemCols);
-    }
-}
-
-// Intensity step of Sec. II-E after k_filter_tc, one warp per pixel: b = K / T and r = 0 for a pixel that is
-// not present, r = b = 0 for a faulty one, else the MLE of (r, b) under Eq. lik_bg_poisson with the template at
-// round-half-even(mu) (px::intensity_mle over the L-bin window, read from the FP16 row). K, the photon count
-// that the tensor cores accumulated, arrives in bg and is replaced by b. Kept out of the fused kernel: a solve
-// there holds the whole 128-pixel block and stalls the MMA pipeline until its slowest pixel converges.
-// Sum over the 8 lanes of this lane's group (lanes 8 g .. 8 g + 7).
-__device__ __forceinline__ float group8_sum(float v) {
-#pragma unroll
-    for (int o = 4; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// The intensity MLE of px::intensity_mle for four pixels per warp, one per group of 8 lanes (templates of at most
-// 64 taps: lane s of a group holds bins s + 8 q, q < 8). The groups iterate together (the shuffles are warp-wide)
-// until every group has converged; a converged group keeps its f.
-__device__ __forceinline__ void intensity_mle_g8(const float* zj, const float* aj, float K, int L, int T, float hsum,
-                                                 bool need, float& r, float& b) {
-    const float u = 1.f / static_cast<float>(T);
-    float kin = 0.f, za = 0.f, p1 = 0.f;
-    bool zero_tap = false;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        kin += zj[q];
-        za = fmaf(zj[q], aj[q], za);
-        if (zj[q] > 0.f) {
-            if (aj[q] > 0.f) p1 += zj[q] * __fdividef(aj[q] - u, aj[q]);
-            else zero_tap = true;
-        }
-    }
-    kin = group8_sum(kin);
-    za = group8_sum(za);
-    p1 = group8_sum(p1);
-    const unsigned zt = __ballot_sync(0xffffffffu, zero_tap);
-    zero_tap = ((zt >> (threadIdx.x & 24)) & 0xffu) != 0;
-    const float kout = fmaxf(K - kin, 0.f);
-    const float psi0 = static_cast<float>(T) * za - K;
-    float f = 0.f, lo = 0.f, hi = 1.f;
-    bool active = false;
-    if (!need || !(psi0 > 0.f)) {
-        f = 0.f;
-    } else if (!(kout > 0.f) && !zero_tap && p1 >= 0.f) {
-        f = 1.f;
-    } else {
-        const float fr = static_cast<float>(L) * u;
-        f = fr < 1.f ? (kin - K * fr) / (K * (1.f - fr)) : 0.5f;
-        f = fminf(fmaxf(f, 0.02f), 0.98f);
-        active = true;
-    }
-    for (int it = 0; it < 64; ++it) {
-        if (!__any_sync(0xffffffffu, active)) break;
-        float gs = 0.f, gp = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (zj[q] > 0.f) {
-                const float e = __fdividef(aj[q] - u, fmaf(f, aj[q] - u, u));
-                gs = fmaf(zj[q], e, gs);
-                gp = fmaf(zj[q] * e, e, gp);
-            }
-        }
-        gs = group8_sum(gs);
-        gp = group8_sum(gp);
-        if (active) {
-            const float rom = __fdividef(1.f, 1.f - f);
-            gs = fmaf(-kout, rom, gs);
-            gp = fmaf(kout * rom, rom, gp);
-            if (gs > 0.f) lo = f; else hi = f;
-            float fn = f + __fdividef(gs, gp);
-            if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
-            const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
-            f = fn;
-            if (conv) active = false;
-        }
-    }
-    r = f * K / hsum;
-    b = (1.f - f) * K * u;
-}
-
-// Four pixels per warp (templates of at most 64 taps): the rules of k_intensity_tc with intensity_mle_g8.
-__global__ void __launch_bounds__(256) k_intensity_tc4(const EstimateArgs a) {
-    __shared__ float as[64];
-    __shared__ float s_hsum;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, sl = lane & 7;
-    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-        const float hj = j < a.L ? a.h[j] : 0.f;
-        as[j] = hj > 0.f ? hj : 0.f;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        float sum = 0.f;
-        for (int j = lane; j < a.L; j += 32) sum += as[j];
-        sum = px::warp_sum(sum);
-        if (lane == 0) s_hsum = sum;
-    }
-    __syncthreads();
-    const float hsum = s_hsum;
-    if (hsum > 0.f)
-        for (int j = threadIdx.x; j < a.L; j += blockDim.x) as[j] /= hsum;
-    __syncthreads();
-    const long long P = static_cast<long long>(a.H) * a.W;
-    const long long stride = 4LL * gridDim.x * (blockDim.x >> 5);
-    const int T = a.T, L = a.L;
-    const __half* z = static_cast<const __half*>(a.z);
-    for (long long p0 = 4LL * (static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + warp); p0 < P; p0 += stride) {
-        const long long p = p0 + grp;
-        const bool valid = p < P;
-        const float K = valid ? a.bg[p] : 0.f;
-        const bool faulty = valid && a.faulty ? a.faulty[p] != 0 : false;
-        const bool present = valid && (a.present_now ? a.present_now[p] != 0 : true);
-        const bool need = valid && !faulty && present && K > 0.f && hsum > 0.f;
-        float zj[8], aj[8];
-        int t0 = 0;
-        if (need) {
-            const int rm = __float2int_rn(fminf(fmaxf(a.mu[p], 0.f), static_cast<float>(T)));
-            t0 = min(max(rm - a.peak, 0), T - L);  // template at round-half-even(mu)
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int j = sl + 8 * q;
-            zj[q] = need && j < L ? __half2float(z[p * a.pitch + t0 + j]) : 0.f;
-            aj[q] = j < L ? as[j] : 0.f;
-        }
-        float r = 0.f, b = 0.f;
-        intensity_mle_g8(zj, aj, K, L, T, hsum, need, r, b);
-        if (valid && sl == 0) {
-            if (faulty) {
-                r = b = 0.f;
-            } else if (!need) {
-                r = 0.f;
-                b = K / static_cast<float>(T);
-            }
-            a.refl[p] = r;
-            a.bg[p] = b;
-        }
-        __syncwarp();
-    }
-}
-
-__global__ void __launch_bounds__(256) k_intensity_tc(const EstimateArgs a) {
-    __shared__ float as[SPL_MAX_TAPS];
-    __shared__ float s_hsum;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < SPL_MAX_TAPS; j += blockDim.x) {
-        const float hj = j < a.L ? a.h[j] : 0.f;
-        as[j] = hj > 0.f ? hj : 0.f;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        float sum = 0.f;
-        for (int j = lane; j < a.L; j += 32) sum += as[j];
-        sum = px::warp_sum(sum);
-        if (lane == 0) s_hsum = sum;
-    }
-    __syncthreads();
-    const float hsum = s_hsum;
-    if (hsum > 0.f)
-        for (int j = threadIdx.x; j < a.L; j += blockDim.x) as[j] /= hsum;
-    __syncthreads();
-    const long long P = static_cast<long long>(a.H) * a.W;
-    const long long stride = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
-    const int T = a.T, L = a.L;
-    const __half* z = static_cast<const __half*>(a.z);
-    for (long long p = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + warp; p < P; p += stride) {
-        const float K = a.bg[p];
-        const float mu = a.mu[p];
-        const bool faulty = a.faulty ? a.faulty[p] != 0 : false;
-        const bool present = a.present_now ? a.present_now[p] != 0 : true;
-        float r = 0.f, b = 0.f;
-        if (faulty) {
-            r = b = 0.f;
-        } else if (!present || !(K > 0.f) || !(hsum > 0.f)) {
-            r = 0.f;
-            b = K / static_cast<float>(T);
-        } else {
-            const int rm = __float2int_rn(fminf(fmaxf(mu, 0.f), static_cast<float>(T)));
-            const int t0 = min(max(rm - a.peak, 0), T - L);  // template at round-half-even(mu)
-            float zj[SPL_MAX_TAPS / 32], aj[SPL_MAX_TAPS / 32];
-#pragma unroll
-            for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
-                const int j = lane + 32 * q;
-                zj[q] = j < L ? __half2float(z[p * a.pitch + t0 + j]) : 0.f;
-                aj[q] = j < L ? as[j] : 0.f;
-            }
-            px::intensity_mle<SPL_MAX_TAPS / 32>(zj, aj, K, L, T, hsum, r, b);
-        }
-        if (lane == 0) {
-            a.refl[p] = r;
-            a.bg[p] = b;
-        }
-        __syncwarp();
     }
 }
 
@@ -912,13 +720,7 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
     const int grid = static_cast<int>(g.npt < want ? g.npt : want);
     k_filter_tc<<<grid, kThreads, smem, s>>>(map, a, g, status);
     if ((e = cudaGetLastError()) != cudaSuccess || !a.refl) return e;
-    const long long px_per_block = a.L <= 64 ? 32 : 8;  // 8 warps of 4 pixels (L <= 64) or of 1 pixel
-    const long long blocks = (P + px_per_block - 1) / px_per_block;
-    const long long cap = static_cast<long long>(nsm) * 8;  // at most 8 blocks of 256 threads per SM
-    const unsigned nb = static_cast<unsigned>(blocks < cap ? blocks : cap);
-    if (a.L <= 64) k_intensity_tc4<<<nb, 256, 0, s>>>(a);
-    else k_intensity_tc<<<nb, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_intensity(a, s);
 }
 
 }  // namespace spl
