@@ -42,17 +42,17 @@ SEED = 2
 WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.1,1} x beta {0.2,0.5,1}"
 
 
-# DRAM bytes (read + write) per launch of each workload's dominant kernel, from one ncu capture of that kernel
-# (the full-size launch, or a smaller launch scaled by the pixels processed where the full one is too large to
-# capture), valid only for the exact kernel sources it was taken on: the bench reports null for "traffic" when
-# the sources' hash differs.
+# DRAM bytes (read + write) per filter step of each workload's dominant kernel (its depth launch plus the
+# intensity launch after it), from one ncu capture of both (a 256 x 256 frame, scaled by the pixels processed),
+# valid only for the exact kernel sources it was taken on: the bench reports null for "traffic" when the
+# sources' hash differs.
 TRAFFIC_CAPTURES = {
-    "k_estimate": {"sources": ("estimate.cu", "pixel.cuh"),
-                   "sha256": "7fba7a62574d59a268ff7304a1393940b778a0f5ff4684dd304eed1d999b2a91",
-                   "bytes_per_pixel": 201.55e6 / 65536},
-    "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh"),
-                    "sha256": "e28bd2fec48f8c9d9720055e3eb9797d42510f1116a5f3384f11662c9b41c1a2",
-                    "bytes_per_pixel": 555.17e6 / 65536},
+    "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "intensity.cu"),
+                   "sha256": "bc47459e80c75f107c0c7ad0009c8c427aca9412b0d999a2c2e017c482d885e0",
+                   "bytes_per_pixel": (201.53e6 + 15.08e6) / 65536},
+    "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu"),
+                    "sha256": "dfefbf8b3c285e505b2b06ac75890b0f6af4deabed0f3e0c1b48a12d0b8df6ae",
+                    "bytes_per_pixel": (542.04e6 + 17.19e6) / 65536},
 }
 
 
