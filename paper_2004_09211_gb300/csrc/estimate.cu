@@ -9,8 +9,8 @@
 //
 // Correlation. C(d) = sum_j g_j z[d - peak + j] (g = h^beta) for every candidate, into shared memory. A row
 // with few non-empty bins (photon-starved data) is correlated from a compacted list of those bins (exact zero
-// skip: lane = candidate, four 32-candidate blocks per pass over the bins that reach them); a denser row uses
-// a register-blocked direct sum (8 candidates per lane, taps in groups of 4).
+// skip: lane = tap, each bin added into the L candidates it reaches); a denser row uses a register-blocked
+// direct sum (8 candidates per lane, taps in groups of 4).
 //
 // The pseudo-posterior moments are in pixel.cuh (shared with the photon-list kernel).
 #include <cuda_fp16.h>
@@ -26,15 +26,15 @@ namespace {
 
 using namespace px;
 
-constexpr int kNnzSparse = 320;  // capacity of the packed non-empty-bin list
-constexpr int kLaneNnz = 64;     // zero-skip correlation up to this many non-empty bins, dense tap sum above
+constexpr int kTapNnz = 128;  // zero-skip correlation up to this many non-empty bins (list capacity), dense above
 
 // Shared-memory slice of one warp (all offsets in 4-byte words; every array starts 16-byte aligned).
 struct Slice {
     int nch;     // 16-byte chunks per row
     int rawsz;   // words per staging buffer: nch * 4 + 16 zero words (windows read up to 11 bins past T)
     int raw;     // two staging buffers (cp.async targets): the current pixel's row and the next one's
-    int ent;     // non-empty bins packed as (bin << 16 | count), kNnzSparse entries
+    int ebin;    // non-empty bins of a sparse row, in bin order (kTapNnz words)
+    int eval;    // their counts (kTapNnz words)
     int cps;     // photon-count prefix over chunks, nch + 1 words
     int cpe;     // non-empty-bin prefix over chunks, nch + 1 words
     int ubs;     // per-block upper bounds, NB words
@@ -50,8 +50,9 @@ __host__ __device__ __forceinline__ Slice make_slice(int T, int D, int cb) {
     const int nb = (D + 31) / 32;
     s.rawsz = s.nch * 4 + 16;
     s.raw = 0;
-    s.ent = 2 * s.rawsz;
-    s.cps = s.ent + kNnzSparse;
+    s.ebin = 2 * s.rawsz;
+    s.eval = s.ebin + kTapNnz;
+    s.cps = s.eval + kTapNnz;
     s.cpe = s.cps + round4(s.nch + 1);
     s.ubs = s.cpe + round4(s.nch + 1);
     s.cs = s.ubs + round4(nb);
@@ -256,47 +257,41 @@ __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const 
     return warp_max(mx);
 }
 
-// Sparse rows (at most kLaneNnz non-empty bins): lane = candidate, four 32-candidate blocks per pass over the
-// packed bins whose chunks meet the four blocks' window. Every lane runs the same photon loop (no divergence) with
-// four independent accumulators; a tap index outside 0 .. L-1 reads gs[L] = 0. Returns max C.
-__device__ __forceinline__ float corr_lanes(const float* __restrict__ gs, const unsigned* ent, const int* cpe,
-                                           float* cs, int NB, int D, int L, int u0, int cb, int nch, int lane) {
+// Sparse rows (at most kTapNnz non-empty bins, listed in bin order): lane l owns the taps j = l + 32 k (k < 4) and
+// adds z_t g_j into candidate t - u0 - j for each listed bin t in turn. The candidates of one bin are distinct
+// across lanes and taps, and the warp synchronises between bins, so every C(d) is summed in bin order (the same
+// in every run). Taps j >= L hold g_j = 0. Returns max C (every partial sum is <= its final value).
+__device__ __forceinline__ float corr_taps(const float* __restrict__ gs, const int* ebin, const float* eval, int nnz,
+                                          float* cs, int NB, int D, int L, int u0, int lane) {
+    constexpr int KG = SPL_MAX_TAPS / 32;
+    zero_words(cs, NB * 8, lane);
+    float g[KG];
+#pragma unroll
+    for (int k = 0; k < KG; ++k) g[k] = gs[lane + 32 * k];
+    const int ntg = (L + 31) >> 5;
+    const int off = -u0 - lane;
     float mx = 0.f;
-    for (int b0 = 0; b0 < NB; b0 += 4) {
-        const int nblk = min(4, NB - b0);
-        const int c0 = 32 * b0 + lane;
-        const int ch_lo = (u0 + 32 * b0) / cb;
-        const int ch_hi = min((u0 + 32 * (b0 + nblk) - 1 + L - 1) / cb + 1, nch);
-        const int e_lo = cpe[ch_lo], e_hi = cpe[ch_hi];
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int e = e_lo; e < e_hi; ++e) {
-            const unsigned en = ent[e];
-            const int base = static_cast<int>(en >> 16) - u0 - c0;
-            const float z = static_cast<float>(en & 0xffffu);
+    for (int e = 0; e < nnz; ++e) {
+        const int c = ebin[e] + off;
+        const float z = eval[e];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int j = base - 32 * k;
-                acc[k] = fmaf(z, gs[static_cast<unsigned>(j) < static_cast<unsigned>(L) ? j : L], acc[k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (k < nblk) {
-                const int c = c0 + 32 * k;
-                const float v = c < D ? acc[k] : 0.f;
-                cs[c] = v;
+        for (int k = 0; k < KG; ++k) {
+            const int ck = c - 32 * k;
+            if (k < ntg && static_cast<unsigned>(ck) < static_cast<unsigned>(D)) {
+                const float v = fmaf(z, g[k], cs[ck]);
+                cs[ck] = v;
                 mx = fmaxf(mx, v);
             }
         }
+        __syncwarp();
     }
-    __syncwarp();
     return warp_max(mx);
 }
 
-// C(d) for all candidates of one pixel (staged row in raw, prefix sums in cps/cpe). Returns max C. Zero skip
-// needs every count below 2^16 (packed entries); `sparse_ok` says so.
+// C(d) for all candidates of one pixel (staged row in raw, non-empty-bin prefix over chunks in cpe). Returns
+// max C. `sparse`: the row has at most kTapNnz non-empty bins.
 template <int FMT, int CB>
-__device__ __forceinline__ float correlate(const float* __restrict__ gs, const float* raw, unsigned* ent,
+__device__ __forceinline__ float correlate(const float* __restrict__ gs, const float* raw, int* ebin, float* eval,
                                            const int* cpe, float* cs, int nch, int T, bool empty, bool sparse,
                                            int NB, int D, int L, int u0, int lane) {
     if (empty) {
@@ -311,10 +306,13 @@ __device__ __forceinline__ float correlate(const float* __restrict__ gs, const f
             convert_chunk<FMT>(raw, i, T, f);
 #pragma unroll
             for (int k = 0; k < CB; ++k)
-                if (f[k] != 0.f) ent[o++] = (static_cast<unsigned>(i * CB + k) << 16) | static_cast<unsigned>(f[k]);
+                if (f[k] != 0.f) {
+                    ebin[o] = i * CB + k;
+                    eval[o++] = f[k];
+                }
         }
         __syncwarp();
-        return corr_lanes(gs, ent, cpe, cs, NB, D, L, u0, CB, nch, lane);
+        return corr_taps(gs, ebin, eval, cpe[nch], cs, NB, D, L, u0, lane);
     }
     return corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
 }
@@ -348,7 +346,8 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     const int T = a.T, L = a.L, D = a.D, u0 = a.dmin - a.peak, NB = (D + 31) >> 5;
     const Slice sl = make_slice(T, D, CB);
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
-    unsigned* ent = reinterpret_cast<unsigned*>(base + sl.ent);
+    int* ebin = reinterpret_cast<int*>(base + sl.ebin);
+    float* eval = base + sl.eval;
     float* cps = base + sl.cps;
     int* cpe = reinterpret_cast<int*>(base + sl.cpe);
     float* ubs = base + sl.ubs;
@@ -386,7 +385,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         }
 
         // ---- 1. per-chunk photon and non-empty-bin counts of the staged row ----
-        float K = 0.f, zmax = 0.f;
+        float K = 0.f;
         int nnz = 0;
         if (!faulty) {
             for (int i = lane; i < sl.nch; i += 32) {
@@ -398,7 +397,6 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
                 for (int k = 0; k < CB; ++k) {
                     s += f[k];
                     c += f[k] != 0.f;
-                    zmax = fmaxf(zmax, f[k]);
                 }
                 cps[i] = s;
                 cpe[i] = c;
@@ -407,15 +405,15 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             }
             K = warp_sum(K);
             nnz = static_cast<int>(warp_sum(static_cast<float>(nnz)));
-            zmax = warp_max(zmax);
             __syncwarp();
             warp_scan2(cps, cpe, sl.nch, lane);
         }
         const bool empty = faulty || nnz == 0;
-        const bool sparse = nnz <= kLaneNnz && zmax < 65536.f;
+        const bool sparse = nnz <= kTapNnz;
 
         // ---- 2. C(d) for every candidate ----
-        const float cmax = correlate<FMT, CB>(gs, raw, ent, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane);
+        const float cmax =
+            correlate<FMT, CB>(gs, raw, ebin, eval, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane);
 
         if (COST_ONLY) {
             float best = -INFINITY;
@@ -467,8 +465,10 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         float mu, var;
         posterior(
             grid, pr, cmax, empty, cs, ubs, [&](int s_bin, int e_bin) { return cps[e_bin / CB + 1] - cps[s_bin / CB]; },
-            [&]() { correlate<FMT, CB>(gs, raw, ent, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane); }, lane,
-            bidx, mu, var);
+            [&]() {
+                correlate<FMT, CB>(gs, raw, ebin, eval, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane);
+            },
+            lane, bidx, mu, var);
         if (lane == 0) {
             a.mu[p] = mu;
             a.var[p] = var;
