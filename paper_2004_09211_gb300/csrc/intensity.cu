@@ -117,12 +117,17 @@ __device__ __forceinline__ void intensity_mle_g8(const float* zj, const float* a
             const float rom = __fdividef(1.f, 1.f - f);
             gs = fmaf(-kout, rom, gs);
             gp = fmaf(kout * rom, rom, gp);
-            if (gs > 0.f) lo = f; else hi = f;
-            float fn = f + __fdividef(gs, gp);  // Newton step on psi (psi' = -gp)
-            if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
-            const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
-            f = fn;
-            if (conv) active = false;
+            const float step = __fdividef(gs, gp);  // Newton step on psi (psi' = -gp)
+            if (fabsf(step) <= px::kNewtonTol * f) {  // converged (tested before the bracket update)
+                f += step;
+                active = false;
+            } else {
+                if (gs > 0.f) lo = f; else hi = f;
+                float fn = f + step;
+                if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
+                if (hi - lo <= 1e-7f * hi) active = false;
+                f = fn;
+            }
         }
     }
     r = f * K / hsum;

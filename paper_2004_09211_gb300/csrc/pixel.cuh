@@ -37,6 +37,11 @@ constexpr float kLog2TwoPi = 2.6514961294723187f;  // log2(2 pi)
 constexpr int kMaxComp = 9;                         // at most 9 distinct components (3x3 stencil)
 constexpr float kPrune2 = 64.f;                     // log2 margin below the best value for dropping a block
 constexpr int kRestart = 16;                        // exact restart interval of the mixture recurrences
+// Newton on the signal fraction stops once its step is below this fraction of f: the error after that step is of
+// the order of the step squared, below FP32 resolution. The test comes before the bracket update: at the root,
+// psi's rounding noise can put the next iterate on the bracket's end, and a bisection from there would throw away
+// a converged f.
+constexpr float kNewtonTol = 1e-5f;
 
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -419,10 +424,15 @@ __device__ __forceinline__ void intensity_mle(const float* zj, const float* aj, 
             const float rom = __fdividef(1.f, 1.f - f);
             gs = fmaf(-kout, rom, gs);
             gp = fmaf(kout * rom, rom, gp);
+            const float step = __fdividef(gs, gp);  // Newton step on psi (psi' = -gp)
+            if (fabsf(step) <= kNewtonTol * f) {  // converged (tested before the bracket: see kNewtonTol)
+                f += step;
+                break;
+            }
             if (gs > 0.f) lo = f; else hi = f;
-            float fn = f + __fdividef(gs, gp);  // Newton step on psi (psi' = -gp)
+            float fn = f + step;
             if (!(fn > lo && fn < hi)) fn = 0.5f * (lo + hi);
-            const bool conv = fabsf(fn - f) <= 1e-6f * fn || hi - lo <= 1e-7f * hi;
+            const bool conv = hi - lo <= 1e-7f * hi;
             f = fn;
             if (conv) break;
         }
