@@ -216,6 +216,34 @@ def test_ragged_shapes(orc, H, W, T, L, peak, dmin, dmax):
     _run_filter(orc, q, prm, h, [z, z[::-1].copy()], T)
 
 
+@pytest.mark.parametrize("L,peak,bg", [
+    (33, 12, 0.02),    # two tap groups of 32, the second with one tap
+    (100, 40, 0.05),   # four tap groups
+    (128, 90, 0.1),    # largest supported IRF
+    (48, 20, 0.135),   # 110-140 non-empty bins: both sides of the zero-skip limit (128)
+])
+def test_sparse_rows_long_templates(orc, L, peak, bg):
+    """Photon-starved rows (zero-skip correlation) with templates over several groups of 32 taps."""
+    H, W, T = 4, 33, 900
+    rng = np.random.default_rng(L * 7 + 1)
+    h = rng.uniform(0.0, 1.0, size=L).astype(np.float32)
+    h[peak] = 2.0
+    h /= h.sum()
+    q = orc.params(T, L, peak, beta=0.4, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    z = rng.poisson(bg, size=(H, W, T)).astype(np.float64)
+    for y in range(H):
+        for x in range(W):
+            d = int(rng.integers(q.dmin, q.dmax + 1))
+            z[y, x, d - peak:d - peak + L] += rng.poisson(4 * h)
+    prm = spl.make_params(H, W, T, L, peak, beta=0.4, sigma_rw2=3.0)
+    cost, am = spl.spl_depth_cost(prm, _gpu_hist(z, T), torch.from_numpy(h).to(DEV))
+    torch.cuda.synchronize()
+    C = orc.cost(q, h, z).reshape(H * W, -1)
+    check_close(_np(cost), C, "C", atol=1e-6 * C.max())
+    check_argmax(_np(am), C.argmax(1) + q.dmin, C, q.dmin)
+    _run_filter(orc, q, prm, h, [z, z[:, ::-1].copy()], T)
+
+
 def test_empty_histograms_give_the_prior(orc):
     """No photons: the GPU posterior moments equal the prior's (and the oracle's)."""
     h, peak = synth.asymmetric_irf(L=48)
