@@ -78,6 +78,9 @@ def lib():
             L.orc_intensity_mle.argtypes = [P, d, d, ct.c_int, d, d]
             L.orc_intensity.argtypes = [P, d, d, ct.c_long, d, i32, u8, u8, d, d]
             L.orc_pi_propagate.argtypes = [ct.c_int, ct.c_int, d, d, u8, d]
+            L.orc_log_lik_ratio.argtypes = [P, d, d, ct.c_int, ct.c_double, ct.c_double]
+            L.orc_log_lik_ratio.restype = ct.c_double
+            L.orc_detect.argtypes = [P, d, d, ct.c_long, d, d, u8, d, d, u8, d, d]
             _lib = L
     return _lib
 
@@ -212,6 +215,30 @@ def intensity(q: Params, h, z, mu, present=None, faulty=None, dr=None):
                         _ptr(drr, ct.c_int32), _ptr(pr, ct.c_uint8), _ptr(fa, ct.c_uint8),
                         _ptr(r, ct.c_double), _ptr(b, ct.c_double))
     return r.reshape(shape), b.reshape(shape)
+
+
+def log_lik_ratio(q: Params, h, z, dr: int, r: float, b: float) -> float:
+    """Log-likelihood ratio of Eq. lik_bg_poisson, (r, b) at template position dr against r = 0, b = K/T."""
+    return float(lib().orc_log_lik_ratio(ct.byref(q), _ptr(_d(h), ct.c_double), _ptr(_d(z), ct.c_double),
+                                         int(dr), float(r), float(b)))
+
+
+def detect(q: Params, h, z, mu, pi0=None, faulty=None):
+    """Detection surrogate (BIC-approximated Bayes factor at the intensity MLE, combined with pi0):
+    dict(pi, llr, present, refl, bg), each shaped like mu."""
+    h, z = _d(h), _d(z)
+    shape = np.shape(mu)
+    P = z.size // q.T
+    m = _d(mu).reshape(-1)
+    p0 = None if pi0 is None else _d(pi0).reshape(-1)
+    fa = _u8(faulty)
+    pi, llr, r, b = (np.empty(P) for _ in range(4))
+    pres = np.empty(P, dtype=np.uint8)
+    lib().orc_detect(ct.byref(q), _ptr(h, ct.c_double), _ptr(z, ct.c_double), P, _ptr(m, ct.c_double),
+                     _ptr(p0, ct.c_double), _ptr(fa, ct.c_uint8), _ptr(pi, ct.c_double), _ptr(llr, ct.c_double),
+                     _ptr(pres, ct.c_uint8), _ptr(r, ct.c_double), _ptr(b, ct.c_double))
+    return dict(pi=pi.reshape(shape), llr=llr.reshape(shape), present=pres.reshape(shape), refl=r.reshape(shape),
+                bg=b.reshape(shape))
 
 
 def pi_propagate(nu, pi_in, faulty=None):

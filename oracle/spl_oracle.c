@@ -23,7 +23,9 @@
  * noiseless templates (Hoelder); invariance of sum s_d^(1+beta) over the domain; a one-photon box-IRF
  * closed form of the posterior moments; posterior = prior on an empty histogram (Gaussian moments);
  * translation equivariance and the dependency cone of the filter; the box-IRF closed form of the intensity
- * MLE and its KKT conditions checked by scipy; the fixed points of Eq. prior_detect.
+ * MLE and its KKT conditions checked by scipy; the fixed points of Eq. prior_detect; for the detection
+ * surrogate, the box-IRF closed form of the two-region Poisson likelihood ratio, the logistic combination with
+ * pi0 and its limits.
  */
 #include <math.h>
 #include <stdint.h>
@@ -346,6 +348,80 @@ void orc_intensity(const orc_params* q, const double* h, const double* z, long P
         }
         const int d = dr ? dr[p] : (int)rint(mu[p]);
         orc_intensity_mle(q, h, zp, d, refl + p, bg + p);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Presence probability: a detection surrogate                                                          */
+/* ---------------------------------------------------------------------------------------------------- */
+
+/* Log-likelihood ratio of Eq. lik_bg_poisson between (r, b) with the template at the integer position dr and
+ * the background-only model (r = 0, b = K / T), summed over every bin t of the histogram:
+ *     sum_t z_t log(lambda_t / lambda0) - sum_t (lambda_t - lambda0),
+ *     lambda_t = r h[t - dr + peak] + b,  lambda0 = K / T  (the log z_t! terms cancel).
+ * A bin with z_t > 0 and lambda_t = 0 makes the ratio -infinity. */
+double orc_log_lik_ratio(const orc_params* q, const double* h, const double* z, int dr, double r, double b) {
+    const int T = q->T;
+    double K = 0.0;
+    for (int t = 0; t < T; ++t) K += z[t];
+    if (K <= 0.0) return 0.0;
+    const double l0 = K / T;
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const double lam = r * tmpl(q, h, dr, t) + b;
+        if (z[t] > 0.0) s += (lam > 0.0) ? z[t] * log(lam / l0) : -INFINITY;
+        s -= lam - l0;
+    }
+    return s;
+}
+
+/* Detection surrogate. The paper decides presence with the Bayesian test of [TachellaSPIE2019] (Sec. II-E,
+ * Algorithm 1 step "Estimate pi", Sec. III-B), which it cites but does not define. This surrogate keeps that
+ * test's inputs and output -- the likelihood Eq. lik_bg_poisson, the template at the depth point estimate
+ * (round-half-even(mu)), the prior probability of presence pi0 of Eq. prior_detect, and the posterior
+ * probability pi of r > 0 -- and replaces the marginalisation over (r, b) by the Bayesian-information-criterion
+ * approximation of the Bayes factor at the maximum-likelihood point (one extra parameter, r, over about K
+ * photons):
+ *     log BF = LLR(r_hat, b_hat) - (1/2) log max(K, 1),     pi = sigmoid(logit(pi0) + log BF),
+ * with (r_hat, b_hat) from orc_intensity_mle and LLR from orc_log_lik_ratio. pi0 (nullable: 0.5 everywhere) is
+ * limited to [1e-7, 1 - 1e-7] as in Eq. prior_detect. Faulty pixels: pi = 0.5, r = b = 0 (Sec. III-B). Then
+ * Algorithm 1's branch: present = pi > 0.5 keeps (r_hat, b_hat); otherwise r = 0, b = K / T (Sec. II-E).
+ * llr (nullable) receives LLR (0 for faulty pixels). */
+void orc_detect(const orc_params* q, const double* h, const double* z, long P, const double* mu, const double* pi0,
+                const uint8_t* faulty, double* pi, double* llr, uint8_t* present, double* refl, double* bg) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long p = 0; p < P; ++p) {
+        const double* zp = z + p * (long)q->T;
+        if (faulty && faulty[p]) {
+            pi[p] = 0.5;
+            if (llr) llr[p] = 0.0;
+            present[p] = 0;
+            refl[p] = 0.0;
+            bg[p] = 0.0;
+            continue;
+        }
+        double K = 0.0;
+        for (int t = 0; t < q->T; ++t) K += zp[t];
+        const int d = (int)rint(mu[p]);
+        double r, b;
+        orc_intensity_mle(q, h, zp, d, &r, &b);
+        const double l = orc_log_lik_ratio(q, h, zp, d, r, b);
+        const double lmax = log(1e7 - 1.0);
+        const double v = pi0 ? pi0[p] : 0.5;
+        double lg = log(v) - log1p(-v);
+        if (!(lg > -lmax)) lg = -lmax;
+        if (!(lg < lmax)) lg = lmax;
+        const double x = lg + l - 0.5 * log(K > 1.0 ? K : 1.0);
+        pi[p] = 1.0 / (1.0 + exp(-x));
+        if (llr) llr[p] = l;
+        present[p] = pi[p] > 0.5;
+        if (present[p]) {
+            refl[p] = r;
+            bg[p] = b;
+        } else {
+            refl[p] = 0.0;
+            bg[p] = K / q->T;
+        }
     }
 }
 

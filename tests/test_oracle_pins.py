@@ -428,6 +428,120 @@ def test_intensity_matches_generic_optimizer(orc):
 
 
 # ------------------------------------------------------------------------------------------------------
+# Detection surrogate (BIC-approximated Bayes factor under Eq. lik_bg_poisson, combined with pi0)
+# ------------------------------------------------------------------------------------------------------
+
+
+def _logit(p):
+    return math.log(p) - math.log1p(-p)
+
+
+def test_detect_box_irf_likelihood_ratio_closed_form(orc):
+    """Box IRF: the maximised two-region Poisson likelihood ratio is
+    K_in log(K_in T / (K L)) + K_out log(K_out T / (K (T - L))) when the window rate exceeds the outside
+    rate, and 0 otherwise (then r = 0 is the maximiser)."""
+    L, T, peak = 8, 200, 4
+    h = np.full(L, 1.0 / L, np.float32)
+    q = orc.params(T, L, peak)
+    rng = _rng(41)
+    for trial in range(24):
+        z = rng.poisson(rng.uniform(0.05, 1.5), size=T).astype(np.float64)
+        d = int(rng.integers(q.dmin, q.dmax + 1))
+        z[d - peak:d - peak + L] += rng.poisson(rng.uniform(0, 4), size=L) * (trial % 3 != 0)
+        K = z.sum()
+        Kin = z[d - peak:d - peak + L].sum()
+        Kout = K - Kin
+        if Kin / L > Kout / (T - L):
+            ref = (Kin * math.log(Kin * T / (K * L)) if Kin > 0 else 0.0) + \
+                  (Kout * math.log(Kout * T / (K * (T - L))) if Kout > 0 else 0.0)
+        else:
+            ref = 0.0
+        out = orc.detect(q, h, z[None, :], np.array([float(d)]), pi0=np.array([0.3]))
+        assert out["llr"][0] == pytest.approx(ref, rel=1e-9, abs=1e-9)
+
+
+def test_detect_bayes_factor_does_not_depend_on_the_prior(orc):
+    """logit(pi) - logit(pi0) is the log Bayes factor: the same for every pi0 (and it is LLR - log(K)/2),
+    pi grows with pi0, and the decision follows pi > 0.5."""
+    h, peak = synth.asymmetric_irf(L=48)
+    T = 600
+    q = orc.params(T, len(h), peak)
+    rng = _rng(43)
+    P = 12
+    z = rng.poisson(0.05, size=(P, T)).astype(np.float64)
+    mu = rng.integers(q.dmin, q.dmax + 1, size=P).astype(np.float64)
+    for p in range(P):
+        d = int(mu[p])
+        z[p, d - peak:d - peak + len(h)] += rng.poisson((p % 4) * 0.25 * h / h.max())
+    outs = [orc.detect(q, h, z, mu, pi0=np.full(P, v)) for v in (0.1, 0.5, 0.9)]
+    K = z.sum(1)
+    checked = 0
+    for p in range(P):
+        if not all(1e-9 < o["pi"][p] < 1 - 1e-9 for o in outs):
+            continue  # saturated: the log Bayes factor is not recoverable from pi in double precision
+        checked += 1
+        lbf = [_logit(o["pi"][p]) - _logit(v) for o, v in zip(outs, (0.1, 0.5, 0.9))]
+        assert lbf[0] == pytest.approx(lbf[1], abs=1e-7) and lbf[2] == pytest.approx(lbf[1], abs=1e-7)
+        assert lbf[1] == pytest.approx(outs[1]["llr"][p] - 0.5 * math.log(max(K[p], 1.0)), abs=1e-7)
+        assert outs[0]["pi"][p] < outs[1]["pi"][p] < outs[2]["pi"][p]
+        for o in outs:
+            assert o["present"][p] == (o["pi"][p] > 0.5)
+            if o["present"][p]:
+                r, b = orc.intensity_mle(q, h, z[p], int(mu[p]))
+                assert (o["refl"][p], o["bg"][p]) == (pytest.approx(r, rel=1e-12), pytest.approx(b, rel=1e-12))
+            else:
+                assert o["refl"][p] == 0.0 and o["bg"][p] == pytest.approx(K[p] / T, rel=1e-12)
+    assert checked >= 8
+    assert sum(outs[1]["present"]) not in (0, P)  # both branches taken
+
+
+def test_detect_limits(orc):
+    """No photons: pi = pi0 (no evidence). Faulty: pi = 1/2, r = b = 0. A flat histogram: r = 0, LLR = 0 and
+    pi < pi0. Photons only on the template: pi -> 1, b = 0, r = K / sum(h)."""
+    h, peak = synth.asymmetric_irf(L=48)
+    T = 400
+    q = orc.params(T, len(h), peak)
+    d = 150
+    z = np.zeros((4, T))
+    z[1] = 3.0                                               # flat: exactly the background-only model
+    z[2, d - peak:d - peak + len(h)] = np.rint(300 * h)      # noiseless template, no background
+    z[3] = 2.0
+    pi0 = np.array([0.7, 0.5, 0.5, 0.5])
+    faulty = np.array([0, 0, 0, 1], np.uint8)
+    o = orc.detect(q, h, z, np.full(4, float(d)), pi0=pi0, faulty=faulty)
+    assert o["pi"][0] == pytest.approx(0.7, rel=1e-12) and o["llr"][0] == 0.0
+    assert o["refl"][0] == 0.0 and o["bg"][0] == 0.0
+    assert o["llr"][1] == pytest.approx(0.0, abs=1e-9) and o["pi"][1] < 0.5 and not o["present"][1]
+    assert o["refl"][1] == 0.0 and o["bg"][1] == pytest.approx(3.0, rel=1e-12)
+    assert o["pi"][2] > 1 - 1e-12 and o["present"][2]
+    assert o["bg"][2] == pytest.approx(0.0, abs=1e-9)
+    assert o["refl"][2] == pytest.approx(z[2].sum() / float(np.sum(h.astype(np.float64))), rel=1e-9)
+    assert o["pi"][3] == 0.5 and not o["present"][3] and o["refl"][3] == 0.0 and o["bg"][3] == 0.0
+
+
+def test_detect_llr_is_the_maximum(orc):
+    """The LLR at the intensity MLE is >= 0 and >= the ratio at any other (r, b) with r sum(h) + b T = K."""
+    h, peak = synth.asymmetric_irf(L=48)
+    T = 500
+    q = orc.params(T, len(h), peak)
+    rng = _rng(47)
+    hs = float(np.sum(h.astype(np.float64)))
+    for trial in range(10):
+        z = rng.poisson(rng.uniform(0.01, 0.3), size=T).astype(np.float64)
+        d = int(rng.integers(q.dmin, q.dmax + 1))
+        z[d - peak:d - peak + len(h)] += rng.poisson(rng.uniform(0, 3) * h / h.max())
+        o = orc.detect(q, h, z[None, :], np.array([float(d)]))
+        llr = o["llr"][0]
+        assert llr >= -1e-12
+        r_hat, _ = orc.intensity_mle(q, h, z, d)
+        K = z.sum()
+        for r in np.linspace(0.0, 0.999 * K / hs, 17):
+            assert orc.log_lik_ratio(q, h, z, d, r, (K - r * hs) / T) <= llr + 1e-9
+        if r_hat > 0:
+            assert orc.log_lik_ratio(q, h, z, d, r_hat, (K - r_hat * hs) / T) == pytest.approx(llr, abs=1e-12)
+
+
+# ------------------------------------------------------------------------------------------------------
 # Prior probability of presence (Eq. prior_detect)
 # ------------------------------------------------------------------------------------------------------
 
