@@ -80,7 +80,7 @@ def lib():
             L.orc_pi_propagate.argtypes = [ct.c_int, ct.c_int, d, d, u8, d]
             L.orc_log_lik_ratio.argtypes = [P, d, d, ct.c_int, ct.c_double, ct.c_double]
             L.orc_log_lik_ratio.restype = ct.c_double
-            L.orc_detect.argtypes = [P, d, d, ct.c_long, d, d, u8, d, d, u8, d, d]
+            L.orc_detect.argtypes = [P, d, d, ct.c_long, d, i32, d, d, u8, d, d, u8, d, d]
             _lib = L
     return _lib
 
@@ -223,19 +223,22 @@ def log_lik_ratio(q: Params, h, z, dr: int, r: float, b: float) -> float:
                                          int(dr), float(r), float(b)))
 
 
-def detect(q: Params, h, z, mu, pi0=None, faulty=None):
-    """Detection surrogate (BIC-approximated Bayes factor at the intensity MLE, combined with pi0):
-    dict(pi, llr, present, refl, bg), each shaped like mu."""
+def detect(q: Params, h, z, mu, dmap=None, var=None, pi0=None, faulty=None):
+    """Detection surrogate (maximum-point approximation of the Bayes factor at the pseudo-posterior mode dmap,
+    with the Occam term of the pseudo-posterior variance var, combined with pi0), then the intensity rule at
+    round(mu): dict(pi, llr, present, refl, bg) shaped like mu. dmap None: round(mu); var None: no Occam term."""
     h, z = _d(h), _d(z)
     shape = np.shape(mu)
     P = z.size // q.T
     m = _d(mu).reshape(-1)
+    dm = None if dmap is None else np.ascontiguousarray(dmap, dtype=np.int32).reshape(-1)
+    vr = None if var is None else _d(var).reshape(-1)
     p0 = None if pi0 is None else _d(pi0).reshape(-1)
     fa = _u8(faulty)
     pi, llr, r, b = (np.empty(P) for _ in range(4))
     pres = np.empty(P, dtype=np.uint8)
     lib().orc_detect(ct.byref(q), _ptr(h, ct.c_double), _ptr(z, ct.c_double), P, _ptr(m, ct.c_double),
-                     _ptr(p0, ct.c_double), _ptr(fa, ct.c_uint8), _ptr(pi, ct.c_double), _ptr(llr, ct.c_double),
+                     _ptr(dm, ct.c_int32), _ptr(vr, ct.c_double), _ptr(p0, ct.c_double), _ptr(fa, ct.c_uint8), _ptr(pi, ct.c_double), _ptr(llr, ct.c_double),
                      _ptr(pres, ct.c_uint8), _ptr(r, ct.c_double), _ptr(b, ct.c_double))
     return dict(pi=pi.reshape(shape), llr=llr.reshape(shape), present=pres.reshape(shape), refl=r.reshape(shape),
                 bg=b.reshape(shape))

@@ -376,19 +376,40 @@ double orc_log_lik_ratio(const orc_params* q, const double* h, const double* z, 
 }
 
 /* Detection surrogate. The paper decides presence with the Bayesian test of [TachellaSPIE2019] (Sec. II-E,
- * Algorithm 1 step "Estimate pi", Sec. III-B), which it cites but does not define. This surrogate keeps that
- * test's inputs and output -- the likelihood Eq. lik_bg_poisson, the template at the depth point estimate
- * (round-half-even(mu)), the prior probability of presence pi0 of Eq. prior_detect, and the posterior
- * probability pi of r > 0 -- and replaces the marginalisation over (r, b) by the Bayesian-information-criterion
- * approximation of the Bayes factor at the maximum-likelihood point (one extra parameter, r, over about K
- * photons):
- *     log BF = LLR(r_hat, b_hat) - (1/2) log max(K, 1),     pi = sigmoid(logit(pi0) + log BF),
- * with (r_hat, b_hat) from orc_intensity_mle and LLR from orc_log_lik_ratio. pi0 (nullable: 0.5 everywhere) is
- * limited to [1e-7, 1 - 1e-7] as in Eq. prior_detect. Faulty pixels: pi = 0.5, r = b = 0 (Sec. III-B). Then
- * Algorithm 1's branch: present = pi > 0.5 keeps (r_hat, b_hat); otherwise r = 0, b = K / T (Sec. II-E).
- * llr (nullable) receives LLR (0 for faulty pixels). */
-void orc_detect(const orc_params* q, const double* h, const double* z, long P, const double* mu, const double* pi0,
-                const uint8_t* faulty, double* pi, double* llr, uint8_t* present, double* refl, double* bg) {
+ * Algorithm 1 step "Estimate pi", Sec. III-B), which it cites but does not define; that test marginalises the
+ * depth with the pseudo-posterior as its prior (Sec. III-B, empirical Bayes). This surrogate keeps the test's
+ * inputs and output -- the likelihood Eq. lik_bg_poisson, the pseudo-posterior, the prior probability of
+ * presence pi0 of Eq. prior_detect, and the posterior probability pi of r > 0 -- and replaces the
+ * marginalisations by their maximum-point (Laplace / Bayesian-information-criterion) approximations:
+ *   - depth: Laplace's method for the integral of the likelihood ratio against the pseudo-posterior (variance
+ *     var) at its mode dmap; the likelihood ratio's width in depth is taken as the template's, sigma_h^2 =
+ *     sum_j a_j (j - mean)^2 with a = max(h, 0) / sum(max(h, 0)), and a pseudo-posterior narrower than that
+ *     costs nothing: the Occam term is max(0, (1/2) log(var / sigma_h^2));
+ *   - (r, b): their maximum likelihood, one extra parameter (r) over about K photons: (1/2) log max(K, 1).
+ *     log BF = LLR(dmap; r_hat, b_hat) - (1/2) log max(K, 1) - max(0, (1/2) log(var / sigma_h^2)),
+ *     pi = sigmoid(logit(pi0) + log BF),
+ * with (r_hat, b_hat) from orc_intensity_mle at dmap and LLR from orc_log_lik_ratio. pi0 (nullable: 0.5
+ * everywhere) is limited to [1e-7, 1 - 1e-7] as in Eq. prior_detect. Faulty pixels: pi = 0.5, r = b = 0
+ * (Sec. III-B). Then Algorithm 1's branch with the intensity rule of Sec. II-E: present = pi > 0.5 gives the
+ * MLE (r, b) with the template at the depth point estimate round-half-even(mu); absent gives r = 0, b = K / T.
+ * dmap nullable: round-half-even(mu); var nullable: no Occam term. llr (nullable) receives LLR (0 for faulty
+ * pixels). */
+void orc_detect(const orc_params* q, const double* h, const double* z, long P, const double* mu, const int32_t* dmap,
+                const double* var, const double* pi0, const uint8_t* faulty, double* pi, double* llr,
+                uint8_t* present, double* refl, double* bg) {
+    double hs = 0.0, hm = 0.0, hv = 0.0;
+    for (int j = 0; j < q->L; ++j) {
+        const double a = h[j] > 0.0 ? h[j] : 0.0;
+        hs += a;
+        hm += a * j;
+    }
+    if (hs > 0.0) {
+        hm /= hs;
+        for (int j = 0; j < q->L; ++j) {
+            const double a = h[j] > 0.0 ? h[j] : 0.0;
+            hv += a / hs * (j - hm) * (j - hm);
+        }
+    }
 #pragma omp parallel for schedule(dynamic, 64)
     for (long p = 0; p < P; ++p) {
         const double* zp = z + p * (long)q->T;
@@ -402,16 +423,19 @@ void orc_detect(const orc_params* q, const double* h, const double* z, long P, c
         }
         double K = 0.0;
         for (int t = 0; t < q->T; ++t) K += zp[t];
-        const int d = (int)rint(mu[p]);
-        double r, b;
+        const int d = (int)rint(mu[p]), dm = dmap ? dmap[p] : d;
+        double r, b, rm, bm;
         orc_intensity_mle(q, h, zp, d, &r, &b);
-        const double l = orc_log_lik_ratio(q, h, zp, d, r, b);
+        orc_intensity_mle(q, h, zp, dm, &rm, &bm);
+        const double l = orc_log_lik_ratio(q, h, zp, dm, rm, bm);
         const double lmax = log(1e7 - 1.0);
         const double v = pi0 ? pi0[p] : 0.5;
         double lg = log(v) - log1p(-v);
         if (!(lg > -lmax)) lg = -lmax;
         if (!(lg < lmax)) lg = lmax;
-        const double x = lg + l - 0.5 * log(K > 1.0 ? K : 1.0);
+        double occam = 0.0;
+        if (var && hv > 0.0 && var[p] > hv) occam = 0.5 * log(var[p] / hv);
+        const double x = lg + l - 0.5 * log(K > 1.0 ? K : 1.0) - occam;
         pi[p] = 1.0 / (1.0 + exp(-x));
         if (llr) llr[p] = l;
         present[p] = pi[p] > 0.5;

@@ -519,6 +519,48 @@ def test_detect_limits(orc):
     assert o["pi"][3] == 0.5 and not o["present"][3] and o["refl"][3] == 0.0 and o["bg"][3] == 0.0
 
 
+def test_detect_mode_for_the_test_mean_for_the_estimate(orc):
+    """The evidence is taken with the template at the pseudo-posterior mode dmap (the surface's photons there);
+    the reported (r, b) of a present pixel use the depth point estimate round(mu), as in Sec. II-E."""
+    h, peak = synth.asymmetric_irf(L=48)
+    T = 600
+    q = orc.params(T, len(h), peak)
+    z = np.zeros((1, T))
+    z[0] += (np.arange(T) % 37 == 0)                         # a few background photons
+    dtrue = 300
+    z[0, dtrue - peak:dtrue - peak + len(h)] += np.rint(40 * h)
+    mu = np.array([450.0])                                   # a mean pulled away from the surface
+    on = orc.detect(q, h, z, mu, dmap=np.array([dtrue]))
+    off = orc.detect(q, h, z, mu)                            # test at round(mu): no surface there
+    r_m, b_m = orc.intensity_mle(q, h, z[0], dtrue)
+    assert on["llr"][0] == pytest.approx(orc.log_lik_ratio(q, h, z[0], dtrue, r_m, b_m), rel=1e-12)
+    assert on["llr"][0] > 50 and on["present"][0]
+    assert off["llr"][0] < on["llr"][0] and not off["present"][0]
+    r, b = orc.intensity_mle(q, h, z[0], 450)
+    assert on["refl"][0] == pytest.approx(r, rel=1e-12, abs=1e-12) and on["bg"][0] == pytest.approx(b, rel=1e-12)
+
+
+def test_detect_occam_term_of_the_depth_marginal(orc):
+    """Laplace's method over the depth: a pseudo-posterior of variance var wider than the template costs
+    (1/2) log(var / sigma_h^2) nats of evidence; narrower costs nothing. For a box IRF of L taps sigma_h^2 is
+    the discrete-uniform variance (L^2 - 1) / 12."""
+    L, T, peak = 9, 300, 4
+    h = np.full(L, 1.0 / L)
+    q = orc.params(T, L, peak)
+    rng = _rng(53)
+    z = rng.poisson(0.2, size=(1, T)).astype(np.float64)
+    z[0, 100 - peak:100 - peak + 3] += 1                  # a weak surface: pi stays well inside (0, 1)
+    s2 = (L * L - 1) / 12.0
+    mu = np.array([100.0])
+    base = orc.detect(q, h, z, mu, pi0=np.array([0.4]))
+    x0 = _logit(base["pi"][0])
+    assert abs(x0) < 20
+    for var, shift in ((0.5 * s2, 0.0), (s2, 0.0), (s2 * math.e ** 2, 1.0), (s2 * math.e ** 5, 2.5)):
+        o = orc.detect(q, h, z, mu, var=np.array([var]), pi0=np.array([0.4]))
+        assert _logit(o["pi"][0]) == pytest.approx(x0 - shift, abs=1e-9)
+        assert o["llr"][0] == base["llr"][0]
+
+
 def test_detect_llr_is_the_maximum(orc):
     """The LLR at the intensity MLE is >= 0 and >= the ratio at any other (r, b) with r sum(h) + b T = K."""
     h, peak = synth.asymmetric_irf(L=48)
