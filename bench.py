@@ -78,11 +78,12 @@ def parse():
                     help="mixed workload only: image side (default 1024; smaller sides for profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc"],
+    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc", "detect"],
                     help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
                          "frame; diff: differentiable filter forward + backward; mixed: 1024x1024 FP16 frames "
                          "through the tensor-core filter step; video_tc: the video job through the tensor-core "
-                         "filter step on FP16 copies of its frames, beside the FP32 path")
+                         "filter step on FP16 copies of its frames, beside the FP32 path; detect: the video job "
+                         "with the presence decision on the device (detection surrogate + Eq. prior_detect)")
     return ap.parse_args()
 
 
@@ -649,6 +650,92 @@ def video_tc(args):
     print(json.dumps(line), flush=True)
 
 
+def detect(args):
+    """The video job with the presence decision of Algorithm 1 on the device: per frame spl_filter_step_detect
+    (depth, moments and the detection surrogate with the intensity rule) and spl_pi_propagate (Eq. prior_detect
+    for the next frame), the decision feeding the next frame's present_in. Timed like the headline, beside the
+    plain spl_filter_step job. Every pixel of this scene has a surface, so the fraction declared present at each
+    run's last frame is the detection rate; the false-alarm rate is measured on one background-only frame per
+    SBR (same background level, pi0 = 0.5)."""
+    import paper_2004_09211_gb300 as spl
+    from paper_2004_09211_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    frames = args.frames
+    h, peak, hd, sc, videos = make_sequences(frames, dev)
+    P = H * W
+    prms = [spl.make_params(H, W, T, L, peak, beta=b, sigma_rw2=SIGMA_RW2) for b in BETAS]
+    states = [[([torch.empty(P, device=dev) for _ in range(2)], [torch.empty(P, device=dev) for _ in range(2)])
+               for _ in BETAS] for _ in SBRS]
+    outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                bg=torch.empty(P, device=dev))
+    pi_buf = [torch.empty(P, device=dev) for _ in range(2)]
+    pres_buf = [torch.empty(P, dtype=torch.uint8, device=dev) for _ in range(2)]
+    pi0_buf = torch.empty(P, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    units = len(SBRS) * len(BETAS) * frames * P
+
+    def run(vi, bi):
+        """One (SBR, beta) run over all frames; returns the last frame's decisions."""
+        prm = prms[bi]
+        mu, var = states[vi][bi]
+        spl.spl_state_init(prm, mu[0], var[0], stream=stream)
+        pi0 = pres = None
+        for n, z in enumerate(videos[vi]):
+            src, dst = n & 1, (n + 1) & 1
+            o = spl.spl_filter_step_detect(prm, z, hd, mu[src], var[src], present_in=pres, pi0=pi0,
+                                           out=dict(mu=mu[dst], var=var[dst], pi=pi_buf[n & 1],
+                                                    present=pres_buf[n & 1], **outs), stream=stream)
+            pi0 = spl.spl_pi_propagate(prm, o["pi"], pi_out=pi0_buf, stream=stream)
+            pres = o["present"]
+        return pres
+
+    def job():
+        for vi in range(len(SBRS)):
+            for bi in range(len(BETAS)):
+                run(vi, bi)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    with ClockSampler(0) as clk:
+        ms_det = timed(job)
+    launches = len(SBRS) * len(BETAS) * (1 + 3 * frames) * args.steps
+    p_d = {f"SBR {SBRS[vi]} beta {BETAS[bi]}": float(run(vi, bi).float().mean())
+           for vi in range(len(SBRS)) for bi in range(len(BETAS))}
+    p_fa = {}
+    gen = torch.Generator(device=dev).manual_seed(SEED + 7)
+    for vi, sbr in enumerate(SBRS):
+        b = float(sc.signal[0].mean()) / (sbr * T)
+        zbg = synth.pitched(synth.poisson_histograms(torch.full((P, T), b, device=dev), gen).reshape(P, T),
+                            synth.pad_pitch(T))
+        for bi, prm in enumerate(prms):
+            mu, var = states[vi][bi]
+            o = spl.spl_filter_step_detect(prm, zbg, hd, mu[frames & 1], var[frames & 1], stream=stream)
+            p_fa[f"SBR {sbr} beta {BETAS[bi]}"] = float(o["present"].float().mean())
+    ms_plain = timed(lambda: run_job(spl, prms, hd, videos, states, outs, stream))
+    line = {"metric": "pixel-frames/s", "value": units / (ms_det / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_det, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + ", presence decided on the device (detection surrogate)",
+                       "pixels": P, "frames": frames, "pixel_frames_per_step": units},
+            "plain_path": {"value": units / (ms_plain / 1e3), "ms_per_step": ms_plain,
+                           "detection_overhead": ms_det / ms_plain - 1.0},
+            "detection_rate_last_frame": p_d, "false_alarm_rate_background_frame": p_fa,
+            "gpu_launches": launches, "clocks": clk.summary(), "roofline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------------------------------------
 # mixed precision: the filter step with the data term on the tensor cores
 # ---------------------------------------------------------------------------------------------------------
@@ -832,6 +919,8 @@ def main():
         mixed(args)
     elif args.workload == "video_tc":
         video_tc(args)
+    elif args.workload == "detect":
+        detect(args)
     else:
         native(args)
 

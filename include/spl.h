@@ -149,6 +149,34 @@ SPL_API spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, con
                            float* refl, float* bg, void* stream);
 
 /*
+ * spl_filter_step_detect -- spl_filter_step with the presence decision of Algorithm 1 made on the device
+ *   ("Estimate pi", then "if target present, i.e. pi > 0.5"). The detector the paper uses ([TachellaSPIE2019],
+ *   Sec. II-E, Sec. III-B) is cited but not defined there; this call implements a SURROGATE with the same
+ *   inputs and output, and takes its marginalisations at their maximum points (Laplace / Bayesian-information-
+ *   criterion approximation): the depth at the pseudo-posterior's mode (argmax, the cited test's depth prior
+ *   being the pseudo-posterior), (r, b) at their maximum likelihood under Eq. lik_bg_poisson. With K the
+ *   pixel's photon count and (r, b) the MLE with the template at argmax,
+ *     LLR     = log L(r, b) - log L(0, K/T)            (maximised log-likelihood ratio, >= 0)
+ *     log BF  = LLR - log(max(K, 1)) / 2               (one extra parameter over about K photons)
+ *               - max(0, log(var_out / sigma_h^2) / 2) (Laplace over the depth: a pseudo-posterior wider
+ *                                                       than the template, sigma_h^2 = its variance in bins^2)
+ *     pi      = sigmoid(logit(pi0) + log BF)            (posterior probability of presence)
+ *   pi0[p] is the prior probability of presence (Eq. prior_detect, e.g. spl_pi_propagate of the previous
+ *   frame's pi; NULL = 0.5 everywhere), limited to [1e-7, 1 - 1e-7]. present = pi > 0.5 then selects the
+ *   intensity rule (present: the MLE (r, b) with the template at the depth point estimate
+ *   round-half-even(mu_out), as in spl_depth_estimate; absent: r = 0, b = K/T). Faulty pixels get pi = 0.5,
+ *   absent, refl = bg = 0 (Sec. III-B).
+ *   Arguments as spl_filter_step, with present_now replaced by pi0; outputs argmax (required here), pi [P]
+ *   float (required), present_out [P] uint8 (nullable: 1 where pi > 0.5, usable as the next frame's
+ *   present_in), refl and bg (required). pi must not alias pi0.
+ */
+SPL_API spl_status spl_filter_step_detect(const spl_params* prm, const spl_hist* z, const float* h,
+                                          const float* mu_in, const float* var_in, const uint8_t* present_in,
+                                          const uint8_t* faulty, const float* pi0, float* mu_out, float* var_out,
+                                          int32_t* argmax, float* pi, uint8_t* present_out, float* refl, float* bg,
+                                          void* stream);
+
+/*
  * spl_state_init -- initial Gaussians of Algorithm 1 (n = 0): the weakly informative Gaussian of Sec. III-A,
  *   mu = (dmin + dmax)/2 and var = (dmax - dmin)^2/12, for every pixel. mu, var: [P] float.
  */

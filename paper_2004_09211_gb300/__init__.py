@@ -18,7 +18,7 @@ from ._abi import (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY, SPL_HIST_F16, SPL_HIST
                    SPL_MAX_BINS, SPL_MAX_PHOTONS, SPL_MAX_TAPS, SplError, spl_hist, spl_params, spl_seq_frame)
 
 __all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate",
-           "spl_filter_step", "spl_filter_step_tc", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
+           "spl_filter_step", "spl_filter_step_detect", "spl_filter_step_tc", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
            "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status",
            "spl_diff_scratch_size", "spl_diff_forward", "spl_diff_backward", "FilterLoss", "spl_depth_cost_tc",
            "spl_tc_status", "SplError",
@@ -211,6 +211,31 @@ def spl_filter_step(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: to
         _dev(o["mu"], "mu", torch.float32, P), _dev(o["var"], "var", torch.float32, P),
         _dev(o.get("argmax"), "argmax", torch.int32, P),
         _dev(o.get("refl"), "refl", torch.float32, P), _dev(o.get("bg"), "bg", torch.float32, P),
+        _stream(stream)))
+    return o
+
+
+def spl_filter_step_detect(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor,
+                           var_in: torch.Tensor, present_in=None, faulty=None, pi0=None, out: dict | None = None,
+                           stream=None) -> dict:
+    """spl_filter_step with the presence decision made on the device by the detection surrogate.
+    Returns dict(mu, var, argmax, pi, present, refl, bg); present (uint8) can be the next frame's present_in."""
+    P = _P(prm)
+    o = dict(out or {})
+    for k, dt in (("mu", torch.float32), ("var", torch.float32), ("argmax", torch.int32), ("pi", torch.float32),
+                  ("present", torch.uint8), ("refl", torch.float32), ("bg", torch.float32)):
+        o.setdefault(k, _empty((P,), dt, z))
+    lib = _abi.load()
+    hz = _hist(prm, z)
+    _abi.check(lib.spl_filter_step_detect(
+        ct.byref(prm), ct.byref(hz), _dev(h, "h", torch.float32, prm.L),
+        _dev(mu_in, "mu_in", torch.float32, P), _dev(var_in, "var_in", torch.float32, P),
+        _dev(present_in, "present_in", torch.uint8, P), _dev(faulty, "faulty", torch.uint8, P),
+        _dev(pi0, "pi0", torch.float32, P),
+        _dev(o["mu"], "mu", torch.float32, P), _dev(o["var"], "var", torch.float32, P),
+        _dev(o.get("argmax"), "argmax", torch.int32, P), _dev(o["pi"], "pi", torch.float32, P),
+        _dev(o.get("present"), "present", torch.uint8, P),
+        _dev(o["refl"], "refl", torch.float32, P), _dev(o["bg"], "bg", torch.float32, P),
         _stream(stream)))
     return o
 

@@ -57,6 +57,8 @@ SIGNATURES = {
     "spl_tc_status": (ct.c_int, [ct.POINTER(ct.c_uint32)]),
     "spl_depth_estimate": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_filter_step": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "spl_filter_step_detect": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                          _vp, _vp]),
     "spl_filter_step_tc": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_state_init": (ct.c_int, [_P, _vp, _vp, _vp]),
     "spl_pi_propagate": (ct.c_int, [_P, _vp, _vp, _vp, _vp]),

@@ -213,6 +213,39 @@ spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float
     return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_filter_step launch");
 }
 
+spl_status spl_filter_step_detect(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                                  const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                                  const float* pi0, float* mu_out, float* var_out, int32_t* argmax, float* pi,
+                                  uint8_t* present_out, float* refl, float* bg, void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, true);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(mu_in && var_in && mu_out && var_out, "mu_in, var_in, mu_out and var_out are required");
+    SPL_REQUIRE(mu_out != mu_in && var_out != var_in && mu_out != var_in && var_out != mu_in,
+                "outputs must not alias the previous-frame state");
+    SPL_REQUIRE(argmax != nullptr && pi != nullptr && refl != nullptr && bg != nullptr,
+                "argmax, pi, refl and bg are required");
+    SPL_REQUIRE(pi0 == nullptr || pi0 != pi, "pi must not alias pi0");
+    EstimateArgs a = base_args(prm, z, h);
+    a.prior_mode = PRIOR_STENCIL;
+    a.pmu = mu_in;
+    a.pvar = var_in;
+    a.present_in = present_in;
+    a.faulty = faulty;
+    a.argmax = argmax;
+    a.mu = mu_out;
+    a.var = var_out;
+    a.refl = refl;
+    a.bg = bg;
+    a.detect = 1;
+    a.pi0 = pi0;
+    a.pi_out = pi;
+    a.present_out = present_out;
+    return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_filter_step_detect launch");
+}
+
 spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
                               const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
                               const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,

@@ -10,6 +10,17 @@
 // Kept out of the depth kernels: there a solve holds the pixel's warp (or the 128-pixel block of the tensor-core
 // pipeline) until its slowest pixel converges; here every resident warp hides the others' latency, and with
 // templates of at most 64 taps a warp solves four pixels at once, one per group of 8 lanes.
+//
+// Detection mode (a.detect): the presence decision of Algorithm 1 comes from a surrogate of the cited detector,
+// its marginalisations taken at their maximum points: the template at the pseudo-posterior's mode (argmax),
+// (r, b) at the solve's maximum there, and
+//   log BF = LLR - log(max(K, 1)) / 2 - max(0, log(var / sigma_h^2) / 2),
+//   LLR = sum_{t in W, z_t > 0} z_t log(1 - f + T f a_t) + K_out log(1 - f)
+// (the maximised log-likelihood ratio against b = K / T alone; sum_t lambda_t = K at the maximum; the last
+// term is Laplace's method over the depth for a pseudo-posterior of variance var wider than the template,
+// sigma_h^2 = the template's variance), then pi = sigmoid(logit(pi0) + log BF) with pi0 limited to
+// [1e-7, 1 - 1e-7] as in Eq. prior_detect, and present = pi > 0.5 selects the intensity rule (at round(mu),
+// the depth point estimate) in place of present_now. Faulty pixels: pi = 0.5.
 #include <cuda_fp16.h>
 #include <math.h>
 #include <stdint.h>
@@ -20,6 +31,18 @@
 namespace spl {
 namespace {
 
+// pi = sigmoid(logit(pi0) + llr - log(max(K, 1)) / 2 - occam), pi0 limited to [1e-7, 1 - 1e-7] (through its
+// logit); occam = max(0, log(var / sigma_h^2) / 2) for a pseudo-posterior of variance var.
+__device__ __forceinline__ float presence(float pi0, float llr, float K, float var, float hvar) {
+    const float lmax = 16.118095f;  // log(1e7 - 1)
+    float lg = logf(pi0) - log1pf(-pi0);
+    if (!(lg > -lmax)) lg = -lmax;
+    if (!(lg < lmax)) lg = lmax;
+    const float occam = hvar > 0.f && var > hvar ? 0.5f * logf(var / hvar) : 0.f;
+    const float x = lg + llr - 0.5f * logf(fmaxf(K, 1.f)) - occam;
+    return 1.f / (1.f + expf(-x));
+}
+
 // Count in bin t of pixel p's row (u16, f16 or f32 storage).
 template <int FMT>
 __device__ __forceinline__ float hist_value(const void* z, long long pitch, long long p, int t) {
@@ -29,8 +52,9 @@ __device__ __forceinline__ float hist_value(const void* z, long long pitch, long
     return static_cast<float>(static_cast<const unsigned short*>(z)[i]);
 }
 
-// Normalised template h / sum(h) (taps <= 0 count as 0) into as[0 .. SPL_MAX_TAPS); returns sum(h). Block-wide.
-__device__ __forceinline__ float template_table(const EstimateArgs& a, float* as, float* s_hsum) {
+// Normalised template h / sum(h) (taps <= 0 count as 0) into as[0 .. SPL_MAX_TAPS); returns sum(h), and the
+// template's variance in bins^2 (sum_j a_j (j - mean)^2) in *s_hvar. Block-wide.
+__device__ __forceinline__ float template_table(const EstimateArgs& a, float* as, float* s_hsum, float* s_hvar) {
     for (int j = threadIdx.x; j < SPL_MAX_TAPS; j += blockDim.x) {
         const float hj = j < a.L ? a.h[j] : 0.f;
         as[j] = hj > 0.f ? hj : 0.f;
@@ -46,6 +70,19 @@ __device__ __forceinline__ float template_table(const EstimateArgs& a, float* as
     const float hsum = *s_hsum;
     if (hsum > 0.f)
         for (int j = threadIdx.x; j < a.L; j += blockDim.x) as[j] /= hsum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float m = 0.f;
+        for (int j = threadIdx.x; j < a.L; j += 32) m = fmaf(as[j], static_cast<float>(j), m);
+        m = px::warp_sum(m);
+        float v = 0.f;
+        for (int j = threadIdx.x; j < a.L; j += 32) {
+            const float e = static_cast<float>(j) - m;
+            v = fmaf(as[j] * e, e, v);
+        }
+        v = px::warp_sum(v);
+        if (threadIdx.x == 0) *s_hvar = v;
+    }
     __syncthreads();
     return hsum;
 }
@@ -65,9 +102,8 @@ __device__ __forceinline__ float group8_sum(float v) {
 
 // The solve for four pixels per warp, one per group of 8 lanes (lane s of a group holds bins s + 8 q, q < 8, so
 // L <= 64). The groups iterate together (the shuffles are warp-wide) until every group has converged; a
-// converged group keeps its f. need == false: the group only takes part.
-__device__ __forceinline__ void intensity_mle_g8(const float* zj, const float* aj, float K, int L, int T, float hsum,
-                                                 bool need, float& r, float& b) {
+// converged group keeps its f. need == false: the group only takes part (f = 0). Returns the signal fraction f.
+__device__ __forceinline__ float fraction_g8(const float* zj, const float* aj, float K, int L, int T, bool need) {
     const float u = 1.f / static_cast<float>(T);
     float kin = 0.f, za = 0.f, p1 = 0.f;
     bool zero_tap = false;
@@ -130,16 +166,53 @@ __device__ __forceinline__ void intensity_mle_g8(const float* zj, const float* a
             }
         }
     }
-    r = f * K / hsum;
-    b = (1.f - f) * K * u;
+    return f;
+}
+
+// Maximised log-likelihood ratio of the group's window at signal fraction f (0 when need == false):
+// sum_{z_t > 0} z_t log(1 - f + T f a_t) + K_out log(1 - f). Warp-collective.
+__device__ __forceinline__ float llr_g8(const float* zj, const float* aj, float f, float K, int T, bool need) {
+    const float tf = static_cast<float>(T) * f, of = 1.f - f;
+    float s = 0.f, kin = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        kin += zj[q];
+        if (zj[q] > 0.f) s = fmaf(zj[q], logf(fmaf(tf, aj[q], of)), s);
+    }
+    s = group8_sum(s);
+    kin = group8_sum(kin);
+    const float kout = fmaxf(K - kin, 0.f);
+    return need ? s + (kout > 0.f ? kout * log1pf(-f) : 0.f) : 0.f;
+}
+
+// Writes pixel p's outputs from its solve: the intensity rule of Sec. II-E with the presence decision of the
+// detection surrogate (detect) or of present_now.
+__device__ __forceinline__ void write_pixel(const EstimateArgs& a, long long p, bool faulty, bool present_now,
+                                            float K, float hsum, float hvar, float r, float b, float llr) {
+    bool present = present_now;
+    if (a.detect) {
+        const float pi = faulty ? 0.5f : presence(a.pi0 ? a.pi0[p] : 0.5f, llr, K, a.var[p], hvar);
+        present = !faulty && pi > 0.5f;
+        a.pi_out[p] = pi;
+        if (a.present_out) a.present_out[p] = present ? 1 : 0;
+    }
+    if (faulty) {
+        r = b = 0.f;
+    } else if (!present || !(K > 0.f) || !(hsum > 0.f)) {
+        r = 0.f;
+        b = K / static_cast<float>(a.T);
+    }
+    a.refl[p] = r;
+    a.bg[p] = b;
 }
 
 // Four pixels per warp (templates of at most 64 taps).
 template <int FMT>
 __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
     __shared__ float as[SPL_MAX_TAPS];
-    __shared__ float s_hsum;
-    const float hsum = template_table(a, as, &s_hsum);
+    __shared__ float s_hsum, s_hvar;
+    const float hsum = template_table(a, as, &s_hsum, &s_hvar);
+    const float hvar = s_hvar;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, sl = lane & 7;
     const long long P = static_cast<long long>(a.H) * a.W;
     const long long stride = 4LL * gridDim.x * (blockDim.x >> 5);
@@ -148,7 +221,7 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
         const bool valid = p < P;
         const float K = valid ? a.bg[p] : 0.f;
         const bool faulty = valid && a.faulty ? a.faulty[p] != 0 : false;
-        const bool present = valid && (a.present_now ? a.present_now[p] != 0 : true);
+        const bool present = valid && (a.detect || (a.present_now ? a.present_now[p] != 0 : true));
         const bool need = valid && !faulty && present && K > 0.f && hsum > 0.f;
         const int t0 = need ? window_start(a, a.mu[p]) : 0;
         float zj[8], aj[8];
@@ -158,18 +231,27 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
             zj[q] = need && j < a.L ? hist_value<FMT>(a.z, a.pitch, p, t0 + j) : 0.f;
             aj[q] = j < a.L ? as[j] : 0.f;
         }
-        float r = 0.f, b = 0.f;
-        intensity_mle_g8(zj, aj, K, a.L, a.T, hsum, need, r, b);
-        if (valid && sl == 0) {
-            if (faulty) {
-                r = b = 0.f;
-            } else if (!need) {
-                r = 0.f;
-                b = K / static_cast<float>(a.T);
+        const float f = fraction_g8(zj, aj, K, a.L, a.T, need);
+        const float r = f * K / hsum, b = (1.f - f) * K * (1.f / static_cast<float>(a.T));
+        float llr = 0.f;
+        if (a.detect) {  // the evidence with the template at the pseudo-posterior mode
+            const int t1 = need ? window_start(a, static_cast<float>(a.argmax[p])) : t0;
+            float fm = f;
+            if (__any_sync(0xffffffffu, t1 != t0)) {  // some group's mode differs from round(mu): solve there
+                const bool again = need && t1 != t0;
+                if (again) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int j = sl + 8 * q;
+                        zj[q] = j < a.L ? hist_value<FMT>(a.z, a.pitch, p, t1 + j) : 0.f;
+                    }
+                }
+                const float f1 = fraction_g8(zj, aj, K, a.L, a.T, again);
+                if (again) fm = f1;
             }
-            a.refl[p] = r;
-            a.bg[p] = b;
+            llr = llr_g8(zj, aj, fm, K, a.T, need);
         }
+        if (valid && sl == 0) write_pixel(a, p, faulty, present, K, hsum, hvar, r, b, llr);
         __syncwarp();
     }
 }
@@ -178,36 +260,55 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
 template <int FMT>
 __global__ void __launch_bounds__(256) k_intensity1(const EstimateArgs a) {
     __shared__ float as[SPL_MAX_TAPS];
-    __shared__ float s_hsum;
-    const float hsum = template_table(a, as, &s_hsum);
+    __shared__ float s_hsum, s_hvar;
+    const float hsum = template_table(a, as, &s_hsum, &s_hvar);
+    const float hvar = s_hvar;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long P = static_cast<long long>(a.H) * a.W;
     const long long stride = static_cast<long long>(gridDim.x) * (blockDim.x >> 5);
     for (long long p = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + warp; p < P; p += stride) {
         const float K = a.bg[p];
         const bool faulty = a.faulty ? a.faulty[p] != 0 : false;
-        const bool present = a.present_now ? a.present_now[p] != 0 : true;
-        float r = 0.f, b = 0.f;
-        if (faulty) {
-            r = b = 0.f;
-        } else if (!present || !(K > 0.f) || !(hsum > 0.f)) {
-            r = 0.f;
-            b = K / static_cast<float>(a.T);
-        } else {
+        const bool present = a.detect || (a.present_now ? a.present_now[p] != 0 : true);
+        float r = 0.f, b = 0.f, llr = 0.f;
+        if (!faulty && present && K > 0.f && hsum > 0.f) {  // warp-uniform
+            constexpr int NQ = SPL_MAX_TAPS / 32;
             const int t0 = window_start(a, a.mu[p]);
-            float zj[SPL_MAX_TAPS / 32], aj[SPL_MAX_TAPS / 32];
+            float zj[NQ], aj[NQ];
 #pragma unroll
-            for (int q = 0; q < SPL_MAX_TAPS / 32; ++q) {
+            for (int q = 0; q < NQ; ++q) {
                 const int j = lane + 32 * q;
                 zj[q] = j < a.L ? hist_value<FMT>(a.z, a.pitch, p, t0 + j) : 0.f;
                 aj[q] = j < a.L ? as[j] : 0.f;
             }
-            px::intensity_mle<SPL_MAX_TAPS / 32>(zj, aj, K, a.L, a.T, hsum, r, b);
+            const float f0 = px::intensity_fraction<NQ>(zj, aj, K, a.L, a.T);
+            r = f0 * K / hsum;
+            b = (1.f - f0) * K * (1.f / static_cast<float>(a.T));
+            if (a.detect) {  // the evidence with the template at the pseudo-posterior mode
+                const int t1 = window_start(a, static_cast<float>(a.argmax[p]));
+                float f = f0;
+                if (t1 != t0) {  // warp-uniform
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const int j = lane + 32 * q;
+                        zj[q] = j < a.L ? hist_value<FMT>(a.z, a.pitch, p, t1 + j) : 0.f;
+                    }
+                    f = px::intensity_fraction<NQ>(zj, aj, K, a.L, a.T);
+                }
+                const float tf = static_cast<float>(a.T) * f, of = 1.f - f;
+                float s = 0.f, kin = 0.f;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    kin += zj[q];
+                    if (zj[q] > 0.f) s = fmaf(zj[q], logf(fmaf(tf, aj[q], of)), s);
+                }
+                s = px::warp_sum(s);
+                kin = px::warp_sum(kin);
+                const float kout = fmaxf(K - kin, 0.f);
+                llr = s + (kout > 0.f ? kout * log1pf(-f) : 0.f);
+            }
         }
-        if (lane == 0) {
-            a.refl[p] = r;
-            a.bg[p] = b;
-        }
+        if (lane == 0) write_pixel(a, p, faulty, present, K, hsum, hvar, r, b, llr);
         __syncwarp();
     }
 }

@@ -373,13 +373,12 @@ __device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float 
 // ------------------------------------------------------------------------------------------------------------
 
 // MLE of the signal fraction f of the two-component model "template a_t, uniform 1/T" (Eq. lik_bg with the
-// template placed on the window W), then r = f K / sum(h) and b = (1 - f) K / T. Lane items: zj[q] = photons
+// template placed on the window W); intensity_mle then gives r = f K / sum(h) and b = (1 - f) K / T. Lane items: zj[q] = photons
 // in a window bin whose normalised template value is aj[q] (items of all lanes together cover W once).
 // psi(f) = sum_W z (a - u) / (u + f (a - u)) - Kout / (1 - f), u = 1/T, is decreasing on [0, 1): safeguarded
 // Newton on psi with the bracket [lo, hi] kept around its root.
 template <int NQ>
-__device__ __forceinline__ void intensity_mle(const float* zj, const float* aj, float K, int L, int T, float hsum,
-                                              float& r, float& b) {
+__device__ __forceinline__ float intensity_fraction(const float* zj, const float* aj, float K, int L, int T) {
     const float u = 1.f / static_cast<float>(T);
     float kin = 0.f, za = 0.f, p1 = 0.f;
     bool zero_tap = false;
@@ -437,8 +436,16 @@ __device__ __forceinline__ void intensity_mle(const float* zj, const float* aj, 
             if (conv) break;
         }
     }
+    return f;
+}
+
+// (r, b) from the signal fraction above: r = f K / sum(h), b = (1 - f) K / T.
+template <int NQ>
+__device__ __forceinline__ void intensity_mle(const float* zj, const float* aj, float K, int L, int T, float hsum,
+                                              float& r, float& b) {
+    const float f = intensity_fraction<NQ>(zj, aj, K, L, T);
     r = f * K / hsum;
-    b = (1.f - f) * K * u;
+    b = (1.f - f) * K * (1.f / static_cast<float>(T));
 }
 
 }  // namespace px

@@ -40,6 +40,11 @@ struct EstimateArgs {
     float* refl;
     float* bg;
     const uint8_t* present_now;
+    // detection surrogate (intensity launch only): present_now is then ignored
+    int detect;
+    const float* pi0;       // prior probability of presence (nullable: 0.5)
+    float* pi_out;          // posterior probability of presence
+    uint8_t* present_out;   // pi_out > 0.5 (nullable)
 };
 
 // Launch geometry chosen on the host for one launch.

@@ -152,3 +152,28 @@ def test_tensor_core_argument_checks():
                                 0x6000, None, None, None, None)
     assert st == _abi.SPL_EINVAL and "sigma_rw2" in lib.spl_last_error().decode()
     assert lib.spl_tc_status(None) == _abi.SPL_EINVAL
+
+
+def test_detect_argument_checks():
+    """spl_filter_step_detect requires pi, refl and bg, keeps the filter's checks, and pi must not alias pi0;
+    all decided on the host."""
+    lib = _abi.load()
+    prm = make_params(4, 4, 64, 25, 12)
+    hz = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 64)
+    #                    prm, z, h, mu_in, var_in, present_in, faulty, pi0, mu_out, var_out, argmax, pi, present, refl, bg
+    st = lib.spl_filter_step_detect(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                                    0x6000, 0xa000, None, None, 0x7000, 0x8000, None)
+    assert st == _abi.SPL_EINVAL and "argmax, pi, refl and bg" in lib.spl_last_error().decode()
+    st = lib.spl_filter_step_detect(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                                    0x6000, None, 0x9000, None, 0x7000, 0x8000, None)
+    assert st == _abi.SPL_EINVAL and "argmax, pi, refl and bg" in lib.spl_last_error().decode()
+    st = lib.spl_filter_step_detect(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, 0x9000, 0x5000,
+                                    0x6000, 0xa000, 0x9000, None, 0x7000, 0x8000, None)
+    assert st == _abi.SPL_EINVAL and "alias pi0" in lib.spl_last_error().decode()
+    st = lib.spl_filter_step_detect(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x3000,
+                                    0x6000, 0xa000, 0x9000, None, 0x7000, 0x8000, None)
+    assert st == _abi.SPL_EINVAL and "alias" in lib.spl_last_error().decode()
+    bad = make_params(4, 4, 64, 25, 12, beta=-1.0)
+    st = lib.spl_filter_step_detect(ct.byref(bad), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+                                    0x6000, 0xa000, 0x9000, None, 0x7000, 0x8000, None)
+    assert st == _abi.SPL_EINVAL

@@ -244,6 +244,77 @@ def test_sparse_rows_long_templates(orc, L, peak, bg):
     _run_filter(orc, q, prm, h, [z, z[:, ::-1].copy()], T)
 
 
+def _logit(p):
+    p = np.clip(np.asarray(p, np.float64), 1e-300, 1 - 1e-16)
+    return np.log(p) - np.log1p(-p)
+
+
+@pytest.mark.parametrize("sbr,beta", [(0.1, 0.5), (1.0, 0.3), (0.02, 0.5)])
+def test_filter_step_detect(orc, sbr, beta):
+    """The on-device presence decision (detection surrogate) against the oracle, frame by frame on the GPU's
+    own inputs: a scene whose left third has no surface (background only), faulty pixels, pi0 from
+    Eq. prior_detect of the previous frame's pi and present_in from the previous frame's decision."""
+    H, W, N, T = 18, 24, 4, 500
+    h, peak = synth.asymmetric_irf(L=48)
+    sc = synth.moving_scene(H, W, N, peak + 8, T - 48 + peak - 8, 77)
+    g = torch.Generator().manual_seed(77)
+    rng = np.random.default_rng(77)
+    faulty = (rng.random((H, W)) < 0.05).astype(np.uint8)
+    q = orc.params(T, len(h), peak, beta=beta, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    prm = spl.make_params(H, W, T, len(h), peak, beta=beta, sigma_rw2=3.0)
+    hd = torch.from_numpy(h).to(DEV)
+    fd = torch.from_numpy(faulty).to(DEV).reshape(-1)
+    mu_g, var_g = spl.spl_state_init(prm)
+    pres_g, pi0_g = None, None
+    decided = flipped = 0
+    for n in range(N):
+        sig = sc.signal[n].copy()
+        sig[:, : W // 3] = 0.0                                   # no surface: background only
+        b = float(sc.signal[n].mean()) / (sbr * T)
+        mean = synth.expected_counts(torch.from_numpy(sc.depth[n]), torch.from_numpy(sig), b,
+                                     torch.from_numpy(h), peak, T)
+        z = torch.poisson(mean, generator=g).numpy().astype(np.float64)
+        o = spl.spl_filter_step_detect(prm, _gpu_hist(z, T), hd, mu_g, var_g, present_in=pres_g, faulty=fd,
+                                       pi0=pi0_g)
+        torch.cuda.synchronize()
+        pin = None if pres_g is None else _np(pres_g).reshape(H, W)
+        e = orc.filter_step(q, h, z, _np(mu_g).reshape(H, W), _np(var_g).reshape(H, W), present_in=pin,
+                            faulty=faulty)
+        check_close(_np(o["mu"]), e["mu"], f"mu frame {n}")
+        check_close(_np(o["var"]), e["var"], f"var frame {n}", atol=1e-6)
+        p0 = None if pi0_g is None else _np(pi0_g).reshape(H, W)
+        d = orc.detect(q, h, z, _np(o["mu"]).reshape(H, W), dmap=_np(o["argmax"]).reshape(H, W),
+                       var=_np(o["var"]).reshape(H, W), pi0=p0, faulty=faulty)
+        pi_g = _np(o["pi"]).reshape(-1)
+        pi_o = d["pi"].reshape(-1)
+        # pi = sigmoid(x): an error dx of the evidence x (relative 1e-4, absolute 1e-3) moves pi by
+        # pi (1 - pi) dx, and storing pi in FP32 adds at most 1.2e-7
+        x_o = _logit(pi_o)
+        tol = pi_o * (1 - pi_o) * (1e-3 + 1e-4 * np.abs(x_o)) + 1.2e-7
+        bad = np.abs(pi_g - pi_o) > tol
+        assert not bad.any(), f"pi frame {n}: gpu {pi_g[bad][:5]} oracle {pi_o[bad][:5]}"
+        pr_g = _np(o["present"]).reshape(-1).astype(bool)
+        pr_o = d["present"].reshape(-1).astype(bool)
+        near = np.abs(x_o) <= 1e-3 + 1e-4 * np.abs(x_o)
+        assert np.all((pr_g == pr_o) | near), f"present frame {n}: {np.nonzero((pr_g != pr_o) & ~near)[0][:5]}"
+        assert np.all(pr_g == (pi_g > 0.5))
+        same = pr_g == pr_o
+        K = z.reshape(-1, T).sum(1)
+        hs = float(np.sum(h.astype(np.float64)))
+        check_close(_np(o["bg"])[same], d["bg"].reshape(-1)[same], f"bg frame {n}", atol=1e-5 * (K[same] / T) + 1e-12)
+        check_close(_np(o["refl"])[same], d["refl"].reshape(-1)[same], f"refl frame {n}",
+                    atol=1e-5 * K[same] / hs + 1e-12)
+        assert np.all(pi_g[faulty.reshape(-1) == 1] == 0.5)
+        decided += pr_g.sum()
+        flipped += int((~same).sum())
+        pi0_g = spl.spl_pi_propagate(prm, o["pi"], faulty=fd)
+        pres_g = o["present"]
+        mu_g, var_g = o["mu"], o["var"]
+    # both decisions occur: the surface region is mostly detected, the empty third mostly not
+    assert 0 < decided < N * H * W
+    assert flipped <= 2
+
+
 def test_empty_histograms_give_the_prior(orc):
     """No photons: the GPU posterior moments equal the prior's (and the oracle's)."""
     h, peak = synth.asymmetric_irf(L=48)
