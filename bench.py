@@ -78,12 +78,14 @@ def parse():
                     help="mixed workload only: image side (default 1024; smaller sides for profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc", "detect"],
+    ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc", "detect",
+                                                              "pd_curves"],
                     help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
                          "frame; diff: differentiable filter forward + backward; mixed: 1024x1024 FP16 frames "
                          "through the tensor-core filter step; video_tc: the video job through the tensor-core "
                          "filter step on FP16 copies of its frames, beside the FP32 path; detect: the video job "
-                         "with the presence decision on the device (detection surrogate + Eq. prior_detect)")
+                         "with the presence decision on the device (detection surrogate + Eq. prior_detect); "
+                         "pd_curves: the single-pixel p_d experiment of Sec. IV-A (Gaussian IRF, five betas)")
     return ap.parse_args()
 
 
@@ -736,6 +738,88 @@ def detect(args):
     print(json.dumps(line), flush=True)
 
 
+PD_T, PD_FWHM, PD_PRIOR_MU, PD_PRIOR_VAR, PD_ETA, PD_NMC = 1500, 28.0, 600.0, 2500.0, 28.0, 2000
+PD_BETAS = (0.1, 0.3, 0.5, 0.7, 0.9)
+
+
+def pd_inputs(sbr, msc, n_mc, seed, device):
+    """The single-pixel experiment of Sec. IV-A with the Gaussian IRF (FWHM 28 bins, taps +-4 sigma, unit sum):
+    n_mc histograms per (SBR, MSC) cell, depth drawn from N(600, 2500) and rounded to the bin grid (kept inside
+    the full-support range), z ~ Poisson(MSC s_d + MSC / (SBR T)) (Eq. lik_bg_poisson). Returns (h, peak,
+    depth [cells * n_mc] int, z [cells * n_mc, pitch] uint16) with cells = len(sbr) * len(msc), SBR fastest."""
+    from paper_2004_09211_gb300 import synth
+    sigma = PD_FWHM / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    h, peak = synth.gaussian_irf(sigma, int(math.ceil(4 * sigma)))
+    hd = torch.from_numpy(h).to(device)
+    gen = torch.Generator(device=device).manual_seed(seed)
+    pitch = synth.pad_pitch(PD_T)
+    lo, hi = peak, PD_T - len(h) + peak
+    depth, zs = [], []
+    for m in msc:
+        d = torch.randn(len(sbr) * n_mc, generator=gen, device=device) * math.sqrt(PD_PRIOR_VAR) + PD_PRIOR_MU
+        d = d.round().clamp(lo, hi).to(torch.int64)
+        b = torch.tensor([m / (s * PD_T) for s in sbr], device=device).repeat_interleave(n_mc)
+        mean = synth.expected_counts(d, torch.full_like(b, m), b, hd, peak, PD_T)
+        zs.append(synth.pitched(synth.poisson_histograms(mean, gen), pitch))
+        depth.append(d)
+        del mean
+    return h, peak, torch.cat(depth), torch.cat(zs)
+
+
+def pd_curves(args):
+    """Curves of satisfactory detection (Sec. IV-A, Fig. MMSE_synth, Gaussian-IRF half, the PB estimator only):
+    p_d = fraction of |d_hat - d| < 28 with d_hat the pseudo-posterior mean under the prior N(600, 2500), over a
+    25 x 13 grid of SBR in [1e-4, 1e2] and mean signal count in [10, 1000], 2000 histograms per cell, for five
+    values of beta. Reports, per beta and MSC, the smallest SBR on the grid from which p_d >= 0.85, and the
+    estimate throughput (one spl_depth_estimate launch over all cells per beta)."""
+    import paper_2004_09211_gb300 as spl
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    sbr = np.logspace(-4, 2, 25)
+    msc = np.logspace(1, 3, 13)
+    h, peak, depth, z = pd_inputs(sbr, msc, PD_NMC, SEED + 11, dev)
+    hd = torch.from_numpy(h).to(dev)
+    P = z.shape[0]
+    W_ = 1000
+    assert P % W_ == 0
+    pm = torch.full((P,), PD_PRIOR_MU, device=dev)
+    pv = torch.full((P,), PD_PRIOR_VAR, device=dev)
+    out = {}
+    ms_all = []
+    with ClockSampler(0) as clk:
+        for beta in PD_BETAS:
+            prm = spl.make_params(P // W_, W_, PD_T, len(h), peak, beta=beta)
+            o = dict(mu=torch.empty(P, device=dev), var=torch.empty(P, device=dev),
+                     argmax=torch.empty(P, dtype=torch.int32, device=dev))
+            for _ in range(max(args.warmup, 1)):
+                spl.spl_depth_estimate(prm, z, hd, pm, pv, intensity=False, out=o)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                spl.spl_depth_estimate(prm, z, hd, pm, pv, intensity=False, out=o)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms_all.append(e0.elapsed_time(e1) / args.steps)
+            ok = ((o["mu"] - depth.float()).abs() < PD_ETA).float().view(len(msc), len(sbr), PD_NMC).mean(-1).cpu()
+            limit = {}
+            for i, m in enumerate(msc):
+                good = [j for j in range(len(sbr)) if bool((ok[i, j:] >= 0.85).all())]
+                limit[f"{m:.4g}"] = float(sbr[good[0]]) if good else None
+            out[f"beta {beta}"] = {"limiting_sbr_by_msc": limit, "pd_grid": ok.numpy().round(4).tolist()}
+    ms = sum(ms_all)
+    line = {"metric": "pixel-estimates/s", "value": P * len(PD_BETAS) / (ms / 1e3), "unit": "pixel-estimates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "single-pixel p_d experiment (Sec. IV-A, Gaussian IRF FWHM 28, T=1500, prior "
+                                   "N(600, 2500), eta 28): 25 SBR x 13 MSC x 2000 histograms per beta",
+                       "sbr_grid": sbr.tolist(), "msc_grid": msc.tolist(), "betas": list(PD_BETAS), "pixels": P},
+            "curves": out, "gpu_launches": 2 * len(PD_BETAS) * args.steps, "clocks": clk.summary(),
+            "roofline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------------------------------------
 # mixed precision: the filter step with the data term on the tensor cores
 # ---------------------------------------------------------------------------------------------------------
@@ -921,6 +1005,8 @@ def main():
         video_tc(args)
     elif args.workload == "detect":
         detect(args)
+    elif args.workload == "pd_curves":
+        pd_curves(args)
     else:
         native(args)
 

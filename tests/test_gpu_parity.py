@@ -315,6 +315,38 @@ def test_filter_step_detect(orc, sbr, beta):
     assert flipped <= 2
 
 
+def test_pd_experiment_estimates_match_the_oracle(orc):
+    """The single-pixel p_d experiment (Sec. IV-A, Gaussian IRF, prior N(600, 2500)) on a small grid: the GPU
+    pseudo-posterior means equal the oracle's, and so do the satisfactory-detection indicators |mu - d| < 28
+    (except where the oracle's error is within 1e-3 of the threshold)."""
+    import bench
+    sbr, msc = [0.001, 1.0, 50.0], [12.0, 300.0]
+    n_mc = 40
+    h, peak, depth, z = bench.pd_inputs(sbr, msc, n_mc, 5, DEV)
+    P = z.shape[0]
+    T = bench.PD_T
+    q = orc.params(T, len(h), peak, beta=0.5)
+    prm = spl.make_params(1, P, T, len(h), peak, beta=0.5)
+    pm = torch.full((P,), bench.PD_PRIOR_MU, device=DEV)
+    pv = torch.full((P,), bench.PD_PRIOR_VAR, device=DEV)
+    o = spl.spl_depth_estimate(prm, z, torch.from_numpy(h).to(DEV), pm, pv, intensity=False)
+    torch.cuda.synchronize()
+    zc = _np(z)[:, :T].astype(np.float64)
+    e = orc.estimate(q, h, zc.reshape(1, P, T), prior_mu=np.full((1, P), bench.PD_PRIOR_MU),
+                     prior_var=np.full((1, P), bench.PD_PRIOR_VAR))
+    mu_o = e["mu"].reshape(-1)
+    check_close(_np(o["mu"]), mu_o, "mu")
+    d = _np(depth).astype(np.float64)
+    ok_g = np.abs(_np(o["mu"]) - d) < bench.PD_ETA
+    ok_o = np.abs(mu_o - d) < bench.PD_ETA
+    edge = np.abs(np.abs(mu_o - d) - bench.PD_ETA) < 1e-3
+    assert np.all((ok_g == ok_o) | edge)
+    # the grid spans failure and success: 12 signal photons under 6000 background photons leave about the
+    # prior's own rate (|N(0, 2500)| < 28: 0.42); 300 photons at SBR 50 succeed
+    cell = ok_o.reshape(len(msc), len(sbr), n_mc).mean(-1)
+    assert cell[1, 2] > 0.85 and cell[0, 0] < 0.7
+
+
 def test_empty_histograms_give_the_prior(orc):
     """No photons: the GPU posterior moments equal the prior's (and the oracle's)."""
     h, peak = synth.asymmetric_irf(L=48)
