@@ -25,7 +25,8 @@
  * translation equivariance and the dependency cone of the filter; the box-IRF closed form of the intensity
  * MLE and its KKT conditions checked by scipy; the fixed points of Eq. prior_detect; for the detection
  * surrogate, the box-IRF closed form of the two-region Poisson likelihood ratio, the logistic combination with
- * pi0 and its limits.
+ * pi0 and its limits; for the sub-bin grid, the reduction to the integer grid at S = 1, the half-bin average
+ * at beta = 1 (linear interpolation commutes with the correlation), translation and the empty histogram.
  */
 #include <math.h>
 #include <stdint.h>
@@ -193,6 +194,80 @@ void orc_estimate(const orc_params* q, const double* h, const double* z, long P,
             if (ell_out) memcpy(ell_out + p * (long)D, ell, sizeof(double) * D);
         }
         free(C);
+        free(ell);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------- */
+/* Sub-bin depth: Eq. beta_div2 with a continuous IRF on a fine candidate grid                           */
+/* ---------------------------------------------------------------------------------------------------- */
+
+/* Continuous IRF from the taps (a reading: the paper's continuous model, Eq. lik_ideal and Eq. beta_div2 over
+ * continuous ToAs, uses the instrument's continuous response, of which the tabulated taps are samples):
+ * piecewise-linear interpolation of h[0..L) with h[-1] = h[L] = 0, i.e. support (-1, L). */
+static double irf_c(const orc_params* q, const double* h, double x) {
+    if (!(x > -1.0) || !(x < (double)q->L)) return 0.0;
+    const double fl = floor(x);
+    const int j = (int)fl;
+    const double w = x - fl;
+    const double a = (j >= 0) ? h[j] : 0.0;
+    const double b = (j + 1 < q->L) ? h[j + 1] : 0.0;
+    return (1.0 - w) * a + w * b;
+}
+
+/* Single-frame estimate on the fine grid d_k = dmin + k / S, k = 0 .. (dmax - dmin) S. The histogram's photons
+ * sit at their bin positions t, so Eq. beta_div2 reads C(d) = sum_t z_t h_c(t - d + peak)^beta (0^beta = 0);
+ * ell(d) = lambda C(d) + log N(d; prior_mu[p], prior_var[p]) (uniform without a prior); outputs the smallest
+ * maximising index k, and the mean and variance of the normalised weights on the fine grid (two passes).
+ * The integral of f0^(1+beta) that Eq. beta_div2 drops is exactly constant only for whole-bin shifts of the
+ * sampled template; it is dropped here as well (reading). With S = 1 this is orc_estimate. ell_out
+ * (nullable) receives ell[p][k]. */
+void orc_estimate_fine(const orc_params* q, int S, const double* h, const double* z, long P,
+                       const double* prior_mu, const double* prior_var, int* argmax_k, double* mu, double* var,
+                       double* ell_out) {
+    const int Kf = (q->dmax - q->dmin) * S + 1;
+    const double lam = lambda_of(q->beta);
+#pragma omp parallel
+    {
+        double* ell = (double*)malloc(sizeof(double) * Kf);
+#pragma omp for schedule(dynamic, 16)
+        for (long p = 0; p < P; ++p) {
+            const double* zp = z + p * (long)q->T;
+            for (int k = 0; k < Kf; ++k) {
+                const double d = q->dmin + (double)k / S;
+                double c = 0.0;
+                for (int t = 0; t < q->T; ++t) {
+                    const double x = t - d + q->peak;
+                    if (zp[t] != 0.0 && x > -1.0 && x < (double)q->L) c += zp[t] * powb(irf_c(q, h, x), q->beta);
+                }
+                double lp = 0.0;
+                if (prior_mu) {
+                    const double one = 1.0, m = prior_mu[p], s2 = prior_var[p];
+                    lp = orc_log_mixture(1, &one, &m, &s2, d);
+                }
+                ell[k] = lam * c + lp;
+            }
+            int a = 0;
+            for (int k = 1; k < Kf; ++k)
+                if (ell[k] > ell[a]) a = k;
+            double s0 = 0.0, s1 = 0.0;
+            for (int k = 0; k < Kf; ++k) {
+                const double w = exp(ell[k] - ell[a]);
+                s0 += w;
+                s1 += w * (q->dmin + (double)k / S);
+            }
+            const double mean = s1 / s0;
+            double s2 = 0.0;
+            for (int k = 0; k < Kf; ++k) {
+                const double w = exp(ell[k] - ell[a]);
+                const double e = q->dmin + (double)k / S - mean;
+                s2 += w * e * e;
+            }
+            argmax_k[p] = a;
+            mu[p] = mean;
+            var[p] = s2 / s0;
+            if (ell_out) memcpy(ell_out + p * (long)Kf, ell, sizeof(double) * Kf);
+        }
         free(ell);
     }
 }
