@@ -79,13 +79,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc", "detect",
-                                                              "pd_curves"],
+                                                              "pd_curves", "fine"],
                     help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
                          "frame; diff: differentiable filter forward + backward; mixed: 1024x1024 FP16 frames "
                          "through the tensor-core filter step; video_tc: the video job through the tensor-core "
                          "filter step on FP16 copies of its frames, beside the FP32 path; detect: the video job "
                          "with the presence decision on the device (detection surrogate + Eq. prior_detect); "
-                         "pd_curves: the single-pixel p_d experiment of Sec. IV-A (Gaussian IRF, five betas)")
+                         "pd_curves: the single-pixel p_d experiment of Sec. IV-A (Gaussian IRF, five betas); "
+                         "fine: single-frame estimates on the sub-bin grid")
     return ap.parse_args()
 
 
@@ -738,6 +739,52 @@ def detect(args):
     print(json.dumps(line), flush=True)
 
 
+def fine(args):
+    """Sub-bin depth (spl_depth_estimate_fine): single-frame estimates of the video frames (SBR 1 sequence, beta
+    0.5, uniform prior) on the fine grid with S = 1, 2, 4, 8 steps per bin, beside spl_depth_estimate on the
+    integer grid. Throughput in pixel-estimates/s per S."""
+    import paper_2004_09211_gb300 as spl
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    frames = min(args.frames, 4)
+    h, peak, hd, sc, videos = make_sequences(frames, dev)
+    P = H * W
+    prm = spl.make_params(H, W, T, L, peak, beta=0.5)
+    zs = videos[SBRS.index(1.0)]
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            for z in zs:
+                fn(z)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            for z in zs:
+                fn(z)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / (args.steps * len(zs))
+
+    res = {}
+    with ClockSampler(0) as clk:
+        ms_int = timed(lambda z: spl.spl_depth_estimate(prm, z, hd, intensity=False))
+        for S in (1, 2, 4, 8):
+            ms = timed(lambda z: spl.spl_depth_estimate_fine(prm, S, z, hd))
+            res[f"S={S}"] = {"ms_per_frame": ms, "pixel_estimates_per_s": P / (ms / 1e3),
+                             "candidates_per_pixel": (prm.dmax - prm.dmin) * S + 1}
+    line = {"metric": "pixel-estimates/s", "value": res["S=4"]["pixel_estimates_per_s"],
+            "unit": "pixel-estimates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["S=4"]["ms_per_frame"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sub-bin single-frame estimate, S = 4, video frames 256x256, T=1500, SBR 1, "
+                                   "beta 0.5, uniform prior", "frames": frames},
+            "by_S": res, "integer_grid": {"ms_per_frame": ms_int, "pixel_estimates_per_s": P / (ms_int / 1e3)},
+            "gpu_launches": (4 + 1) * args.steps * len(zs), "clocks": clk.summary(), "roofline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 PD_T, PD_FWHM, PD_PRIOR_MU, PD_PRIOR_VAR, PD_ETA, PD_NMC = 1500, 28.0, 600.0, 2500.0, 28.0, 2000
 PD_BETAS = (0.1, 0.3, 0.5, 0.7, 0.9)
 
@@ -1007,6 +1054,8 @@ def main():
         detect(args)
     elif args.workload == "pd_curves":
         pd_curves(args)
+    elif args.workload == "fine":
+        fine(args)
     else:
         native(args)
 

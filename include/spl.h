@@ -130,6 +130,24 @@ SPL_API spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, 
                               float* var, float* refl, float* bg, void* stream);
 
 /*
+ * spl_depth_estimate_fine -- spl_depth_estimate on a sub-bin candidate grid (the continuous form of the data
+ *   term, Eq. beta_div2 over continuous times of arrival). Candidates d_k = dmin + k / S, k = 0 .. (dmax - dmin) S.
+ *   The IRF is made continuous by piecewise-linear interpolation of its taps, with h[-1] = h[L] = 0 (support
+ *   (-1, L)); a surface at d has the binned template s_d[t] = h_c(t - d + peak) and C(d) = sum_t z_t s_d[t]^beta.
+ *   The pseudo-likelihood is exp(-K D_beta) with the whole beta-divergence: the template-power term
+ *   -K sum_t s_d[t]^(1+beta), which Eq. beta_div2 drops because it is the same for every whole-bin shift, changes
+ *   with the phase of an interpolated template and is kept (K = the photon count):
+ *     ell(d) = lambda C(d) - K sum_t s_d[t]^(1+beta) + log N(d; prior_mu[p], prior_var[p])
+ *   (uniform prior when prior_mu is NULL). Outputs per pixel: argmax_fine (nullable) = the smallest maximising
+ *   index k (depth dmin + k / S), mu and var = mean and variance of the normalised pseudo-posterior on the fine
+ *   grid. Every candidate is evaluated (no pruning). S in 1..16 and (dmax - dmin) S + 1 <= 16384, else
+ *   SPL_EUNSUPPORTED. S = 1 gives the results of spl_depth_estimate (the kept term is then one constant).
+ */
+SPL_API spl_status spl_depth_estimate_fine(const spl_params* prm, int S, const spl_hist* z, const float* h,
+                                           const float* prior_mu, const float* prior_var, int32_t* argmax_fine,
+                                           float* mu, float* var, void* stream);
+
+/*
  * spl_filter_step -- one frame of the online filter (one outer iteration of Algorithm 1).
  *   Prior (Eq. predict): for each pixel p, a Gaussian mixture over the 3x3 stencil with weights nu. Stencil
  *   entry p' contributes N(mu_in[p'], var_in[p'] + sigma_rw2) if p' is inside the frame, present_in[p'] != 0

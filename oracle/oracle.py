@@ -78,7 +78,7 @@ def lib():
             L.orc_intensity_mle.argtypes = [P, d, d, ct.c_int, d, d]
             L.orc_intensity.argtypes = [P, d, d, ct.c_long, d, i32, u8, u8, d, d]
             L.orc_pi_propagate.argtypes = [ct.c_int, ct.c_int, d, d, u8, d]
-            L.orc_estimate_fine.argtypes = [P, ct.c_int, d, d, ct.c_long, d, d, i32, d, d, d]
+            L.orc_estimate_fine.argtypes = [P, ct.c_int, d, d, ct.c_long, d, d, i32, d, d, d, d]
             L.orc_log_lik_ratio.argtypes = [P, d, d, ct.c_int, ct.c_double, ct.c_double]
             L.orc_log_lik_ratio.restype = ct.c_double
             L.orc_detect.argtypes = [P, d, d, ct.c_long, d, i32, d, d, u8, d, d, u8, d, d]
@@ -169,9 +169,9 @@ def estimate(q: Params, h, z, prior_mu=None, prior_var=None, want_ell=False):
     return out
 
 
-def estimate_fine(q: Params, S: int, h, z, prior_mu=None, prior_var=None, want_ell=False):
-    """Single-frame estimate on the fine grid dmin + k/S (continuous IRF by linear interpolation of the taps):
-    dict(argmax_k, mu, var[, ell]) shaped like z[..., :]."""
+def estimate_fine(q: Params, S: int, h, z, prior_mu=None, prior_var=None, want_ell=False, want_cost=False):
+    """Single-frame estimate on the fine grid dmin + k/S (continuous IRF by linear interpolation of the taps, the
+    template-power term of the beta-divergence kept): dict(argmax_k, mu, var[, ell][, cost]) shaped like z[..., :]."""
     assert check_domain(q) == 0 and S >= 1
     h, z = _d(h), _d(z)
     shape = z.shape[:-1]
@@ -181,13 +181,17 @@ def estimate_fine(q: Params, S: int, h, z, prior_mu=None, prior_var=None, want_e
     mu = np.empty(P)
     var = np.empty(P)
     ell = np.empty((P, Kf)) if want_ell else None
+    cst = np.empty((P, Kf)) if want_cost else None
     pm, pv = _d(prior_mu), _d(prior_var)
     lib().orc_estimate_fine(ct.byref(q), int(S), _ptr(h, ct.c_double), _ptr(z, ct.c_double), P,
                             _ptr(pm, ct.c_double), _ptr(pv, ct.c_double), _ptr(a, ct.c_int32),
-                            _ptr(mu, ct.c_double), _ptr(var, ct.c_double), _ptr(ell, ct.c_double))
+                            _ptr(mu, ct.c_double), _ptr(var, ct.c_double), _ptr(ell, ct.c_double),
+                            _ptr(cst, ct.c_double))
     out = dict(argmax_k=a.reshape(shape), mu=mu.reshape(shape), var=var.reshape(shape))
     if want_ell:
         out["ell"] = ell.reshape(*shape, Kf)
+    if want_cost:
+        out["cost"] = cst.reshape(*shape, Kf)
     return out
 
 

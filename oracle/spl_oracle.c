@@ -204,27 +204,32 @@ void orc_estimate(const orc_params* q, const double* h, const double* z, long P,
 
 /* Continuous IRF from the taps (a reading: the paper's continuous model, Eq. lik_ideal and Eq. beta_div2 over
  * continuous ToAs, uses the instrument's continuous response, of which the tabulated taps are samples):
- * piecewise-linear interpolation of h[0..L) with h[-1] = h[L] = 0, i.e. support (-1, L). */
+ * piecewise-linear interpolation of h[0..L) with h[-1] = h[L] = 0, i.e. support (-1, L). Taps <= 0 (or NaN)
+ * count as 0 before the interpolation, as they do on the integer grid. */
 static double irf_c(const orc_params* q, const double* h, double x) {
     if (!(x > -1.0) || !(x < (double)q->L)) return 0.0;
     const double fl = floor(x);
     const int j = (int)fl;
     const double w = x - fl;
-    const double a = (j >= 0) ? h[j] : 0.0;
-    const double b = (j + 1 < q->L) ? h[j + 1] : 0.0;
+    const double a = (j >= 0 && h[j] > 0.0) ? h[j] : 0.0;
+    const double b = (j + 1 < q->L && h[j + 1] > 0.0) ? h[j + 1] : 0.0;
     return (1.0 - w) * a + w * b;
 }
 
-/* Single-frame estimate on the fine grid d_k = dmin + k / S, k = 0 .. (dmax - dmin) S. The histogram's photons
- * sit at their bin positions t, so Eq. beta_div2 reads C(d) = sum_t z_t h_c(t - d + peak)^beta (0^beta = 0);
- * ell(d) = lambda C(d) + log N(d; prior_mu[p], prior_var[p]) (uniform without a prior); outputs the smallest
- * maximising index k, and the mean and variance of the normalised weights on the fine grid (two passes).
- * The integral of f0^(1+beta) that Eq. beta_div2 drops is exactly constant only for whole-bin shifts of the
- * sampled template; it is dropped here as well (reading). With S = 1 this is orc_estimate. ell_out
- * (nullable) receives ell[p][k]. */
+/* Single-frame estimate on the fine grid d_k = dmin + k / S, k = 0 .. (dmax - dmin) S. The binned template of a
+ * surface at d is s_d[t] = h_c(t - d + peak) (for whole-bin d the taps themselves); the data term of Eq.
+ * beta_div2 is C(d) = sum_t z_t s_d[t]^beta (0^beta = 0). The pseudo-likelihood is exp(-K D_beta) with the
+ * beta-divergence between the histogram (normalised by its photon count K) and s_d, whose d-dependent part is
+ * lambda C(d) / K - sum_t s_d[t]^(1+beta): Eq. beta_div2 drops the second sum because it is the same for every
+ * whole-bin shift (Sec. II-B); at fractional shifts the interpolated template's power changes with the phase,
+ * so it is kept here:
+ *     ell(d) = lambda C(d) - K sum_t s_d[t]^(1+beta) + log N(d; prior_mu[p], prior_var[p])
+ * (uniform without a prior). Outputs the smallest maximising index k, and the mean and variance of the
+ * normalised weights on the fine grid (two passes). With S = 1 the kept sum is one constant and this is
+ * orc_estimate. ell_out / cost_out (nullable) receive ell[p][k] and C[p][k]. */
 void orc_estimate_fine(const orc_params* q, int S, const double* h, const double* z, long P,
                        const double* prior_mu, const double* prior_var, int* argmax_k, double* mu, double* var,
-                       double* ell_out) {
+                       double* ell_out, double* cost_out) {
     const int Kf = (q->dmax - q->dmin) * S + 1;
     const double lam = lambda_of(q->beta);
 #pragma omp parallel
@@ -233,19 +238,25 @@ void orc_estimate_fine(const orc_params* q, int S, const double* h, const double
 #pragma omp for schedule(dynamic, 16)
         for (long p = 0; p < P; ++p) {
             const double* zp = z + p * (long)q->T;
+            double K = 0.0;
+            for (int t = 0; t < q->T; ++t) K += zp[t];
             for (int k = 0; k < Kf; ++k) {
                 const double d = q->dmin + (double)k / S;
-                double c = 0.0;
+                double c = 0.0, pw = 0.0;
                 for (int t = 0; t < q->T; ++t) {
                     const double x = t - d + q->peak;
-                    if (zp[t] != 0.0 && x > -1.0 && x < (double)q->L) c += zp[t] * powb(irf_c(q, h, x), q->beta);
+                    if (!(x > -1.0 && x < (double)q->L)) continue;
+                    const double sv = irf_c(q, h, x);
+                    if (zp[t] != 0.0) c += zp[t] * powb(sv, q->beta);
+                    pw += powb(sv, 1.0 + q->beta);
                 }
                 double lp = 0.0;
                 if (prior_mu) {
                     const double one = 1.0, m = prior_mu[p], s2 = prior_var[p];
                     lp = orc_log_mixture(1, &one, &m, &s2, d);
                 }
-                ell[k] = lam * c + lp;
+                ell[k] = lam * c - K * pw + lp;
+                if (cost_out) cost_out[p * (long)Kf + k] = c;
             }
             int a = 0;
             for (int k = 1; k < Kf; ++k)

@@ -17,7 +17,7 @@ from . import _abi
 from ._abi import (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY, SPL_HIST_F16, SPL_HIST_F32, SPL_HIST_U16,
                    SPL_MAX_BINS, SPL_MAX_PHOTONS, SPL_MAX_TAPS, SplError, spl_hist, spl_params, spl_seq_frame)
 
-__all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate",
+__all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate", "spl_depth_estimate_fine",
            "spl_filter_step", "spl_filter_step_detect", "spl_filter_step_tc", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
            "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status",
            "spl_diff_scratch_size", "spl_diff_forward", "spl_diff_backward", "FilterLoss", "spl_depth_cost_tc",
@@ -186,6 +186,25 @@ def spl_depth_estimate(prm: spl_params, z: torch.Tensor, h: torch.Tensor, prior_
         _dev(o["mu"], "mu", torch.float32, P), _dev(o["var"], "var", torch.float32, P),
         _dev(o.get("refl"), "refl", torch.float32, P), _dev(o.get("bg"), "bg", torch.float32, P),
         _stream(stream)))
+    return o
+
+
+def spl_depth_estimate_fine(prm: spl_params, S: int, z: torch.Tensor, h: torch.Tensor, prior_mu=None, prior_var=None,
+                            out: dict | None = None, stream=None) -> dict:
+    """Single-frame estimate on the sub-bin grid dmin + k/S (continuous IRF by linear interpolation of the taps).
+    Returns dict(argmax_k, mu, var); argmax_k is the fine index (depth dmin + argmax_k / S)."""
+    P = _P(prm)
+    o = dict(out or {})
+    o.setdefault("argmax_k", _empty((P,), torch.int32, z))
+    o.setdefault("mu", _empty((P,), torch.float32, z))
+    o.setdefault("var", _empty((P,), torch.float32, z))
+    lib = _abi.load()
+    hz = _hist(prm, z)
+    _abi.check(lib.spl_depth_estimate_fine(
+        ct.byref(prm), int(S), ct.byref(hz), _dev(h, "h", torch.float32, prm.L),
+        _dev(prior_mu, "prior_mu", torch.float32, P), _dev(prior_var, "prior_var", torch.float32, P),
+        _dev(o.get("argmax_k"), "argmax_k", torch.int32, P), _dev(o["mu"], "mu", torch.float32, P),
+        _dev(o["var"], "var", torch.float32, P), _stream(stream)))
     return o
 
 

@@ -57,6 +57,7 @@ SIGNATURES = {
     "spl_tc_status": (ct.c_int, [ct.POINTER(ct.c_uint32)]),
     "spl_depth_estimate": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_filter_step": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "spl_depth_estimate_fine": (ct.c_int, [_P, ct.c_int, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_filter_step_detect": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                           _vp, _vp]),
     "spl_filter_step_tc": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),

@@ -185,6 +185,32 @@ spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, const fl
     return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_depth_estimate launch");
 }
 
+spl_status spl_depth_estimate_fine(const spl_params* prm, int S, const spl_hist* z, const float* h,
+                                   const float* prior_mu, const float* prior_var, int32_t* argmax_fine, float* mu,
+                                   float* var, void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, false);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(S >= 1 && S <= 16, "S must be in 1..16 (got %d)", S);
+    SPL_REQUIRE(mu != nullptr && var != nullptr, "mu and var outputs are required");
+    SPL_REQUIRE((prior_mu == nullptr) == (prior_var == nullptr), "give both prior_mu and prior_var or neither");
+    const long long Kf = static_cast<long long>(prm->dmax - prm->dmin) * S + 1;
+    if (Kf > 16384 || fine_warp_bytes(prm->T, prm->dmax - prm->dmin + 1, S) > 200 * 1024) {
+        set_error("fine grid of %lld candidates (S = %d) exceeds the 16384 a warp holds in shared memory", Kf, S);
+        return SPL_EUNSUPPORTED;
+    }
+    EstimateArgs a = base_args(prm, z, h);
+    a.prior_mode = prior_mu ? PRIOR_GAUSS : PRIOR_UNIFORM;
+    a.pmu = prior_mu;
+    a.pvar = prior_var;
+    a.mu = mu;
+    a.var = var;
+    return cuda_status(launch_estimate_fine(a, S, argmax_fine, static_cast<cudaStream_t>(stream)),
+                       "spl_depth_estimate_fine launch");
+}
+
 spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
                            const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
                            const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,

@@ -62,6 +62,9 @@ spl_status check_params(const spl_params* q, bool need_filter);
 
 // Kernel launchers (estimate.cu / aux.cu). They return cudaSuccess or the launch error.
 cudaError_t launch_estimate(const EstimateArgs& a, bool cost_only, cudaStream_t s);
+// Sub-bin grid (fine.cu): S steps per bin; argmax_k receives fine indices. Shared memory per warp: fine_warp_bytes.
+cudaError_t launch_estimate_fine(const EstimateArgs& a, int S, int* argmax_k, cudaStream_t s);
+size_t fine_warp_bytes(int T, int D, int S);
 cudaError_t launch_state_init(int P, float m, float v, float* mu, float* var, cudaStream_t s);
 cudaError_t launch_pi_propagate(int H, int W, const float* nu, const float* pi_in, const uint8_t* faulty,
                                 float* pi_out, cudaStream_t s);

@@ -154,6 +154,21 @@ def test_tensor_core_argument_checks():
     assert lib.spl_tc_status(None) == _abi.SPL_EINVAL
 
 
+def test_fine_grid_argument_checks():
+    """spl_depth_estimate_fine: S in 1..16, the fine grid fits a warp's shared memory; checked on the host."""
+    lib = _abi.load()
+    prm = make_params(4, 4, 1500, 48, 5)
+    hz = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 1504)
+    st = lib.spl_depth_estimate_fine(ct.byref(prm), 0, ct.byref(hz), 0x2000, None, None, None, 0x3000, 0x4000, None)
+    assert st == _abi.SPL_EINVAL and "S must be" in lib.spl_last_error().decode()
+    st = lib.spl_depth_estimate_fine(ct.byref(prm), 17, ct.byref(hz), 0x2000, None, None, None, 0x3000, 0x4000, None)
+    assert st == _abi.SPL_EINVAL
+    st = lib.spl_depth_estimate_fine(ct.byref(prm), 16, ct.byref(hz), 0x2000, None, None, None, 0x3000, 0x4000, None)
+    assert st == _abi.SPL_EUNSUPPORTED and "16384" in lib.spl_last_error().decode()
+    st = lib.spl_depth_estimate_fine(ct.byref(prm), 4, ct.byref(hz), 0x2000, 0x5000, None, None, 0x3000, 0x4000, None)
+    assert st == _abi.SPL_EINVAL and "prior_mu and prior_var" in lib.spl_last_error().decode()
+
+
 def test_detect_argument_checks():
     """spl_filter_step_detect requires pi, refl and bg, keeps the filter's checks, and pi must not alias pi0;
     all decided on the host."""

@@ -457,11 +457,29 @@ def test_fine_grid_half_bin_is_the_average_at_beta_one(orc):
     q = orc.params(T, len(h), peak, beta=1.0)
     rng = _rng(67)
     z = rng.poisson(1.5, size=(2, T)).astype(np.float64)
-    e = orc.estimate_fine(q, 2, h, z, want_ell=True)
-    C = e["ell"] / 2.0                                   # lambda = 2 at beta = 1, no prior
+    e = orc.estimate_fine(q, 2, h, z, want_cost=True)
+    C = e["cost"]
     assert np.allclose(C[:, 1::2], 0.5 * (C[:, 0:-1:2] + C[:, 2::2]), rtol=1e-12, atol=1e-12)
     Ci = orc.cost(q, h, z)
     assert np.allclose(C[:, 0::2], Ci, rtol=1e-12)
+
+
+def test_fine_grid_recovers_a_fractional_surface_exactly(orc):
+    """The histogram equal to A s_{d*} (expected counts of a surface at a fractional depth d* on the fine grid, no
+    background, real-valued) makes the beta-divergence to s_d zero at d = d* and positive elsewhere, so with a flat
+    prior the maximiser is d* itself, for every beta. (Without the template-power term the maximiser is pulled
+    to whole bins, where the interpolated template is more peaked.)"""
+    h, peak = synth.gaussian_irf(2.5, 10)
+    T, S = 160, 8
+    hp = np.concatenate([[0.0], h.astype(np.float64), [0.0]])
+    for beta in (0.3, 0.7, 1.0):
+        q = orc.params(T, len(h), peak, beta=beta)
+        for kstar in (0, 3, 5):
+            dstar = 70 + kstar / S
+            x = np.arange(T) - dstar + peak
+            z = 1e4 * np.interp(x, np.arange(-1, len(h) + 1), hp, left=0.0, right=0.0)
+            e = orc.estimate_fine(q, S, h, z[None])
+            assert q.dmin + e["argmax_k"][0] / S == dstar
 
 
 def test_fine_grid_translation(orc):
