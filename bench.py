@@ -49,23 +49,27 @@ WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.
 # sources' hash differs.
 TRAFFIC_CAPTURES = {
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "intensity.cu"),
-                   "sha256": "70947b27ba5f4e1633e921be34ad6eeb42b567aee0c3d379f8dcc2004c50f276",
-                   "bytes_per_pixel": (201.95e6 + 15.07e6) / 65536},
+                   "sha256": "0710fe083149f06cf64ebfb5eb8d4a772a81eeec2654e4ed9ee6b750fc8dabc0",
+                   "bytes_per_pixel": (202.30e6 + 15.08e6) / 65536,
+                   # warp-instructions of one filter step (depth + intensity launches), mean over frames 0-3 of the
+                   # nine runs (ncu smsp__inst_executed.sum, 36 launches each)
+                   "inst_per_pixel": (390.31e6 + 17.46e6) / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu"),
-                    "sha256": "a9e7b056d03418f0a128a2eb76bc8e040dc82a78885d96d8904a1b9e2a70a4e1",
-                    "bytes_per_pixel": (541.49e6 + 17.19e6) / 65536},
+                    "sha256": "79739b36cf73e920d4795bca6dd3ca1e8446e59bc3404efe5a80cf71efba510e",
+                    "bytes_per_pixel": (542.29e6 + 17.20e6) / 65536},
 }
 
 
-def capture_traffic(kernel: str, pixels: int):
-    """Traffic per launch of `kernel` over `pixels` pixels from its capture, or None if the sources changed."""
+def capture_traffic(kernel: str, pixels: int, key: str = "bytes_per_pixel"):
+    """Traffic (or, key="inst_per_pixel", warp-instructions) per launch of `kernel` over `pixels` pixels from its
+    capture, or None if the sources changed since."""
     import hashlib
     cap = TRAFFIC_CAPTURES[kernel]
     h = hashlib.sha256()
     for f in cap["sources"]:
         with open(os.path.join(ROOT, "paper_2004_09211_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return cap["bytes_per_pixel"] * pixels if h.hexdigest() == cap["sha256"] else None
+    return cap[key] * pixels if h.hexdigest() == cap["sha256"] and key in cap else None
 
 
 def parse():
@@ -281,6 +285,14 @@ def native(args):
                 "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": avg_kernel_s * 1e3,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    # the binding limit: instruction issue (4 warp-instructions per clock per SM), from the captured count
+    inst = capture_traffic("k_estimate", P, "inst_per_pixel")
+    if inst is not None:
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = 4.0 * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        roofline["issue"] = {"achieved": inst / avg_kernel_s, "peak": issue_peak, "unit": "warp-instructions/s",
+                             "frac": inst / avg_kernel_s / issue_peak, "inst_per_step": inst,
+                             "source": "ncu smsp__inst_executed.sum, mean of frames 0-3 of the nine runs"}
 
     e2e = None
     if not args.no_e2e:

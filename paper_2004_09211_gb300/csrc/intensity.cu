@@ -187,10 +187,11 @@ __device__ __forceinline__ float llr_g8(const float* zj, const float* aj, float 
 
 // Writes pixel p's outputs from its solve: the intensity rule of Sec. II-E with the presence decision of the
 // detection surrogate (detect) or of present_now.
+template <bool DETECT>
 __device__ __forceinline__ void write_pixel(const EstimateArgs& a, long long p, bool faulty, bool present_now,
                                             float K, float hsum, float hvar, float r, float b, float llr) {
     bool present = present_now;
-    if (a.detect) {
+    if (DETECT) {
         const float pi = faulty ? 0.5f : presence(a.pi0 ? a.pi0[p] : 0.5f, llr, K, a.var[p], hvar);
         present = !faulty && pi > 0.5f;
         a.pi_out[p] = pi;
@@ -207,7 +208,7 @@ __device__ __forceinline__ void write_pixel(const EstimateArgs& a, long long p, 
 }
 
 // Four pixels per warp (templates of at most 64 taps).
-template <int FMT>
+template <int FMT, bool DETECT>
 __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
     __shared__ float as[SPL_MAX_TAPS];
     __shared__ float s_hsum, s_hvar;
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
         const bool valid = p < P;
         const float K = valid ? a.bg[p] : 0.f;
         const bool faulty = valid && a.faulty ? a.faulty[p] != 0 : false;
-        const bool present = valid && (a.detect || (a.present_now ? a.present_now[p] != 0 : true));
+        const bool present = valid && (DETECT || (a.present_now ? a.present_now[p] != 0 : true));
         const bool need = valid && !faulty && present && K > 0.f && hsum > 0.f;
         const int t0 = need ? window_start(a, a.mu[p]) : 0;
         float zj[8], aj[8];
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
         const float f = fraction_g8(zj, aj, K, a.L, a.T, need);
         const float r = f * K / hsum, b = (1.f - f) * K * (1.f / static_cast<float>(a.T));
         float llr = 0.f;
-        if (a.detect) {  // the evidence with the template at the pseudo-posterior mode
+        if (DETECT) {  // the evidence with the template at the pseudo-posterior mode
             const int t1 = need ? window_start(a, static_cast<float>(a.argmax[p])) : t0;
             float fm = f;
             if (__any_sync(0xffffffffu, t1 != t0)) {  // some group's mode differs from round(mu): solve there
@@ -251,13 +252,13 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
             }
             llr = llr_g8(zj, aj, fm, K, a.T, need);
         }
-        if (valid && sl == 0) write_pixel(a, p, faulty, present, K, hsum, hvar, r, b, llr);
+        if (valid && sl == 0) write_pixel<DETECT>(a, p, faulty, present, K, hsum, hvar, r, b, llr);
         __syncwarp();
     }
 }
 
 // One pixel per warp (any template length up to SPL_MAX_TAPS): the warp-cooperative solve of pixel.cuh.
-template <int FMT>
+template <int FMT, bool DETECT>
 __global__ void __launch_bounds__(256) k_intensity1(const EstimateArgs a) {
     __shared__ float as[SPL_MAX_TAPS];
     __shared__ float s_hsum, s_hvar;
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(256) k_intensity1(const EstimateArgs a) {
     for (long long p = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + warp; p < P; p += stride) {
         const float K = a.bg[p];
         const bool faulty = a.faulty ? a.faulty[p] != 0 : false;
-        const bool present = a.detect || (a.present_now ? a.present_now[p] != 0 : true);
+        const bool present = DETECT || (a.present_now ? a.present_now[p] != 0 : true);
         float r = 0.f, b = 0.f, llr = 0.f;
         if (!faulty && present && K > 0.f && hsum > 0.f) {  // warp-uniform
             constexpr int NQ = SPL_MAX_TAPS / 32;
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(256) k_intensity1(const EstimateArgs a) {
             const float f0 = px::intensity_fraction<NQ>(zj, aj, K, a.L, a.T);
             r = f0 * K / hsum;
             b = (1.f - f0) * K * (1.f / static_cast<float>(a.T));
-            if (a.detect) {  // the evidence with the template at the pseudo-posterior mode
+            if (DETECT) {  // the evidence with the template at the pseudo-posterior mode
                 const int t1 = window_start(a, static_cast<float>(a.argmax[p]));
                 float f = f0;
                 if (t1 != t0) {  // warp-uniform
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(256) k_intensity1(const EstimateArgs a) {
                 llr = s + (kout > 0.f ? kout * log1pf(-f) : 0.f);
             }
         }
-        if (lane == 0) write_pixel(a, p, faulty, present, K, hsum, hvar, r, b, llr);
+        if (lane == 0) write_pixel<DETECT>(a, p, faulty, present, K, hsum, hvar, r, b, llr);
         __syncwarp();
     }
 }
@@ -320,8 +321,13 @@ cudaError_t launch_fmt(const EstimateArgs& a, int nsm, cudaStream_t s) {
     const long long blocks = (P + px_per_block - 1) / px_per_block;
     const long long cap = static_cast<long long>(nsm) * 8;  // at most 8 resident blocks of 256 threads per SM
     const unsigned nb = static_cast<unsigned>(blocks < cap ? blocks : cap);
-    if (a.L <= 64) k_intensity4<FMT><<<nb, 256, 0, s>>>(a);
-    else k_intensity1<FMT><<<nb, 256, 0, s>>>(a);
+    if (a.detect) {  // the detection surrogate's kernels (kept apart: their extra state costs the plain ones)
+        if (a.L <= 64) k_intensity4<FMT, true><<<nb, 256, 0, s>>>(a);
+        else k_intensity1<FMT, true><<<nb, 256, 0, s>>>(a);
+    } else {
+        if (a.L <= 64) k_intensity4<FMT, false><<<nb, 256, 0, s>>>(a);
+        else k_intensity1<FMT, false><<<nb, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
