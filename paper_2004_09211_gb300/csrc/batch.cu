@@ -5,7 +5,8 @@
 // candidate depths) so the largest are taken first. Each warp repeatedly takes the next unit from a device
 // work-queue head (one atomicAdd by lane 0), loads that sequence's IRF into its own shared-memory tables,
 // and processes the tile's pixels one at a time with the same per-pixel arithmetic as the histogram kernel
-// (pixel.cuh). The data term uses the photon-sum form of Eq. beta_div2: C(d) = sum_k g[y_k - d + peak].
+// (pixel.cuh). The data term uses the photon-sum form of Eq. beta_div2: C(d) = sum_k g[y_k - d + peak], formed
+// lane = tap (corr_photons).
 // The queue head is reset by a memset on the launch stream before every step, so a step is a memset node and
 // a kernel node in a CUDA graph. The plan (unit list, descriptor tables, queue heads, status word) is
 // allocated once at creation; nothing is allocated per step.
@@ -51,6 +52,35 @@ __host__ __device__ __forceinline__ BSlice make_bslice(int maxD) {
     s.cs = s.ubs + r4(nb);
     s.words = s.cs + (nb * 32 > SPL_MAX_TAPS ? nb * 32 : SPL_MAX_TAPS);  // cs doubles as the window histogram
     return s;
+}
+
+// C over every candidate from a pixel's photon list (the photon-sum form of Eq. beta_div2), lane = tap: lane l
+// owns taps l + 32 k, and each photon y in list order adds g_j to candidate y - u0 - j for its taps. The
+// candidates of one photon are distinct across lanes and taps and the warp synchronises between photons, so
+// each C(d) is summed in photon order. Returns max C.
+__device__ __forceinline__ float corr_photons(const float* __restrict__ gs, const int* ph, int nk, float* cs, int NB,
+                                             int D, int L, int u0, int lane) {
+    constexpr int KG = SPL_MAX_TAPS / 32;
+    zero_words(cs, NB * 8, lane);
+    float g[KG];
+#pragma unroll
+    for (int k = 0; k < KG; ++k) g[k] = gs[lane + 32 * k];
+    const int ntg = (L + 31) >> 5;
+    float mx = 0.f;
+    for (int e = 0; e < nk; ++e) {
+        const int c = ph[e] - u0 - lane;
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+            const int ck = c - 32 * k;
+            if (k < ntg && static_cast<unsigned>(ck) < static_cast<unsigned>(D)) {
+                const float v = cs[ck] + g[k];
+                cs[ck] = v;
+                mx = fmaxf(mx, v);
+            }
+        }
+        __syncwarp();
+    }
+    return warp_max(mx);
 }
 
 __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, const Unit* __restrict__ units,
@@ -105,8 +135,6 @@ __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, 
         grid.L = L;
         grid.lam2 = lam2;
         grid.gmax = gmax;
-        const int run = (D + 31) >> 5;
-        const int r0 = lane * run, r1 = min(r0 + run, D);
 
         for (int p = un.p0; p < un.p1; ++p) {
             const bool faulty = f.faulty && f.faulty[p];
@@ -141,20 +169,8 @@ __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, 
             if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, SPL_BATCH_BAD_BIN);
             __syncwarp();
 
-            // C(d) over this lane's run of candidates: each photon y adds g[y - u0 - c] for c in reach
-            float mx = 0.f;
-            for (int c = r0; c < r1; ++c) cs[c] = 0.f;
-            for (int k = 0; k < nk; ++k) {
-                const int tc = ph[k] - u0;
-                const int lo = max(tc - L + 1, r0), hi = min(tc, r1 - 1);
-                for (int c = lo; c <= hi; ++c) {
-                    const float v = cs[c] + gs[tc - c];
-                    cs[c] = v;
-                    mx = fmaxf(mx, v);
-                }
-            }
-            __syncwarp();
-            const float cmax = warp_max(mx);
+            // C(d) for every candidate
+            const float cmax = corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane);
 
             // prior from the previous frame's states of this sequence (Eq. predict)
             Prior pr;
@@ -191,15 +207,7 @@ __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, 
                     for (int k = 0; k < nk; ++k) n += (ph[k] >= s_bin) & (ph[k] <= e_bin);
                     return static_cast<float>(n);
                 },
-                [&]() {
-                    for (int c = r0; c < r1; ++c) cs[c] = 0.f;
-                    for (int k = 0; k < nk; ++k) {
-                        const int tc = ph[k] - u0;
-                        const int lo = max(tc - L + 1, r0), hi = min(tc, r1 - 1);
-                        for (int c = lo; c <= hi; ++c) cs[c] += gs[tc - c];
-                    }
-                    __syncwarp();
-                },
+                [&]() { corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane); },
                 lane, bidx, mu, var);
             if (lane == 0) {
                 f.mu_out[p] = mu;
