@@ -57,15 +57,18 @@ struct DiffArgs {
     float* part;           // [grid][kPartial] (backward, accumulated across frames)
 };
 
-// Shared-memory slice of one warp: the row as floats, C, ell.
+// Shared-memory slice of one warp: the row as floats (zero from T on: the blocked correlation's windows read up
+// to 12 bins past the last candidate's), C, ell.
+constexpr int kRowPad = 16;
 struct DSlice {
     int zs, cs, ls, ent, words;
 };
+__host__ __device__ __forceinline__ int dslice_row(int T) { return ((T + 3) & ~3) + kRowPad; }
 __host__ __device__ __forceinline__ DSlice make_dslice(int T, int D) {
     DSlice s;
     const int Dp = (D + 3) & ~3;
     s.zs = 0;
-    s.cs = s.zs + ((T + 3) & ~3);
+    s.cs = s.zs + dslice_row(T);
     s.ls = s.cs + Dp;
     s.ent = s.ls + Dp;
     s.words = s.ent + ((T + 3) & ~3);
@@ -102,13 +105,37 @@ __device__ __forceinline__ PixFwd pixel_forward(const DiffArgs& a, int p, const 
         if (zs[t] != 0.f) ent[o++] = t;
     const int nnz = __shfl_sync(0xffffffffu, incl, 31);
     __syncwarp();
-    // C(d): candidates over lanes, taps in order
-    for (int c = lane; c < D; c += 32) {
-        const float* zz = zs + u0 + c;
-        float acc = 0.f;
-        for (int j = 0; j < L; ++j) acc = fmaf(gs[j], zz[j], acc);
-        cs[c] = acc;
+    // C(d): 8 consecutive candidates per lane from a register window of the row, taps in order in groups of 4
+    // (each C is the same tap-ordered fmaf chain as a per-candidate loop); windows start on 4-bin boundaries
+    const float4* g4 = reinterpret_cast<const float4*>(gs);
+    for (int cb = -(u0 & 3); cb < D; cb += 256) {
+        const int cl = cb + 8 * lane;
+        if (cl < D && cl + 7 >= 0) {
+            const float4* r4 = reinterpret_cast<const float4*>(zs + u0 + cl);
+            float acc[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+            float4 c0 = r4[0], c1 = r4[1];
+            for (int jg = 0; jg < L; jg += 4) {
+                const float4 nx = r4[jg / 4 + 2];
+                const float4 g = g4[jg / 4];
+                const float wv[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, nx.x, nx.y, nx.z, nx.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    acc[r] = fmaf(g.x, wv[r], acc[r]);
+                    acc[r] = fmaf(g.y, wv[r + 1], acc[r]);
+                    acc[r] = fmaf(g.z, wv[r + 2], acc[r]);
+                    acc[r] = fmaf(g.w, wv[r + 3], acc[r]);
+                }
+                c0 = c1;
+                c1 = nx;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (cl + r >= 0 && cl + r < D) cs[cl + r] = acc[r];
+        }
     }
+    __syncwarp();
     // ell and its maximum (ties to the smallest candidate)
     float best = -INFINITY;
     int bidx = 0x7fffffff;
@@ -185,12 +212,13 @@ __device__ __forceinline__ void load_irf(const DiffArgs& a, float* gs) {
 
 __global__ void __launch_bounds__(256) k_diff_forward(const DiffArgs a, DSlice sl) {
     extern __shared__ __align__(16) float dyn[];
-    __shared__ float gs[SPL_MAX_TAPS];
+    __shared__ __align__(16) float gs[SPL_MAX_TAPS];
     __shared__ float wl[8];
     load_irf(a, gs);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
     float* zs = base + sl.zs;
+    for (int t = a.T + lane; t < dslice_row(a.T); t += 32) zs[t] = 0.f;  // the row loads never write past T
     float* cs = base + sl.cs;
     float* ls = base + sl.ls;
     int* ent = reinterpret_cast<int*>(base + sl.ent);
@@ -225,12 +253,13 @@ __global__ void __launch_bounds__(256) k_diff_forward(const DiffArgs a, DSlice s
 
 __global__ void __launch_bounds__(256) k_diff_backward(const DiffArgs a, DSlice sl) {
     extern __shared__ __align__(16) float dyn[];
-    __shared__ float gs[SPL_MAX_TAPS];
+    __shared__ __align__(16) float gs[SPL_MAX_TAPS];
     __shared__ float red[8][kPartial];
     load_irf(a, gs);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
     float* zs = base + sl.zs;
+    for (int t = a.T + lane; t < dslice_row(a.T); t += 32) zs[t] = 0.f;  // the row loads never write past T
     float* cs = base + sl.cs;
     float* ls = base + sl.ls;
     int* ent = reinterpret_cast<int*>(base + sl.ent);
