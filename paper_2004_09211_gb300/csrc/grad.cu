@@ -503,9 +503,12 @@ DiffArgs make_args(const spl_params* q, const spl_hist* z, const float* h, float
 }
 
 // Warps per CTA (up to 8) whose slices fit in 200 KB of shared memory.
+// Warps per CTA: the grid is two CTAs per SM, so size a CTA to let both be resident (half of about 200 KB of
+// shared memory each) when one warp's slice allows it; otherwise one CTA per SM.
 int warps_for(const DSlice& ds) {
     const size_t per = sizeof(float) * ds.words;
-    const int w = static_cast<int>((200u * 1024u) / per);
+    const int two = static_cast<int>((100u * 1024u) / per);
+    const int w = two >= 1 ? two : static_cast<int>((200u * 1024u) / per);
     return w > 8 ? 8 : w;
 }
 
