@@ -56,7 +56,10 @@ TRAFFIC_CAPTURES = {
                    "inst_per_pixel": (390.31e6 + 17.46e6) / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu"),
                     "sha256": "79739b36cf73e920d4795bca6dd3ca1e8446e59bc3404efe5a80cf71efba510e",
-                    "bytes_per_pixel": (542.29e6 + 17.20e6) / 65536},
+                    "bytes_per_pixel": (542.29e6 + 17.20e6) / 65536,
+                    # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture
+                    # of a 256 x 256 frame of the mixed workload
+                    "inst_per_pixel": (343.21e6 + 16.98e6) / 65536},
 }
 
 
@@ -1019,6 +1022,13 @@ def mixed(args):
         cpu = mixed_cpu_baseline(spl, synth, h, hd, peak, sc, dev)
 
     rt, rf = statistics.mean(rmse_tc), statistics.mean(rmse_fp32)
+    inst = capture_traffic("k_filter_tc", P, "inst_per_pixel")
+    if inst is not None:
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = 4.0 * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        roofline["issue"] = {"achieved": inst / frame_s, "peak": issue_peak, "unit": "warp-instructions/s",
+                             "frac": inst / frame_s / issue_peak, "inst_per_step": inst,
+                             "source": "ncu smsp__inst_executed.sum of one 256 x 256 step, scaled by the pixels"}
     line = {"metric": "pixel-frames/s", "value": P * N / (ms / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 x f16 -> f32 (tensor), f32 epilogue",
