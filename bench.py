@@ -60,6 +60,16 @@ TRAFFIC_CAPTURES = {
                     # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture
                     # of a 256 x 256 frame of the mixed workload
                     "inst_per_pixel": (343.21e6 + 16.98e6) / 65536},
+    # one launch of the photon-list kernel over all 64 sequences of the batched workload (7 050 240 pixels)
+    "k_batch": {"sources": ("batch.cu", "pixel.cuh"),
+                "sha256": "873cefe879aacd19fac8786189689c74b59cd3aecd920ba6d05a93ffebf97ea1",
+                "bytes_per_pixel": (457.70e6 + 124.52e6) / 7050240,
+                "inst_per_pixel": 26806.0e6 / 7050240},
+    # one backward launch of the differentiable filter (a 128 x 128 frame, T = 1024)
+    "k_diff_backward": {"sources": ("grad.cu", "pixel.cuh"),
+                        "sha256": "3a4957cdfa4f3d4133cd5908c6e504be9c1068f46da005053d300b27dc2d2669",
+                        "bytes_per_pixel": (33.98e6 + 0.0) / 16384,
+                        "inst_per_pixel": 262.62e6 / 16384},
 }
 
 
@@ -73,6 +83,27 @@ def capture_traffic(kernel: str, pixels: int, key: str = "bytes_per_pixel"):
         with open(os.path.join(ROOT, "paper_2004_09211_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return cap[key] * pixels if h.hexdigest() == cap["sha256"] and key in cap else None
+
+
+def hbm_roofline(peaks, alg_bytes, launch_s, traffic, kernel, **extra):
+    """The HBM roof of a launch: `alg_bytes` algorithmic bytes over `launch_s` seconds against the measured copy
+    bandwidth; `traffic` is the captured DRAM bytes per launch or None."""
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / launch_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": traffic, "kernel": kernel, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_s * 1e3,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s", **extra}
+
+
+def issue_roofline(dev, peaks, inst, launch_s, source):
+    """The instruction-issue roof of a launch: `inst` warp-instructions (from its capture) over `launch_s` seconds
+    against 4 warp-instructions per clock per SM at the maximum SM clock; None without a valid capture."""
+    if inst is None:
+        return None
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 4.0 * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    return {"achieved": inst / launch_s, "peak": peak, "unit": "warp-instructions/s",
+            "frac": inst / launch_s / peak, "inst_per_launch": inst, "source": source}
 
 
 def parse():
@@ -563,6 +594,18 @@ def batched(args):
     for pl in plans:
         spl.spl_batch_destroy(pl)
     spl.spl_batch_destroy(plan)
+    # roofline of k_batch: algorithmic bytes per launch (one frame of every sequence) = 4 B per photon (bin
+    # index) + 32 B per pixel (list offset, previous state, new state, argmax, refl, bg); its average launch time
+    # = the graph's time over its 10 frames (each frame's node pair is a 4-byte memset and the kernel)
+    peaks = _peaks()
+    P_all = units // BATCH_FRAMES
+    launch_s = ms / BATCH_FRAMES / 1e3
+    roofline = hbm_roofline(
+        peaks, 4 * photons // BATCH_FRAMES + 32 * P_all, launch_s, capture_traffic("k_batch", P_all),
+        "k_batch (one frame of all 64 sequences)",
+        issue=issue_roofline(dev, peaks, capture_traffic("k_batch", P_all, "inst_per_pixel"), launch_s,
+                             "ncu smsp__inst_executed.sum of one launch of this workload"),
+        note="latency-bound: up to 4049 candidates per pixel from at most 30 photons")
     line = {"metric": "pixel-frames/s", "value": units / (ms / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -572,8 +615,8 @@ def batched(args):
                        "graph": "10 persistent launches captured in one CUDA graph"},
             "unbatched": {"value": units / (ms_unbatched / 1e3), "ms_per_step": ms_unbatched,
                           "note": "same sequences, one single-sequence plan per sequence, 640 launches"},
-            "status_flags": flags, "gpu_launches": 2 * BATCH_FRAMES * args.steps, "clocks": clk.summary(),
-            "roofline": None}
+            "status_flags": flags, "gpu_launches": BATCH_FRAMES * args.steps, "clocks": clk.summary(),
+            "roofline": roofline}
     print(json.dumps(line), flush=True)
 
 
@@ -606,30 +649,48 @@ def diff(args):
     var_s = torch.empty(N + 1, P, device=dev)
     scratch = torch.empty(spl.spl_diff_scratch_size(prm), dtype=torch.uint8, device=dev)
 
-    def step():
+    def step(ev=None):
         spl.spl_state_init(prm, mu_s[0], var_s[0])
         fw = spl.spl_diff_forward(prm, z, hd, 0.5, d_ref=d_ref, mu_states=mu_s, var_states=var_s, scratch=scratch)
+        if ev is not None:
+            ev[0].record()
         bw = spl.spl_diff_backward(prm, z, hd, 0.5, d_ref, mu_s, var_s, scratch=scratch)
+        if ev is not None:
+            ev[1].record()
         return fw, bw
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(0) as clk:
         e0.record()
-        for _ in range(args.steps):
-            fw, bw = step()
+        for i in range(args.steps):
+            fw, bw = step(bev[i])
         e1.record()
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
+    # roofline of the dominant kernel, k_diff_backward (65 % of the step): algorithmic bytes per launch = the
+    # frame's rows (2 T per pixel) + the previous states and this state's adjoints (16 B) + d_ref (4 B) + the
+    # 9 x 2 neighbour-state adjoints written (72 B); its average launch time = spl_diff_backward's event time
+    # over its N launches (the call's 19 gather launches and one finalize launch, about 1 % of it, included)
+    peaks = _peaks()
+    bw_s = sum(a.elapsed_time(b) for a, b in bev) / args.steps / N / 1e3
+    roofline = hbm_roofline(
+        peaks, P * (2 * Td + 92), bw_s, capture_traffic("k_diff_backward", P),
+        "k_diff_backward (one frame of the reverse sweep)",
+        issue=issue_roofline(dev, peaks, capture_traffic("k_diff_backward", P, "inst_per_pixel"), bw_s,
+                             "ncu smsp__inst_executed.sum of one backward launch"),
+        note="latency-bound at 12 resident warps per SM (register and shared-memory limits)")
     line = {"metric": "pixel-frames/s", "value": P * N / (ms / 1e3), "unit": "pixel-frames/s (forward+backward)",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "differentiable 128x128x20 frames, T=1024, L=48, tau=0.5", "pixels": P,
                        "frames": N},
             "loss": float(fw["loss"].item()), "grad_beta": float(bw["grad_beta"].item()),
-            "gpu_launches": (1 + N + 1 + 2 * N + 1) * args.steps, "clocks": clk.summary(), "roofline": None}
+            "gpu_launches": (1 + N + 1 + N + (N - 1) + 1) * args.steps, "clocks": clk.summary(),
+            "roofline": roofline}
     print(json.dumps(line), flush=True)
 
 
@@ -674,6 +735,11 @@ def video_tc(args):
     flags = spl.spl_tc_status()
     ms_32, rmse_32 = timed(spl.spl_filter_step, videos)
     runs = [f"SBR {sb} beta {b}" for sb in SBRS for b in BETAS]
+    # roofline of one filter step (tensor-core depth launch + intensity launch): FP16 row (2 T) + previous state
+    # (8 B) + outputs (20 B) per pixel; time per step = job time / steps (no capture of this workload)
+    roofline = hbm_roofline(_peaks(), P * (2 * T + 8 + 20), ms_tc / 1e3 / (len(SBRS) * len(BETAS) * frames), None,
+                            "k_filter_tc + k_intensity4 (one spl_filter_step_tc)",
+                            note="traffic not captured for this workload")
     line = {"metric": "pixel-frames/s", "value": units / (ms_tc / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_tc, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 x f16 -> f32 (tensor), f32 epilogue",
@@ -683,7 +749,7 @@ def video_tc(args):
             "fp32_path": {"value": units / (ms_32 / 1e3), "ms_per_step": ms_32, "speedup_tc_over_fp32": ms_32 / ms_tc},
             "depth_rmse_bins_last_frame": {r: {"tc": a, "fp32": b} for r, a, b in zip(runs, rmse_tc, rmse_32)},
             "status_flags": flags, "gpu_launches": len(SBRS) * len(BETAS) * (2 * frames + 1) * args.steps,
-            "clocks": clk.summary(), "roofline": None, "e2e": None}
+            "clocks": clk.summary(), "roofline": roofline, "e2e": None}
     print(json.dumps(line), flush=True)
 
 
@@ -761,6 +827,12 @@ def detect(args):
             o = spl.spl_filter_step_detect(prm, zbg, hd, mu[frames & 1], var[frames & 1], stream=stream)
             p_fa[f"SBR {sbr} beta {BETAS[bi]}"] = float(o["present"].float().mean())
     ms_plain = timed(lambda: run_job(spl, prms, hd, videos, states, outs, stream))
+    # roofline of one detect step (depth launch + detecting intensity launch + pi propagation): uint16 row (2 T) +
+    # previous state (8 B) + present_in (1 B) + pi0 (4 B) + outputs mu, var, argmax, refl, bg, pi, present (25 B)
+    # + the propagation's pi read and pi0 write (8 B) per pixel; time per step = job time / steps
+    roofline = hbm_roofline(_peaks(), P * (2 * T + 46), ms_det / 1e3 / (len(SBRS) * len(BETAS) * frames), None,
+                            "k_estimate<u16> + k_intensity4<detect> + k_pi_propagate (one frame)",
+                            note="traffic not captured for this workload")
     line = {"metric": "pixel-frames/s", "value": units / (ms_det / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_det, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -769,7 +841,7 @@ def detect(args):
             "plain_path": {"value": units / (ms_plain / 1e3), "ms_per_step": ms_plain,
                            "detection_overhead": ms_det / ms_plain - 1.0},
             "detection_rate_last_frame": p_d, "false_alarm_rate_background_frame": p_fa,
-            "gpu_launches": launches, "clocks": clk.summary(), "roofline": None, "e2e": None}
+            "gpu_launches": launches, "clocks": clk.summary(), "roofline": roofline, "e2e": None}
     print(json.dumps(line), flush=True)
 
 
@@ -808,6 +880,13 @@ def fine(args):
             ms = timed(lambda z: spl.spl_depth_estimate_fine(prm, S, z, hd))
             res[f"S={S}"] = {"ms_per_frame": ms, "pixel_estimates_per_s": P / (ms / 1e3),
                              "candidates_per_pixel": (prm.dmax - prm.dmin) * S + 1}
+    # roofline of k_estimate_fine at S = 4: algorithmic bytes per launch = the uint16 row (2 T) + argmax_k, mu,
+    # var (12 B) per pixel (the uniform prior reads nothing)
+    peaks = _peaks()
+    launch_s = res["S=4"]["ms_per_frame"] / 1e3
+    roofline = hbm_roofline(peaks, P * (2 * T + 12), launch_s, None, "k_estimate_fine<u16> (S = 4, one frame)",
+                            note="traffic not captured for this workload; every one of the 4 (D - 1) + 1 "
+                                 "candidates is evaluated exactly (no pruning)")
     line = {"metric": "pixel-estimates/s", "value": res["S=4"]["pixel_estimates_per_s"],
             "unit": "pixel-estimates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["S=4"]["ms_per_frame"], "higher_is_better": True, "scaling": "weak",
@@ -815,7 +894,8 @@ def fine(args):
             "config": {"workload": "sub-bin single-frame estimate, S = 4, video frames 256x256, T=1500, SBR 1, "
                                    "beta 0.5, uniform prior", "frames": frames},
             "by_S": res, "integer_grid": {"ms_per_frame": ms_int, "pixel_estimates_per_s": P / (ms_int / 1e3)},
-            "gpu_launches": (4 + 1) * args.steps * len(zs), "clocks": clk.summary(), "roofline": None, "e2e": None}
+            "gpu_launches": (4 + 1) * args.steps * len(zs), "clocks": clk.summary(), "roofline": roofline,
+            "e2e": None}
     print(json.dumps(line), flush=True)
 
 
@@ -890,14 +970,21 @@ def pd_curves(args):
                 limit[f"{m:.4g}"] = float(sbr[good[0]]) if good else None
             out[f"beta {beta}"] = {"limiting_sbr_by_msc": limit, "pd_grid": ok.numpy().round(4).tolist()}
     ms = sum(ms_all)
+    # roofline of k_estimate on this workload: algorithmic bytes per launch = the uint16 row (2 T) + the Gaussian
+    # prior (8 B) + mu, var, argmax (12 B) per pixel; average launch time over the five betas' launches
+    peaks = _peaks()
+    launch_s = ms / len(PD_BETAS) / 1e3
+    roofline = hbm_roofline(peaks, P * (2 * PD_T + 8 + 12), launch_s, None,
+                            "k_estimate<u16> (one spl_depth_estimate over all cells of one beta)",
+                            note="traffic not captured for this workload")
     line = {"metric": "pixel-estimates/s", "value": P * len(PD_BETAS) / (ms / 1e3), "unit": "pixel-estimates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "single-pixel p_d experiment (Sec. IV-A, Gaussian IRF FWHM 28, T=1500, prior "
                                    "N(600, 2500), eta 28): 25 SBR x 13 MSC x 2000 histograms per beta",
                        "sbr_grid": sbr.tolist(), "msc_grid": msc.tolist(), "betas": list(PD_BETAS), "pixels": P},
-            "curves": out, "gpu_launches": 2 * len(PD_BETAS) * args.steps, "clocks": clk.summary(),
-            "roofline": None, "e2e": None}
+            "curves": out, "gpu_launches": len(PD_BETAS) * args.steps, "clocks": clk.summary(),
+            "roofline": roofline, "e2e": None}
     print(json.dumps(line), flush=True)
 
 

@@ -13,8 +13,9 @@
 // Mapping: one warp per pixel (persistent grid). The row is converted to floats in the warp's shared slice
 // (zero past T); each phase's correlation is register-blocked (8 candidates per lane, taps in groups of 4);
 // C of every fine candidate goes to shared memory, then two passes give the smallest maximiser of
-// ell = lambda log2(e) C + log2 N(d; prior) and the argmax-centred moments. No pruning: every candidate is
-// evaluated exactly in the log domain.
+// ell = lambda log2(e) C + log2 N(d; prior) and the argmax-centred moments, and a third pass takes the moments
+// again about the rounded mean when it lies more than two standard deviations from the maximiser. No pruning:
+// every candidate is evaluated exactly in the log domain.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -180,11 +181,32 @@ __global__ void __launch_bounds__(256) k_estimate_fine(const FineArgs a) {
         s0 = warp_sum(s0);
         s1 = warp_sum(s1);
         s2 = warp_sum(s2);
+        int ctr = bk;
+        float m1 = s1 / s0;
+        float var = s2 / s0 - m1 * m1;
+        if (m1 * m1 > 4.f * var + 1.f) {
+            // pass 3: the maximiser lies more than two standard deviations from the mean (a broad or bimodal
+            // posterior), where S2/S0 and the squared offset would cancel: the moments again about the rounded
+            // mean
+            ctr = __float2int_rn(static_cast<float>(bk) + m1);
+            s0 = s1 = s2 = 0.f;
+            for (int k = lane; k < Kf; k += 32) {
+                const float w = ex2(cs[k] - best);
+                const float dd = static_cast<float>(k - ctr);
+                s0 += w;
+                s1 = fmaf(w, dd, s1);
+                s2 = fmaf(w * dd, dd, s2);
+            }
+            s0 = warp_sum(s0);
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            m1 = s1 / s0;
+            var = s2 / s0 - m1 * m1;
+        }
         if (lane == 0) {
-            const float m1 = s1 / s0;
             if (a.argmax) a.argmax[p] = bk;
-            a.mu[p] = static_cast<float>(a.dmin) + (static_cast<float>(bk) + m1) * invS;
-            a.var[p] = fmaxf(s2 / s0 - m1 * m1, 0.f) * invS * invS;
+            a.mu[p] = static_cast<float>(a.dmin) + (static_cast<float>(ctr) + m1) * invS;
+            a.var[p] = fmaxf(var, 0.f) * invS * invS;
         }
         __syncwarp();
     }

@@ -93,6 +93,7 @@ def test_filter_tc_masks_and_stencil(orc):
     (7, 9, 333, 45, 40, None, None),        # odd T, padded pitch, D not a multiple of 64
     (2, 70, 2049, 128, 60, None, None),     # largest supported IRF (4 slabs per window, deeper intensity window)
     (9, 31, 1000, 80, 20, 300, 500),        # sub-range far from bin 0 (count-only slabs on both sides)
+    (2, 9, 8192, 128, 70, None, None),      # largest supported histogram and IRF (128 slabs per row)
 ])
 def test_filter_tc_ragged_shapes(orc, H, W, T, L, peak, dmin, dmax):
     rng = np.random.default_rng(H * 1000 + W + 7)

@@ -35,6 +35,7 @@ def _np(t):
     (7, 33, 260, torch.float32, True),
     (3, 128, 400, torch.float16, False),
     (16, 9, 90, torch.uint16, True),
+    (2, 128, 8192, torch.uint16, True),  # largest histogram and IRF: 16129 fine candidates, one or two warps per CTA
 ])
 def test_fine_grid_matches_the_oracle(orc, S, L, T, dtype, prior):
     H, W = 3, 11
@@ -46,8 +47,9 @@ def test_fine_grid_matches_the_oracle(orc, S, L, T, dtype, prior):
         for x in range(W):
             d = int(rng.integers(q.dmin, q.dmax + 1))
             z[y, x, d - peak:d - peak + len(h)] += rng.poisson(12 * h / h.max())
-    pm = rng.uniform(q.dmin, q.dmax, size=(H, W)) if prior else None
-    pv = rng.uniform(50, 4000, size=(H, W)) if prior else None
+    # the prior as the GPU receives it (FP32), for both sides
+    pm = rng.uniform(q.dmin, q.dmax, size=(H, W)).astype(np.float32).astype(np.float64) if prior else None
+    pv = rng.uniform(50, 4000, size=(H, W)).astype(np.float32).astype(np.float64) if prior else None
     prm = spl.make_params(H, W, T, len(h), peak, beta=0.45)
     dp = (lambda a: torch.from_numpy(a.astype(np.float32)).to(DEV).reshape(-1)) if prior else (lambda a: None)
     o = spl.spl_depth_estimate_fine(prm, S, _gpu_hist(z, T, dtype), torch.from_numpy(h).to(DEV),
@@ -102,3 +104,37 @@ def test_fractional_surface_is_resolved_below_one_bin(orc):
     rmse_int = np.sqrt(np.mean((_np(a["argmax"]) - dstar) ** 2))
     rmse_fine = np.sqrt(np.mean((prm.dmin + _np(b["argmax_k"]) / S - dstar) ** 2))
     assert rmse_int > 0.2 and rmse_fine < rmse_int / 3
+
+
+def test_off_centre_posterior_moments(orc):
+    """A tall, narrow data peak (2-4 photons in one bin, Gaussian IRF sigma = 1 bin) 2.2-3.2 prior standard
+    deviations away from a broad Gaussian prior: the maximiser sits on the peak while most of the mass lies under
+    the prior, so the mean is far from the maximiser (m1^2 > 4 var + 1 in fine units for about half the pixels,
+    checked on the oracle) and the moments are taken again about the rounded mean."""
+    S, T, H, W = 4, 700, 4, 8
+    h, peak = synth.gaussian_irf(1.0, 4)
+    q = orc.params(T, len(h), peak, beta=0.5)
+    rng = np.random.default_rng(77)
+    z = np.zeros((H, W, T))
+    pm = np.zeros((H, W), np.float32)
+    pv = np.zeros((H, W), np.float32)
+    for y in range(H):
+        for x in range(W):
+            d1 = int(rng.integers(q.dmin + 150, q.dmax - 150))
+            z[y, x, d1] += int(rng.integers(2, 5))
+            sd = float(rng.uniform(60, 110))
+            pm[y, x] = d1 + peak + rng.choice([-1, 1]) * rng.uniform(2.2, 3.2) * sd
+            pv[y, x] = sd * sd
+    e = orc.estimate_fine(q, S, h, z, prior_mu=pm.astype(np.float64), prior_var=pv.astype(np.float64),
+                          want_ell=True)
+    m1 = (e["mu"].reshape(-1) - q.dmin) * S - e["argmax_k"].reshape(-1)
+    far = m1 * m1 > 4 * e["var"].reshape(-1) * S * S + 1
+    assert 8 <= far.sum() < H * W  # both branches of the moment pass
+    prm = spl.make_params(H, W, T, len(h), peak, beta=0.5)
+    o = spl.spl_depth_estimate_fine(prm, S, _gpu_hist(z, T, torch.uint16), torch.from_numpy(h).to(DEV),
+                                    prior_mu=torch.from_numpy(pm).to(DEV).reshape(-1),
+                                    prior_var=torch.from_numpy(pv).to(DEV).reshape(-1))
+    torch.cuda.synchronize()
+    check_argmax(_np(o["argmax_k"]), e["argmax_k"].reshape(-1), e["ell"].reshape(H * W, -1), 0, "argmax_k")
+    check_close(_np(o["mu"]), e["mu"], "mu")
+    check_close(_np(o["var"]), e["var"], "var", atol=1e-6)

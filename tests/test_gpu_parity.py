@@ -244,6 +244,32 @@ def test_sparse_rows_long_templates(orc, L, peak, bg):
     _run_filter(orc, q, prm, h, [z, z[:, ::-1].copy()], T)
 
 
+@pytest.mark.parametrize("dtype", [torch.uint16, torch.float16, torch.float32])
+def test_largest_supported_histogram(orc, dtype):
+    """T = SPL_MAX_BINS (8192) with the largest IRF (L = SPL_MAX_TAPS = 128): the largest shared-memory slices
+    (one warp per CTA for FP32 rows), 253 candidate blocks, and dense and zero-skip rows side by side."""
+    H, W, T, L, peak = 2, 9, 8192, 128, 70
+    rng = np.random.default_rng(8192)
+    h = rng.uniform(0.0, 1.0, size=L).astype(np.float32)
+    h[peak] = 2.0
+    h /= h.sum()
+    q = orc.params(T, L, peak, beta=0.6, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    bg = np.where(np.arange(W) % 2 == 0, 0.002, 0.05)  # 27-127 and 390-550 non-empty bins per row
+    z = rng.poisson(np.broadcast_to(bg[None, :, None], (H, W, T))).astype(np.float64)
+    for y in range(H):
+        for x in range(W):
+            d = int(rng.integers(q.dmin, q.dmax + 1))
+            # weak (broad posterior over 8065 candidates) and strong (var < 0.1 bin^2) surfaces
+            z[y, x, d - peak:d - peak + L] += rng.poisson((20.0 if (x + y) % 3 == 0 else 300.0) * h)
+    prm = spl.make_params(H, W, T, L, peak, beta=0.6, sigma_rw2=3.0)
+    cost, am = spl.spl_depth_cost(prm, _gpu_hist(z, T, dtype), torch.from_numpy(h).to(DEV))
+    torch.cuda.synchronize()
+    C = orc.cost(q, h, z).reshape(H * W, -1)
+    check_close(_np(cost), C, "C", atol=1e-6 * C.max())
+    check_argmax(_np(am), C.argmax(1) + q.dmin, C, q.dmin)
+    _run_filter(orc, q, prm, h, [z, z[::-1].copy()], T, dtype=dtype)
+
+
 def _logit(p):
     p = np.clip(np.asarray(p, np.float64), 1e-300, 1 - 1e-16)
     return np.log(p) - np.log1p(-p)
