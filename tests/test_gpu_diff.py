@@ -86,3 +86,52 @@ def test_diff_backward_is_bitwise_reproducible_and_autograd_wired():
     for name, a, b in zip(("grad_h", "grad_beta", "grad_nu", "loss"), grads[0], grads[1]):
         assert torch.equal(a, b), f"{name}: max |diff| {(a - b).abs().max().item():.3g}, run 1 {a[:4].tolist()}"
     assert torch.isfinite(grads[0][0]).all() and torch.isfinite(grads[0][2]).all()
+
+
+def test_diff_forward_off_centre_posteriors():
+    """From a broad prior state (every pixel N(x0, 50^2)), 3-6 photons in one bin 3.0-3.6 prior standard deviations
+    away: the maximiser sits on the photons while most of the mass stays under the prior, so for about a third of
+    the pixels (checked on the oracle) the posterior mean lies more than two standard deviations from the
+    maximiser, about which the forward pass centres its moment sums (the variance's relative rounding error grows
+    like 1e-7 (1 + m1^2 / var): about 1e-6 here). States and readouts of two frames against the FP64 oracle's
+    frames from the same initial state."""
+    from oracle import diff_oracle as dor
+    H, W, T, beta, tau, sigma_rw2 = 5, 6, 500, 0.5, 0.5, 3.0
+    h, peak = synth.asymmetric_irf(L=24)
+    nu = synth.cross_weights(0.5)
+    rng = np.random.default_rng(91)
+    dmin, dmax = peak, T - len(h) + peak
+    x0 = 0.5 * (dmin + dmax)
+    mu0 = np.full((H, W), x0, np.float32)
+    var0 = np.full((H, W), 2500.0, np.float32)
+    z = np.zeros((H, W, T))
+    for y in range(H):
+        for x in range(W):
+            d = int(round(x0 + rng.choice([-1, 1]) * rng.uniform(3.0, 3.6) * 50))
+            z[y, x, d] += int(rng.integers(3, 7))  # the IRF maximum of a surface at depth d falls in bin d
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64)
+    ref, m, v = [], t(mu0), t(var0)
+    for _ in range(2):
+        m, v, ds = dor.frame(t(h), t(beta), t(nu), t(z), m, v, peak, dmin, dmax, sigma_rw2, tau)
+        ref.append((m.numpy(), v.numpy(), ds.numpy()))
+    # the regime: posterior mean more than two standard deviations from the maximiser of ell
+    g = t(h).clamp(min=1e-300) ** beta
+    C = t(z).unfold(-1, len(h), 1)[..., dmin - peak:dmax - peak + 1, :] @ g
+    cm, cv = dor._stencil_components(t(mu0), t(var0), t(nu), sigma_rw2, dmin, dmax)
+    e = torch.arange(dmin, dmax + 1, dtype=torch.float64).view(1, 1, -1, 1) - cm.unsqueeze(2)
+    lp = torch.logsumexp(torch.log(t(nu)).view(1, 1, 1, 9) - 0.5 * torch.log(2 * np.pi * cv).unsqueeze(2)
+                         - e * e / (2 * cv.unsqueeze(2)), -1)
+    am = ((beta + 1) / beta * C + lp).argmax(-1).numpy() + dmin
+    m1 = ref[0][0] - am
+    assert (m1 * m1 > 4 * ref[0][1] + 1).sum() >= 8
+    prm = spl.make_params(H, W, T, len(h), peak, beta=beta, sigma_rw2=sigma_rw2, nu=nu)
+    ms = torch.empty(3, H * W, device=DEV)
+    vs = torch.empty(3, H * W, device=DEV)
+    ms[0] = torch.from_numpy(mu0.reshape(-1)).to(DEV)
+    vs[0] = torch.from_numpy(var0.reshape(-1)).to(DEV)
+    fw = spl.spl_diff_forward(prm, _gpu_z([z, z], T), torch.from_numpy(h).to(DEV), tau, mu_states=ms, var_states=vs)
+    torch.cuda.synchronize()
+    for n in range(2):
+        check_close(ms[n + 1].cpu().numpy(), ref[n][0], f"mu frame {n}")
+        check_close(vs[n + 1].cpu().numpy(), ref[n][1], f"var frame {n}", atol=1e-6)
+        check_close(fw["dsoft"][n].cpu().numpy(), ref[n][2], f"dsoft frame {n}")
