@@ -65,11 +65,12 @@ TRAFFIC_CAPTURES = {
                 "sha256": "873cefe879aacd19fac8786189689c74b59cd3aecd920ba6d05a93ffebf97ea1",
                 "bytes_per_pixel": (457.70e6 + 124.52e6) / 7050240,
                 "inst_per_pixel": 26806.0e6 / 7050240},
-    # one backward launch of the differentiable filter (a 128 x 128 frame, T = 1024)
+    # backward launches of the differentiable filter (128 x 128 frames, T = 1024): mean over the 20 launches of
+    # one reverse sweep
     "k_diff_backward": {"sources": ("grad.cu", "pixel.cuh"),
                         "sha256": "3a4957cdfa4f3d4133cd5908c6e504be9c1068f46da005053d300b27dc2d2669",
-                        "bytes_per_pixel": (33.98e6 + 0.0) / 16384,
-                        "inst_per_pixel": 262.62e6 / 16384},
+                        "bytes_per_pixel": (34.11e6 + 0.0) / 16384,
+                        "inst_per_pixel": 261.2e6 / 16384},
 }
 
 
@@ -681,7 +682,7 @@ def diff(args):
         peaks, P * (2 * Td + 92), bw_s, capture_traffic("k_diff_backward", P),
         "k_diff_backward (one frame of the reverse sweep)",
         issue=issue_roofline(dev, peaks, capture_traffic("k_diff_backward", P, "inst_per_pixel"), bw_s,
-                             "ncu smsp__inst_executed.sum of one backward launch"),
+                             "ncu smsp__inst_executed.sum, mean of the 20 backward launches of one step"),
         note="latency-bound at 12 resident warps per SM (register and shared-memory limits)")
     line = {"metric": "pixel-frames/s", "value": P * N / (ms / 1e3), "unit": "pixel-frames/s (forward+backward)",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
