@@ -188,33 +188,35 @@ __device__ __forceinline__ void lin_run(const Grid& g, const Prior& pr, float* c
         v[i] = q[i] = 0.f;
         kk[i] = i < pr.n ? ex2(-2.f * pr.ck[i]) : 0.f;
     }
-    for (int c = r0; c < r1; ++c) {
-        const float d = static_cast<float>(g.dmin + c);
-        if (((c - r0) & (kRestart - 1)) == 0) {  // exact restart of every component
-#pragma unroll
-            for (int i = 0; i < NC; ++i) {
-                const float e = d - pr.cm[i];
-                v[i] = i < pr.n ? ex2(pr.ca[i] - pr.ck[i] * e * e - sref) : 0.f;
-                q[i] = i < pr.n ? ex2(fminf(-pr.ck[i] * (2.f * e + 1.f), 100.f)) : 0.f;
-            }
-        }
-        float m = NC == 0 ? 1.f : 0.f;
+    float dd = static_cast<float>(r0 - cstar);  // offset of candidate c from cstar (integers below 2^24: exact)
+    for (int c0 = r0; c0 < r1; c0 += kRestart) {
+        const float d = static_cast<float>(g.dmin + c0);  // exact restart of every component
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            m += v[i];
-            v[i] *= q[i];
-            q[i] *= kk[i];
+            const float e = d - pr.cm[i];
+            v[i] = i < pr.n ? ex2(pr.ca[i] - pr.ck[i] * e * e - sref) : 0.f;
+            q[i] = i < pr.n ? ex2(fminf(-pr.ck[i] * (2.f * e + 1.f), 100.f)) : 0.f;
         }
-        const float w = ex2(fmaf(g.lam2, cs[c], -xref)) * m;
-        cs[c] = w;
-        if (w > best) {
-            best = w;
-            bidx = c;
+        const int c1 = min(c0 + kRestart, r1);
+        for (int c = c0; c < c1; ++c) {
+            float m = NC == 0 ? 1.f : 0.f;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                m += v[i];
+                v[i] *= q[i];
+                q[i] *= kk[i];
+            }
+            const float w = ex2(fmaf(g.lam2, cs[c], -xref)) * m;
+            cs[c] = w;
+            if (w > best) {
+                best = w;
+                bidx = c;
+            }
+            s0 += w;
+            s1 = fmaf(w, dd, s1);
+            s2 = fmaf(w * dd, dd, s2);
+            dd += 1.f;
         }
-        const float dd = static_cast<float>(c - cstar);
-        s0 += w;
-        s1 = fmaf(w, dd, s1);
-        s2 = fmaf(w * dd, dd, s2);
     }
 }
 
