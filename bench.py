@@ -43,17 +43,17 @@ SEED = 2
 WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.1,1} x beta {0.2,0.5,1}"
 
 
-# DRAM bytes (read + write) per filter step of each workload's dominant kernel (its depth launch plus the
-# intensity launch after it), from one ncu capture of both (a 256 x 256 frame, scaled by the pixels processed),
-# valid only for the exact kernel sources it was taken on: the bench reports null for "traffic" when the
-# sources' hash differs.
+# DRAM bytes (read + write) and warp-instructions per launch of each workload's dominant kernel (for the filter
+# steps: the depth launch plus the intensity launch after it), from ncu captures, scaled by the pixels processed,
+# valid only for the exact kernel sources they were taken on: the bench reports null for "traffic" and "issue"
+# when the sources' hash differs.
 TRAFFIC_CAPTURES = {
+    # one filter step of the video job: mean over frames 0-3 of the nine runs (36 launches of each kernel;
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum)
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "intensity.cu"),
-                   "sha256": "0710fe083149f06cf64ebfb5eb8d4a772a81eeec2654e4ed9ee6b750fc8dabc0",
-                   "bytes_per_pixel": (202.30e6 + 15.08e6) / 65536,
-                   # warp-instructions of one filter step (depth + intensity launches), mean over frames 0-3 of the
-                   # nine runs (ncu smsp__inst_executed.sum, 36 launches each)
-                   "inst_per_pixel": (390.31e6 + 17.46e6) / 65536},
+                   "sha256": "ad7b3ee2e9621d003782168657bf7be115bb99cb29067053ca1fd76fa52f8931",
+                   "bytes_per_pixel": (198.45e6 + 15.43e6) / 65536,
+                   "inst_per_pixel": (376.12e6 + 17.46e6) / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu"),
                     "sha256": "79739b36cf73e920d4795bca6dd3ca1e8446e59bc3404efe5a80cf71efba510e",
                     "bytes_per_pixel": (542.29e6 + 17.20e6) / 65536,
