@@ -46,29 +46,31 @@ WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.
 # DRAM bytes (read + write) and warp-instructions per launch of each workload's dominant kernel (for the filter
 # steps: the depth launch plus the intensity launch after it), from ncu captures, scaled by the pixels processed,
 # valid only for the exact kernel sources they were taken on: the bench reports null for "traffic" and "issue"
-# when the sources' hash differs.
+# when the sources' hash differs. Each list names every file of this package the kernel's translation unit
+# compiles; the pseudo-posterior code lives in posterior.cuh, apart from the helpers in pixel.cuh, so that a change
+# to it voids exactly the captures of the kernels that call it (the depth and photon-list kernels).
 TRAFFIC_CAPTURES = {
     # one filter step of the video job: mean over frames 0-3 of the nine runs (36 launches of each kernel;
     # ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum)
-    "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "intensity.cu"),
-                   "sha256": "ad7b3ee2e9621d003782168657bf7be115bb99cb29067053ca1fd76fa52f8931",
+    "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "posterior.cuh", "intensity.cu"),
+                   "sha256": "a36f7c2d6073825af831149b14a907d3ccc97952a1dbc9d6c34201d1536f89a1",
                    "bytes_per_pixel": (198.45e6 + 15.43e6) / 65536,
                    "inst_per_pixel": (376.12e6 + 17.46e6) / 65536},
-    "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu"),
-                    "sha256": "79739b36cf73e920d4795bca6dd3ca1e8446e59bc3404efe5a80cf71efba510e",
+    "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh"),
+                    "sha256": "3504d8aa37f4119a2212c012d4174919f373cb7607b8affd5b6daa0919628dce",
                     "bytes_per_pixel": (542.29e6 + 17.20e6) / 65536,
                     # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture
                     # of a 256 x 256 frame of the mixed workload
                     "inst_per_pixel": (343.21e6 + 16.98e6) / 65536},
     # one launch of the photon-list kernel over all 64 sequences of the batched workload (7 050 240 pixels)
-    "k_batch": {"sources": ("batch.cu", "pixel.cuh"),
+    "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh"),
                 "sha256": "873cefe879aacd19fac8786189689c74b59cd3aecd920ba6d05a93ffebf97ea1",
                 "bytes_per_pixel": (457.70e6 + 124.52e6) / 7050240,
                 "inst_per_pixel": 26806.0e6 / 7050240},
     # backward launches of the differentiable filter (128 x 128 frames, T = 1024): mean over the 20 launches of
     # one reverse sweep
     "k_diff_backward": {"sources": ("grad.cu", "pixel.cuh"),
-                        "sha256": "3a4957cdfa4f3d4133cd5908c6e504be9c1068f46da005053d300b27dc2d2669",
+                        "sha256": "fd28dbf3cf434019c64740b88d2361f59afca9c1cf8a8b4957c5a45ade4cc97c",
                         "bytes_per_pixel": (34.11e6 + 0.0) / 16384,
                         "inst_per_pixel": 261.2e6 / 16384},
 }

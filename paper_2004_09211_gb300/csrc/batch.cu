@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "pixel.cuh"
+#include "posterior.cuh"
 #include "spl_internal.h"
 
 namespace spl {

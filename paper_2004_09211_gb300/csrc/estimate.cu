@@ -12,13 +12,14 @@
 // skip: lane = tap, each bin added into the L candidates it reaches); a denser row uses a register-blocked
 // direct sum (8 candidates per lane, taps in groups of 4).
 //
-// The pseudo-posterior moments are in pixel.cuh (shared with the photon-list kernel).
+// The pseudo-posterior moments are in posterior.cuh (shared with the photon-list kernels).
 #include <cuda_fp16.h>
 #include <math.h>
 
 #include <atomic>
 
 #include "pixel.cuh"
+#include "posterior.cuh"
 #include "spl_internal.h"
 
 namespace spl {

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "pixel.cuh"
+#include "posterior.cuh"
 #include "spl_internal.h"
 
 namespace spl {
