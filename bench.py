@@ -337,7 +337,7 @@ def native(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(h, peak, sc)
+        cpu = cpu_baseline(h, peak, sc, single_thread_crop=64)
 
     if rank == 0:
         line = {
@@ -445,23 +445,37 @@ def cpu_sample_inputs(h, peak, sc, frames=CROP_FRAMES, crop=CROP):
     return zs
 
 
-def cpu_baseline(h, peak, sc, frames=CROP_FRAMES, crop=CROP):
+def cpu_baseline(h, peak, sc, frames=CROP_FRAMES, crop=CROP, single_thread_crop=0):
+    """The oracle's filter steps (+ intensity) on a crop of the video job, OpenMP over pixels on every host core;
+    with single_thread_crop > 0, also one frame of a smaller crop on one thread."""
     from oracle import oracle as orc
     from paper_2004_09211_gb300 import synth
-    cores = orc.set_threads(os.cpu_count() or 1)
-    zs = cpu_sample_inputs(h, peak, sc, frames, crop)
     q = orc.params(T, L, peak, beta=0.5, sigma_rw2=SIGMA_RW2, nu=synth.cross_weights(0.5))
-    mu, var = orc.state_init(q, crop, crop)
-    t0 = time.perf_counter()
-    for z in zs:
-        e = orc.filter_step(q, h, z, mu, var)
-        mu, var = e["mu"], e["var"]
-        orc.intensity(q, h, z, mu)
-    dt = time.perf_counter() - t0
-    units = crop * crop * frames
-    return {"value": units / dt, "unit": "pixel-frames/s", "cores": cores, "kind": "oracle",
-            "sample": f"{crop}x{crop} crop x {frames} frames of the SBR 0.1 sequence, beta 0.5 "
-                      f"(filter step + intensity, FP64, OpenMP over pixels)", "seconds": dt}
+
+    def run(zs, c):
+        mu, var = orc.state_init(q, c, c)
+        t0 = time.perf_counter()
+        for z in zs:
+            e = orc.filter_step(q, h, z, mu, var)
+            mu, var = e["mu"], e["var"]
+            orc.intensity(q, h, z, mu)
+        return time.perf_counter() - t0
+
+    cores = orc.set_threads(os.cpu_count() or 1)
+    dt = run(cpu_sample_inputs(h, peak, sc, frames, crop), crop)
+    out = {"value": crop * crop * frames / dt, "unit": "pixel-frames/s", "cores": cores, "kind": "oracle",
+           "sample": f"{crop}x{crop} crop x {frames} frames of the SBR 0.1 sequence, beta 0.5 "
+                     f"(filter step + intensity, FP64, OpenMP over pixels)", "seconds": dt}
+    if single_thread_crop > 0:
+        c = single_thread_crop
+        one = orc.set_threads(1)
+        try:
+            dt1 = run(cpu_sample_inputs(h, peak, sc, 1, c), c)
+        finally:
+            orc.set_threads(cores)
+        out["single_thread"] = {"value": c * c / dt1, "unit": "pixel-frames/s", "cores": one,
+                                "sample": f"{c}x{c} crop x 1 frame, same sequence", "seconds": dt1}
+    return out
 
 
 def reference(args):
