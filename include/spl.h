@@ -43,7 +43,7 @@ typedef enum {
     SPL_ENOMEM = 2,       /* the call needed memory it could not get */
     SPL_ECUDA = 3,        /* a CUDA launch or runtime call failed; spl_last_error() has the CUDA message */
     SPL_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
-    SPL_EUNSUPPORTED = 5  /* valid request outside what this build supports (e.g. L above SPL_MAX_TAPS) */
+    SPL_EUNSUPPORTED = 5  /* valid request outside what the library supports (e.g. L above SPL_MAX_TAPS) */
 } spl_status;
 
 /* Storage of the photon-count histograms z. Counts are non-negative integers in every format. */
@@ -53,7 +53,7 @@ typedef enum {
     SPL_HIST_F32 = 2      /* float counts                                       */
 } spl_hist_format;
 
-/* Largest IRF length and histogram length this build supports. */
+/* Largest IRF length and histogram length the library supports. */
 #define SPL_MAX_TAPS 128
 #define SPL_MAX_BINS 8192
 

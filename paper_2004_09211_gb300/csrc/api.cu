@@ -49,7 +49,7 @@ spl_status check_params(const spl_params* q, bool need_filter) {
                 q->T - q->L + q->peak);
     SPL_REQUIRE(q->beta > 0.f && isfinite(q->beta), "beta must be finite and > 0 (got %g)", q->beta);
     if (q->L > SPL_MAX_TAPS || q->T > SPL_MAX_BINS) {
-        set_error("L (%d) above %d or T (%d) above %d is not supported by this build", q->L, SPL_MAX_TAPS, q->T,
+        set_error("L (%d) above %d or T (%d) above %d is not supported by the library", q->L, SPL_MAX_TAPS, q->T,
                   SPL_MAX_BINS);
         return SPL_EUNSUPPORTED;
     }
