@@ -763,3 +763,26 @@ def test_diff_oracle_gradient_matches_finite_differences():
         else:           # a zero weight must stay >= 0: forward difference
             fd = (f(hd, beta, up) - f(hd, beta, nu)) / 1e-7
         assert fd == pytest.approx(g["grad_nu"][k], rel=1e-4, abs=1e-8)
+
+
+def test_diff_oracle_readout_temperature_limits(orc):
+    """The soft readout sum_d d softmax(ell / tau) tends to the maximiser of ell as tau -> 0 and to the mean of the
+    candidate grid as tau -> infinity (a temperature that multiplied ell instead would swap the two limits)."""
+    import torch
+    from oracle import diff_oracle as dor
+    h, peak, zs, _ = _diff_inputs(33)
+    z = zs[0]
+    T, L = z.shape[-1], len(h)
+    dmin, dmax = peak, T - L + peak
+    q = orc.params(T, L, peak, beta=0.6, sigma_rw2=2.5, nu=NU_ASYM)
+    mu0, var0 = orc.state_init(q, *z.shape[:2])
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64)
+    e = orc.filter_step(q, h, z, mu0, var0, want_ell=True)
+    ell = e["ell"].reshape(z.shape[0], z.shape[1], -1)
+    srt = np.sort(ell, axis=-1)
+    clear = (srt[..., -1] - srt[..., -2]) > 1e-3  # a unique maximiser, by a margin
+    assert clear.sum() >= z.shape[0] * z.shape[1] // 2
+    _, _, ds_cold = dor.frame(t(h), t(0.6), t(NU_ASYM), t(z), t(mu0), t(var0), peak, dmin, dmax, 2.5, 1e-6)
+    np.testing.assert_allclose(ds_cold.numpy()[clear], e["argmax"][clear], atol=1e-9)
+    _, _, ds_hot = dor.frame(t(h), t(0.6), t(NU_ASYM), t(z), t(mu0), t(var0), peak, dmin, dmax, 2.5, 1e9)
+    np.testing.assert_allclose(ds_hot.numpy(), 0.5 * (dmin + dmax), rtol=1e-6)
