@@ -5,8 +5,8 @@
 // candidate depths) so the largest are taken first. Each warp repeatedly takes the next unit from a device
 // work-queue head (one atomicAdd by lane 0), loads that sequence's IRF into its own shared-memory tables,
 // and processes the tile's pixels one at a time with the same per-pixel arithmetic as the histogram kernel
-// (pixel.cuh). The data term uses the photon-sum form of Eq. beta_div2: C(d) = sum_k g[y_k - d + peak], formed
-// lane = tap (corr_photons).
+// (pixel.cuh, posterior.cuh). The data term uses the photon-sum form of Eq. beta_div2:
+// C(d) = sum_k g[y_k - d + peak], formed lane = tap (corr_photons).
 // The queue head is reset by a memset on the launch stream before every step, so a step is a memset node and
 // a kernel node in a CUDA graph. The plan (unit list, descriptor tables, queue heads, status word) is
 // allocated once at creation; nothing is allocated per step.

@@ -7,7 +7,7 @@
 // already owns, and the only working memory -- the work-queue head and the per-sequence prefix of work units --
 // lives in a fixed-size file-scope device array, g_noalloc_scratch, which every GPU that loads the library holds
 // until the process exits. Work units are taken in sequence order (the plan-based path sorts them by cost).
-// The per-pixel arithmetic is that of pixel.cuh, as in the plan-based kernel.
+// The per-pixel arithmetic is that of pixel.cuh and posterior.cuh, as in the plan-based kernel.
 #include <math.h>
 #include <stdio.h>
 
