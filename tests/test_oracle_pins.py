@@ -427,6 +427,68 @@ def test_intensity_matches_generic_optimizer(orc):
         assert b == pytest.approx(res.x[1], rel=1e-3, abs=1e-6)
 
 
+def _box_closed_form(z, d, L, peak):
+    """(r, b) of the box-IRF Poisson MLE with the window at depth d (closed form, see above)."""
+    T = len(z)
+    Kin = z[d - peak:d - peak + L].sum()
+    Kout = z.sum() - Kin
+    r, b = Kin - L * Kout / (T - L), Kout / (T - L)
+    if r < 0:
+        r, b = 0.0, z.sum() / T
+    return r, b
+
+
+def test_intensity_rule_per_pixel(orc):
+    """The per-pixel rule of Sec. II-E around the MLE: an absent pixel has r = 0 and b = K/T (K counted here by
+    hand); a faulty pixel has r = b = 0; a present pixel has the box-IRF closed form with the window at
+    round-half-even(mu) (x.5 goes to the even neighbour, x.4 down, x.6 up); present = NULL means every pixel is
+    present; an explicit template position overrides mu."""
+    L, T, peak = 8, 160, 3
+    h = np.full(L, 1.0 / L, np.float32)
+    q = orc.params(T, L, peak)
+    rng = _rng(31)
+    # eight pixels, each with a strong burst whose window position differs by one bin between the two
+    # roundings, so that the wrong rounding gives a visibly different (r, b)
+    mus = np.array([40.5, 41.5, 40.4, 40.6, 57.5, 90.5, 91.5, 77.0])
+    P = len(mus)
+    z = rng.poisson(0.3, size=(P, T)).astype(np.float64)
+    for p, m in enumerate(mus):
+        lo = int(math.floor(m)) - peak
+        z[p, lo:lo + L + 1] += rng.poisson(6.0, size=L + 1)
+        z[p, lo] += 9.0          # the bin that only the lower window holds
+        z[p, lo + L] += 2.0      # the bin that only the upper window holds
+    expect_pos = np.array([40, 42, 40, 41, 58, 90, 92, 77])
+    assert np.array_equal(np.rint(mus).astype(int), expect_pos)  # numpy rounds half to even as well
+    present = np.array([1, 1, 1, 1, 0, 1, 1, 1], np.uint8)
+    faulty = np.array([0, 0, 0, 0, 0, 0, 0, 1], np.uint8)
+    r, b = orc.intensity(q, h, z, mus, present=present, faulty=faulty)
+    for p in range(P):
+        if faulty[p]:
+            assert r[p] == 0.0 and b[p] == 0.0
+        elif not present[p]:
+            assert r[p] == 0.0
+            assert b[p] == pytest.approx(float(sum(z[p])) / T, rel=1e-15)
+        else:
+            rr, bb = _box_closed_form(z[p], int(expect_pos[p]), L, peak)
+            fl = int(math.floor(mus[p]))
+            other = fl + 1 if expect_pos[p] == fl else fl  # the other neighbour of mu
+            ro, _ = _box_closed_form(z[p], other, L, peak)
+            assert abs(rr - ro) > 0.5, "fixture must separate the two roundings"
+            assert r[p] == pytest.approx(rr, rel=1e-9, abs=1e-9)
+            assert b[p] == pytest.approx(bb, rel=1e-9, abs=1e-12)
+    r_all, b_all = orc.intensity(q, h, z, mus)
+    for p in range(P):
+        rr, bb = _box_closed_form(z[p], int(expect_pos[p]), L, peak)
+        assert r_all[p] == pytest.approx(rr, rel=1e-9, abs=1e-9)
+        assert b_all[p] == pytest.approx(bb, rel=1e-9, abs=1e-12)
+    dr = np.array([45, 46, 47, 48, 49, 50, 51, 52], np.int32)
+    r_dr, b_dr = orc.intensity(q, h, z, mus, dr=dr)
+    for p in range(P):
+        rr, bb = _box_closed_form(z[p], int(dr[p]), L, peak)
+        assert r_dr[p] == pytest.approx(rr, rel=1e-9, abs=1e-9)
+        assert b_dr[p] == pytest.approx(bb, rel=1e-9, abs=1e-12)
+
+
 # ------------------------------------------------------------------------------------------------------
 # Sub-bin depth (fine candidate grid, continuous IRF by linear interpolation of the taps)
 # ------------------------------------------------------------------------------------------------------
