@@ -121,14 +121,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc", "detect",
-                                                              "pd_curves", "fine"],
+                                                              "pd_curves", "fine", "alu_peaks"],
                     help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
                          "frame; diff: differentiable filter forward + backward; mixed: 1024x1024 FP16 frames "
                          "through the tensor-core filter step; video_tc: the video job through the tensor-core "
                          "filter step on FP16 copies of its frames, beside the FP32 path; detect: the video job "
                          "with the presence decision on the device (detection surrogate + Eq. prior_detect); "
                          "pd_curves: the single-pixel p_d experiment of Sec. IV-A (Gaussian IRF, five betas); "
-                         "fine: single-frame estimates on the sub-bin grid")
+                         "fine: single-frame estimates on the sub-bin grid; alu_peaks: measured FP32 FMA, packed "
+                         "FMA and ex2 throughput (the denominators of the ALU rooflines)")
     return ap.parse_args()
 
 
@@ -1183,6 +1184,55 @@ def mixed_cpu_baseline(spl, synth, h, hd, peak, sc, dev):
                                  "max_rel": float((np.abs(d) / np.abs(m)).max())}}
 
 
+def alu_peaks(args):
+    """Measured arithmetic throughput of this GPU: FFMA, packed f32x2 FMA and MUFU ex2 (spl_probe_throughput),
+    as operations per clock per SM (from the blocks' own clock64 counts) and per second (CUDA events), at 4 and 8
+    resident blocks of 256 threads per SM, under the sampled clocks. Prints one JSON line."""
+    import ctypes as ct
+    from paper_2004_09211_gb300 import _abi
+    lib = _abi.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream(dev)
+    kinds = {"ffma": 0, "ffma2": 1, "ex2": 2}
+    iters = {"ffma": 4096, "ffma2": 2048, "ex2": 1024}
+    out = {}
+    with ClockSampler(dev.index or 0) as clk:
+        for name, kind in kinds.items():
+            for bps in (4, 8):
+                nb, opt = ct.c_int(0), ct.c_longlong(0)
+                _abi.check(lib.spl_probe_throughput(kind, bps, iters[name], None, None, ct.byref(nb), ct.byref(opt),
+                                                    None))
+                sink = torch.empty(nb.value * 256, device=dev)
+                cyc = torch.zeros(nb.value, dtype=torch.int64, device=dev)
+                res = []
+                for rep in range(args.warmup + args.steps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize(dev)
+                    e0.record(stream)
+                    _abi.check(lib.spl_probe_throughput(kind, bps, iters[name], ct.c_void_p(sink.data_ptr()),
+                                                        ct.c_void_p(cyc.data_ptr()), ct.byref(nb), ct.byref(opt),
+                                                        ct.c_void_p(stream.cuda_stream)))
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    if rep >= args.warmup:
+                        ops = float(nb.value) * 256 * opt.value
+                        cy = cyc.double()
+                        res.append({"ops_per_s": ops / (e0.elapsed_time(e1) / 1e3),
+                                    "ops_per_clk_sm": ops / nsm / float(cy.mean()),
+                                    "cycles_spread": float(cy.max() / cy.min())})
+                best = max(res, key=lambda r: r["ops_per_s"])
+                out[f"{name}_bps{bps}"] = {"ops_per_clk_sm": round(statistics.median(r["ops_per_clk_sm"] for r in res), 2),
+                                           "ops_per_s_best": best["ops_per_s"],
+                                           "implied_mhz": best["ops_per_s"] / nsm /
+                                           statistics.median(r["ops_per_clk_sm"] for r in res) / 1e6}
+    line = {"metric": "arithmetic throughput (operations per clock per SM, per second)", "workload": "alu_peaks",
+            "n_sm": nsm, "results": out, "clocks": clk.summary(), "steps": args.steps, "warmup": args.warmup,
+            "note": "an FMA counts as one operation (two flops); an f32x2 instruction as two operations"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1201,6 +1251,8 @@ def main():
         pd_curves(args)
     elif args.workload == "fine":
         fine(args)
+    elif args.workload == "alu_peaks":
+        alu_peaks(args)
     else:
         native(args)
 

@@ -266,6 +266,8 @@ typedef struct spl_batch spl_batch;
 /* Device-side conditions recorded by spl_batch_step (read with spl_batch_status). */
 #define SPL_BATCH_BAD_BIN 1u       /* a photon bin outside [0, T): the photon was ignored              */
 #define SPL_BATCH_TOO_MANY 2u      /* a pixel had more than SPL_MAX_PHOTONS photons: outputs set to NaN */
+#define SPL_BATCH_DESC_MISMATCH 4u /* spl_batch_step_noalloc: a device descriptor's candidate count or IRF length
+                                      is outside what its host copy allowed: that unit's outputs set to NaN */
 #define SPL_MAX_PHOTONS 1024
 
 /* Creates a plan for nseq sequences (prms: host array, validated like spl_filter_step) with nslots
@@ -350,7 +352,11 @@ typedef struct {
  *   descs_host : host array of nseq descriptors (validated on the host, as spl_batch_create and
  *                spl_batch_set validate theirs).
  *   descs_dev  : the same nseq descriptors in device memory the caller owns (for example copied there with
- *                cudaMemcpy into memory the caller's pool provides).
+ *                cudaMemcpy into memory the caller's pool provides). The kernels read only this copy; the host copy
+ *                sizes the shared-memory slices. Where the two differ, a device descriptor whose candidate count
+ *                exceeds the host copies' largest (or whose IRF length is invalid) is refused on the device: its
+ *                outputs are set to NaN and SPL_BATCH_DESC_MISMATCH is raised in status; any other difference
+ *                gives results for the device copy's parameters.
  *   tile       : pixels per work unit, 1..4096 (spl_batch_tune's choice of a plan is a good value; 32 is a
  *                reasonable default). Units are processed in sequence order.
  *   status     : nullable device uint32; SPL_BATCH_* condition flags are OR-ed into it.
@@ -368,6 +374,31 @@ typedef struct {
  */
 SPL_API spl_status spl_batch_step_noalloc(const spl_seq_desc* descs_host, const spl_seq_desc* descs_dev, int nseq,
                                           int tile, uint32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------------
+ * Throughput probes (no counterpart in the paper)
+ *
+ * The depth kernels are bound by arithmetic issue rather than by HBM on most workloads; their ALU rooflines are
+ * quoted against these measured rates instead of nominal ones.
+ * ------------------------------------------------------------------------------------------------------------ */
+
+#define SPL_PROBE_FFMA 0   /* fma.rn.f32 (FFMA)                              */
+#define SPL_PROBE_FFMA2 1  /* fma.rn.f32x2 (two FP32 FMAs per instruction)   */
+#define SPL_PROBE_EX2 2    /* ex2.approx.ftz.f32 (the special-function unit) */
+
+/*
+ * spl_probe_throughput -- runs one arithmetic-throughput microkernel on every SM of the current device.
+ *   blocks_per_sm (1..8) blocks of 256 threads per SM; each thread executes iters * 128 operations of `kind` in
+ *   8 independent chains (an f32x2 instruction counts as two operations).
+ *   blocks (host out): number of blocks; ops_per_thread (host out): operations per thread.
+ *   sink  : device float [blocks * 256] (one result per thread, so the work is live).
+ *   cycles: device uint64 [blocks], SM clocks each block spent (clock64 difference).
+ *   With sink or cycles NULL the call only fills blocks and ops_per_thread (size query) and launches nothing.
+ *   Asynchronous on `stream`; time it with events on that stream.
+ */
+SPL_API spl_status spl_probe_throughput(int kind, int blocks_per_sm, int iters, float* sink,
+                                        unsigned long long* cycles, int* blocks, long long* ops_per_thread,
+                                        void* stream);
 
 #ifdef __cplusplus
 }

@@ -42,6 +42,7 @@ class spl_seq_desc(ct.Structure):
 SPL_NOALLOC_MAX_SEQ = 4096
 SPL_BATCH_BAD_BIN = 1
 SPL_BATCH_TOO_MANY = 2
+SPL_BATCH_DESC_MISMATCH = 4
 SPL_MAX_PHOTONS = 1024
 
 
@@ -52,6 +53,8 @@ _vp = ct.c_void_p
 SIGNATURES = {
     "spl_version": (ct.c_char_p, []),
     "spl_last_error": (ct.c_char_p, []),
+    "spl_probe_throughput": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, _vp, _vp, ct.POINTER(ct.c_int),
+                                        ct.POINTER(ct.c_longlong), _vp]),
     "spl_depth_cost": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp]),
     "spl_depth_cost_tc": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp]),
     "spl_tc_status": (ct.c_int, [ct.POINTER(ct.c_uint32)]),

@@ -55,35 +55,6 @@ __host__ __device__ __forceinline__ BSlice make_bslice(int maxD) {
     return s;
 }
 
-// C over every candidate from a pixel's photon list (the photon-sum form of Eq. beta_div2), lane = tap: lane l
-// owns taps l + 32 k, and each photon y in list order adds g_j to candidate y - u0 - j for its taps. The
-// candidates of one photon are distinct across lanes and taps and the warp synchronises between photons, so
-// each C(d) is summed in photon order. Returns max C.
-__device__ __forceinline__ float corr_photons(const float* __restrict__ gs, const int* ph, int nk, float* cs, int NB,
-                                             int D, int L, int u0, int lane) {
-    constexpr int KG = SPL_MAX_TAPS / 32;
-    zero_words(cs, NB * 8, lane);
-    float g[KG];
-#pragma unroll
-    for (int k = 0; k < KG; ++k) g[k] = gs[lane + 32 * k];
-    const int ntg = (L + 31) >> 5;
-    float mx = 0.f;
-    for (int e = 0; e < nk; ++e) {
-        const int c = ph[e] - u0 - lane;
-#pragma unroll
-        for (int k = 0; k < KG; ++k) {
-            const int ck = c - 32 * k;
-            if (k < ntg && static_cast<unsigned>(ck) < static_cast<unsigned>(D)) {
-                const float v = cs[ck] + g[k];
-                cs[ck] = v;
-                mx = fmaxf(mx, v);
-            }
-        }
-        __syncwarp();
-    }
-    return warp_max(mx);
-}
-
 __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, const Unit* __restrict__ units,
                                                int nunits, unsigned* __restrict__ head, unsigned* __restrict__ status,
                                                BSlice sl) {

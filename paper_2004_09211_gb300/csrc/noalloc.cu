@@ -43,21 +43,34 @@ __host__ __device__ __forceinline__ NSlice make_nslice(int maxD) {
     return s;
 }
 
-// Clears the queue head and writes the unit prefix (one thread: at most SPL_NOALLOC_MAX_SEQ additions).
+// Clears the queue head and writes the unit prefix: one warp, 32 sequences per step, each step an inclusive warp
+// scan of the unit counts plus the running total of the steps before it.
 __global__ void k_noalloc_setup(const spl_seq_desc* __restrict__ seqs, int nseq, int tile, unsigned* scratch) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    scratch[0] = 0u;
-    unsigned acc = 0;
-    for (int s = 0; s < nseq; ++s) {
-        scratch[1 + s] = acc;
-        const long long P = static_cast<long long>(seqs[s].prm.H) * seqs[s].prm.W;
-        acc += static_cast<unsigned>((P + tile - 1) / tile);
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    if (lane == 0) scratch[0] = 0u;
+    unsigned carry = 0;
+    for (int s0 = 0; s0 < nseq; s0 += 32) {
+        const int s = s0 + lane;
+        unsigned n = 0;
+        if (s < nseq) {
+            const long long P = static_cast<long long>(seqs[s].prm.H) * seqs[s].prm.W;
+            n = static_cast<unsigned>((P + tile - 1) / tile);
+        }
+        unsigned inc = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (s < nseq) scratch[1 + s] = carry + inc - n;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
-    scratch[1 + nseq] = acc;
+    if (lane == 0) scratch[1 + nseq] = carry;
 }
 
 __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __restrict__ seqs, int nseq, int tile,
-                                                       unsigned* scratch, uint32_t* status, NSlice sl) {
+                                                       unsigned* scratch, uint32_t* status, NSlice sl, int maxD) {
     extern __shared__ __align__(16) float dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
@@ -88,6 +101,17 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
         const int p_end = min(P, p_begin + tile);
         const int T = prm.T, L = prm.L, D = prm.dmax - prm.dmin + 1, NB = (D + 31) >> 5;
         const int u0 = prm.dmin - prm.peak;
+        if (D > maxD || D < 1 || L < 1 || L > SPL_MAX_TAPS || T < L) {
+            // this device descriptor differs from the host copy the shared-memory slice was sized from: refuse the
+            // unit rather than write past the warp's slice
+            for (int p = p_begin + lane; p < p_end; p += 32) {
+                f.mu_out[p] = f.var_out[p] = NAN;
+                if (f.argmax) f.argmax[p] = -1;
+                if (f.refl) f.refl[p] = f.bg[p] = NAN;
+            }
+            if (lane == 0 && status) atomicOr(status, SPL_BATCH_DESC_MISMATCH);
+            continue;
+        }
         const float lam2 = static_cast<float>((static_cast<double>(prm.beta) + 1.0) / prm.beta) * kLog2e;
         const float flat_m = 0.5f * static_cast<float>(prm.dmin + prm.dmax);
         const double span = static_cast<double>(prm.dmax - prm.dmin);
@@ -116,8 +140,6 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
         grid.L = L;
         grid.lam2 = lam2;
         grid.gmax = gmax;
-        const int run = (D + 31) >> 5;
-        const int r0 = lane * run, r1 = min(r0 + run, D);
 
         for (int p = p_begin; p < p_end; ++p) {
             const bool faulty = f.faulty && f.faulty[p];
@@ -151,19 +173,7 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
             if (__any_sync(0xffffffffu, bad) && lane == 0 && status) atomicOr(status, SPL_BATCH_BAD_BIN);
             __syncwarp();
 
-            float mx = 0.f;
-            for (int c = r0; c < r1; ++c) cs[c] = 0.f;
-            for (int k = 0; k < nk; ++k) {
-                const int tc = ph[k] - u0;
-                const int lo2 = max(tc - L + 1, r0), hi2 = min(tc, r1 - 1);
-                for (int c = lo2; c <= hi2; ++c) {
-                    const float v = cs[c] + gs[tc - c];
-                    cs[c] = v;
-                    mx = fmaxf(mx, v);
-                }
-            }
-            __syncwarp();
-            const float cmax = warp_max(mx);
+            const float cmax = corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane);
 
             Prior pr;
             {
@@ -198,15 +208,7 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
                     for (int k = 0; k < nk; ++k) n += (ph[k] >= s_bin) & (ph[k] <= e_bin);
                     return static_cast<float>(n);
                 },
-                [&]() {
-                    for (int c = r0; c < r1; ++c) cs[c] = 0.f;
-                    for (int k = 0; k < nk; ++k) {
-                        const int tc = ph[k] - u0;
-                        const int lo2 = max(tc - L + 1, r0), hi2 = min(tc, r1 - 1);
-                        for (int c = lo2; c <= hi2; ++c) cs[c] += gs[tc - c];
-                    }
-                    __syncwarp();
-                },
+                [&]() { corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane); },
                 lane, bidx, mu, var);
             if (lane == 0) {
                 f.mu_out[p] = mu;
@@ -344,7 +346,8 @@ extern "C" spl_status spl_batch_step_noalloc(const spl_seq_desc* descs_host, con
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        k_noalloc_batch<<<per_sm * nsm, wpc * 32, per_warp * wpc, s>>>(descs_dev, nseq, tile, scratch, status, sl);
+        k_noalloc_batch<<<per_sm * nsm, wpc * 32, per_warp * wpc, s>>>(descs_dev, nseq, tile, scratch, status, sl,
+                                                                         maxD);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

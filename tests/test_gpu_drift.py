@@ -1,0 +1,95 @@
+"""Long-sequence drift of the FP32 filter against the FP64 oracle.
+
+The paper's videos are thousands of frames long (Sec. IV: 3000 frames at 500 frames/s, 6000 at 1000 frames/s).
+The GPU chain and the oracle chain run independently from the same initial state: every frame's state feeds the
+next frame's prior (Eq. predict), so FP32 rounding could accumulate along the sequence. After every frame both
+states are compared at the filter's tolerances (relative 1e-4; variance floor 1e-6 bins^2), and the largest
+relative difference over the whole sequence is printed (run with -s).
+
+Two regimes, 3000 frames each, 8 x 8 pixels, the 48-tap asymmetric IRF, beta = 0.5, sigma_RW^2 = 3, the cross
+weights with nu0 = 0.5:
+  * the paper's first real-data sequence: T = 153 bins, about 55 signal and 35 background photons per pixel and
+    frame (SBR about 1.6); a surface that drifts back and forth by 0.2 bins per frame and a second one at a fixed
+    depth (tight posteriors, the data dominates every frame);
+  * a photon-starved one: T = 400, 3 signal photons per pixel and frame at SBR 0.1 (broad posteriors, the prior
+    carries information from frame to frame, which is where rounding could build up).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2004_09211_gb300 as spl
+from paper_2004_09211_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+H = W = 8
+N = 3000
+
+
+def _sequence(T, signal, sbr, seed):
+    h, peak = synth.asymmetric_irf(L=48)
+    L = len(h)
+    dmin, dmax = peak, T - L + peak
+    rng = np.random.default_rng(seed)
+    n = np.arange(N)
+    lo, hi = dmin + 8, dmax - 8
+    # surface 1 bounces between lo and hi at 0.2 bins per frame; surface 2 sits still
+    period = 2 * (hi - lo) / 0.2
+    ph = (n * 0.2) % (2 * (hi - lo))
+    d1 = lo + np.where(ph < hi - lo, ph, 2 * (hi - lo) - ph)
+    d2 = 0.5 * (lo + hi) + 3.3
+    yy, xx = np.mgrid[0:H, 0:W]
+    first = (xx < W // 2)
+    hd = torch.from_numpy(h.astype(np.float64))
+    z = np.empty((N, H, W, T), np.uint16)
+    b = signal / (sbr * T)
+    for k in range(N):
+        depth = np.rint(np.where(first, d1[k], d2)).astype(np.int64)  # whole-bin templates
+        mean = synth.expected_counts(torch.from_numpy(depth), torch.full((H, W), float(signal), dtype=torch.float64),
+                                     b, hd, peak, T)
+        z[k] = rng.poisson(mean.numpy()).astype(np.uint16)
+    assert period > 10
+    return h, peak, z
+
+
+@pytest.mark.parametrize("T,signal,sbr,seed", [(153, 55.0, 1.6, 3001), (400, 3.0, 0.1, 3002)])
+def test_long_sequence_drift(orc, T, signal, sbr, seed):
+    h, peak, z = _sequence(T, signal, sbr, seed)
+    L = len(h)
+    P = H * W
+    beta, s2 = 0.5, 3.0
+    prm = spl.make_params(H, W, T, L, peak, beta=beta, sigma_rw2=s2)
+    pitch = synth.pad_pitch(T)
+    zd = synth.pitched(torch.from_numpy(z.reshape(N, P, T).astype(np.int32)).to(torch.uint16), pitch).to(DEV)
+    hd = torch.from_numpy(h).to(DEV)
+    mus = torch.empty(N + 1, P, device=DEV)
+    vars_ = torch.empty(N + 1, P, device=DEV)
+    spl.spl_state_init(prm, mus[0], vars_[0])
+    for k in range(N):
+        spl.spl_filter_step(prm, zd[k], hd, mus[k], vars_[k], intensity=False,
+                            out=dict(mu=mus[k + 1], var=vars_[k + 1]))
+    torch.cuda.synchronize()
+    gm, gv = mus.cpu().numpy().astype(np.float64), vars_.cpu().numpy().astype(np.float64)
+
+    q = orc.params(T, L, peak, beta=beta, sigma_rw2=s2, nu=synth.cross_weights(0.5))
+    m, v = orc.state_init(q, H, W)
+    worst_m = worst_v = 0.0
+    worst_frame = 0
+    bad = []
+    for k in range(N):
+        e = orc.filter_step(q, h, z[k].astype(np.float64), m, v)
+        m, v = e["mu"], e["var"]
+        em = np.abs(gm[k + 1] - m.reshape(-1)) / np.abs(m.reshape(-1))
+        ev = np.abs(gv[k + 1] - v.reshape(-1)) / (np.abs(v.reshape(-1)) + 1e-2)
+        if em.max() > worst_m or ev.max() > worst_v:
+            worst_frame = k
+        worst_m, worst_v = max(worst_m, em.max()), max(worst_v, ev.max())
+        okm = np.abs(gm[k + 1] - m.reshape(-1)) <= 1e-4 * np.abs(m.reshape(-1))
+        okv = np.abs(gv[k + 1] - v.reshape(-1)) <= 1e-4 * np.abs(v.reshape(-1)) + 1e-6
+        if not (okm.all() and okv.all()) and len(bad) < 5:
+            bad.append((k, int(np.argmin(okm & okv))))
+    med_var = float(np.median(gv[N]))
+    print(f"\ndrift T={T} signal={signal} SBR={sbr}: {N} frames, largest relative difference mu {worst_m:.3g}, "
+          f"var {worst_v:.3g} (frame {worst_frame}); median variance at the end {med_var:.3g} bins^2")
+    assert not bad, f"first frames/pixels outside the tolerance: {bad}; largest mu {worst_m:.3g}, var {worst_v:.3g}"

@@ -418,30 +418,35 @@ def test_state_init(orc):
 # ------------------------------------------------------------------------------------------------------------
 
 
-def test_full_size_video_frames_sampled(orc):
+@pytest.mark.parametrize("sbr,beta", [(0.1, 0.5), (0.01, 0.2), (1.0, 1.0)])
+def test_full_size_video_frames_sampled(orc, sbr, beta):
     """Two frames of a 256 x 256, T = 1500 video with the full launch configuration, compared on sampled
     pixels: after n frames a pixel depends only on inputs within Chebyshev distance n (the oracle's
-    dependency-cone pin), so the oracle runs on (2n+1)^2 crops."""
+    dependency-cone pin), so the oracle runs on (2n+1)^2 crops. Every output of both frames is compared: mu, var,
+    argmax (near-tie rule) and the intensity pair (refl, bg). Three (SBR, beta) runs of the video job: a dense
+    row at SBR 0.01 with beta 0.2, the middle run, and photon-starved broad posteriors at SBR 1 with beta 1."""
     H = W = 256
     N, T, L = 2, 1500, 48
     h, peak = synth.asymmetric_irf(L=L)
     sc = synth.moving_scene(H, W, N, peak + 8, T - L + peak - 8, seed=251)
     g = torch.Generator(device=DEV).manual_seed(251)
     hd = torch.from_numpy(h).to(DEV)
-    prm = spl.make_params(H, W, T, L, peak, beta=0.5, sigma_rw2=3.0)
+    prm = spl.make_params(H, W, T, L, peak, beta=beta, sigma_rw2=3.0)
     pitch = synth.pad_pitch(T)
     zs = []
     for n in range(N):
-        b = float(sc.signal[n].mean()) / (0.1 * T)
+        b = float(sc.signal[n].mean()) / (sbr * T)
         mean = synth.expected_counts(torch.from_numpy(sc.depth[n]).to(DEV), torch.from_numpy(sc.signal[n]).to(DEV),
                                      b, hd, peak, T)
         zs.append(synth.pitched(synth.poisson_histograms(mean, g).reshape(-1, T), pitch))
     mu, var = spl.spl_state_init(prm)
+    outs = []
     for n in range(N):
         o = spl.spl_filter_step(prm, zs[n], hd, mu, var)
         mu, var = o["mu"], o["var"]
+        outs.append({k: _np(v).reshape(H, W) for k, v in o.items()})
     torch.cuda.synchronize()
-    q = orc.params(T, L, peak, beta=0.5, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    q = orc.params(T, L, peak, beta=beta, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
     samples = [(0, 0), (0, 255), (255, 0), (255, 255), (128, 77), (3, 200), (200, 1), (97, 254)]
     zc = [z[:, :T].reshape(H, W, T) for z in zs]
     for (y, x) in samples:
@@ -450,10 +455,15 @@ def test_full_size_video_frames_sampled(orc):
         m, v = orc.state_init(q, y1 - y0, x1 - x0)
         for n in range(N):
             crop = _np(zc[n][y0:y1, x0:x1]).astype(np.float64)
-            e = orc.filter_step(q, h, crop, m, v)
+            e = orc.filter_step(q, h, crop, m, v, want_ell=True)
             m, v = e["mu"], e["var"]
-        check_close(_np(mu.reshape(H, W)[y, x]), m[y - y0, x - x0], f"mu[{y},{x}]")
-        check_close(_np(var.reshape(H, W)[y, x]), v[y - y0, x - x0], f"var[{y},{x}]", atol=1e-6)
+            cy, cx = y - y0, x - x0
+            o = outs[n]
+            what = f"[{y},{x}] frame {n}"
+            check_close(o["mu"][y, x], m[cy, cx], f"mu{what}")
+            check_close(o["var"][y, x], v[cy, cx], f"var{what}", atol=1e-6)
+            check_argmax(o["argmax"][y, x], e["argmax"][cy, cx], e["ell"][cy, cx], q.dmin, f"argmax{what}")
+            check_intensity(orc, q, h, crop[cy, cx], o["mu"][y, x], m[cy, cx], o["refl"][y, x], o["bg"][y, x])
 
 
 # ------------------------------------------------------------------------------------------------------------

@@ -86,14 +86,18 @@ def test_noalloc_step_matches_plan_step_on_two_calls():
     # allocation-free entry point, two calls in a row (frame 1 starts from frame 0's output)
     mine = [_buffers(q) for q in seqs]
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
-    keep = []
+    descs = [_desc_arrays(seqs, [_frame(q, *mine[i], n) for i, q in enumerate(seqs)]) for n in range(N_FRAMES)]
+    torch.cuda.synchronize()
     for n in range(N_FRAMES):
-        host, dev = _desc_arrays(seqs, [_frame(q, *mine[i], n) for i, q in enumerate(seqs)])
-        keep.append(dev)
+        host, dev = descs[n]
+        if n == 1:  # the set-up of the first call is done: from here on the call may not take device memory
+            free_before = torch.cuda.mem_get_info()[0]
         st = lib.spl_batch_step_noalloc(host, dev.data_ptr(), len(seqs), 32, status.data_ptr(),
                                         torch.cuda.current_stream().cuda_stream)
         assert st == _abi.SPL_OK, lib.spl_last_error()
         torch.cuda.synchronize()
+        if n == 1:
+            assert torch.cuda.mem_get_info()[0] >= free_before, "the second call took device memory"
         for i in range(len(seqs)):
             a_st, a_out = ref[i]
             b_st, b_out = mine[i]
