@@ -7,12 +7,14 @@
 // processed, the next pixel's histogram row is copied into the warp's shared-memory slice with cp.async and its
 // neighbour states are loaded into registers, so HBM and L2 latency overlap compute.
 //
-// Correlation. C(d) = sum_j g_j z[d - peak + j] (g = h^beta) for every candidate, into shared memory. A row
-// with few non-empty bins (photon-starved data) is correlated from a compacted list of those bins (exact zero
-// skip: lane = tap, each bin added into the L candidates it reaches); a denser row uses a register-blocked
-// direct sum (8 candidates per lane, taps in groups of 4).
-//
-// The pseudo-posterior moments are in posterior.cuh (shared with the photon-list kernels).
+// Per pixel: (1) the non-empty 16-byte chunks of the staged row are listed (one load and one test per chunk), then
+// their bins are counted (photons K, non-empty bins) 32 chunks at a time; (2) a row with few non-empty bins
+// (photon-starved data) keeps them as a (bin, count) list in bin order: each block of 32 candidates gets the photon
+// count of its window as its data bound, and C(d) = sum_j g_j z[d - peak + j] (g = h^beta) is scattered from the
+// list, lane = tap; a denser row is correlated by a register-blocked direct sum (8 candidates per lane, taps in
+// groups of 4) whose largest C bounds every block. Both forms add the products of one candidate in tap order, so
+// they give bitwise the same C. (3) The pseudo-posterior (posterior.cuh) drops the blocks whose weights are
+// provably below 2^-64 of the largest and weighs the rest.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -34,12 +36,11 @@ struct Slice {
     int nch;     // 16-byte chunks per row
     int rawsz;   // words per staging buffer: nch * 4 + 16 zero words (windows read up to 11 bins past T)
     int raw;     // two staging buffers (cp.async targets): the current pixel's row and the next one's
-    int ebin;    // non-empty bins of a sparse row, in bin order (kTapNnz words)
+    int ebin;    // non-empty bins of a listed row, in bin order (kTapNnz words)
     int eval;    // their counts (kTapNnz words)
-    int cps;     // photon-count prefix over chunks, nch + 1 words
-    int cpe;     // non-empty-bin prefix over chunks, nch + 1 words
-    int ubs;     // per-block upper bounds, NB words
-    int cs;      // C, then ell or weights, per candidate: NB * 32 words
+    int bnd;     // per-block data bound of a listed row: photons whose windows reach the block, NB words
+    int ubs;     // per-block upper bounds of ell, NB words
+    int cs;      // C, then ell or weights, per candidate: NB * 32 words (first the list of non-empty chunks)
     int words;   // total
 };
 
@@ -53,11 +54,10 @@ __host__ __device__ __forceinline__ Slice make_slice(int T, int D, int cb) {
     s.raw = 0;
     s.ebin = 2 * s.rawsz;
     s.eval = s.ebin + kTapNnz;
-    s.cps = s.eval + kTapNnz;
-    s.cpe = s.cps + round4(s.nch + 1);
-    s.ubs = s.cpe + round4(s.nch + 1);
+    s.bnd = s.eval + kTapNnz;
+    s.ubs = s.bnd + round4(nb);
     s.cs = s.ubs + round4(nb);
-    s.words = s.cs + nb * 32;
+    s.words = s.cs + (nb * 32 > round4(s.nch) ? nb * 32 : round4(s.nch));
     return s;
 }
 
@@ -144,7 +144,7 @@ struct Nbr {
     int faulty;  // lane 0: the pixel itself is faulty
 };
 
-__device__ __forceinline__ Nbr request_nbr(const EstimateArgs& a, long long p, long long P, int lane) {
+__device__ __forceinline__ Nbr request_nbr(const EstimateArgs& a, long long p, int y, int x, long long P, int lane) {
     Nbr r;
     r.m = r.v = 0.f;
     r.info = r.faulty = 0;
@@ -156,7 +156,6 @@ __device__ __forceinline__ Nbr request_nbr(const EstimateArgs& a, long long p, l
             r.info = 1;
         }
     } else if (a.prior_mode == PRIOR_STENCIL && lane < 9) {
-        const int y = static_cast<int>(p / a.W), x = static_cast<int>(p - static_cast<long long>(y) * a.W);
         const int yy = y + lane / 3 - 1, xx = x + lane % 3 - 1;
         if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
             const long long i = static_cast<long long>(yy) * a.W + xx;
@@ -173,52 +172,181 @@ __device__ __forceinline__ Nbr request_nbr(const EstimateArgs& a, long long p, l
     return r;
 }
 
-// In-place exclusive prefix sum of n values (float array x and int array y) of a warp's slice, with the
-// total written at index n.
-__device__ __forceinline__ void warp_scan2(float* x, int* y, int n, int lane) {
-    const int seg = (n + 31) >> 5;
-    const int b = lane * seg, e = min(b + seg, n);
-    float sx = 0.f;
-    int sy = 0;
-    for (int i = b; i < e; ++i) {
-        sx += x[i];
-        sy += y[i];
+// ------------------------------------------------------------------------------------------------------------
+// Row scan and the data term C(d)
+// ------------------------------------------------------------------------------------------------------------
+
+// The non-empty 16-byte chunks of the staged row (bins T and above are zero), listed in chunk order into
+// nzc[0 .. M): 32 consecutive chunks per step (lane = chunk, one load and one test each), appended by ballot, so
+// photon-starved rows cost little here. Returns M (warp-uniform).
+__device__ __forceinline__ int nonempty_chunks(const float* raw, int nch, int* nzc, int lane) {
+    int M = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int i0 = 0; i0 < nch; i0 += 32) {
+        const int i = i0 + lane;
+        bool nz = false;
+        if (i < nch) {
+            const uint4 v = reinterpret_cast<const uint4*>(raw)[i];
+            nz = (v.x | v.y | v.z | v.w) != 0u;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, nz);
+        if (nz) nzc[M + __popc(m & below)] = i;
+        M += __popc(m);
     }
-    float ix = sx;
-    int iy = sy;
+    __syncwarp();
+    return M;
+}
+
+// Photons K and non-empty bins nnz of the listed chunks (32 chunks per round, lane = chunk). While the running
+// count stays within kTapNnz the non-empty bins are also listed as (bin, count) in ebin/eval, in bin order.
+template <int FMT, int CB>
+__device__ __forceinline__ void count_and_list(const float* raw, const int* nzc, int M, int T, int* ebin, float* eval,
+                                               int lane, float& K, int& nnz) {
+    float ks = 0.f;
+    int base = 0;
+    for (int k0 = 0; k0 < M; k0 += 32) {
+        const int k = k0 + lane;
+        float f[CB];
+        int n = 0, i = 0;
+        if (k < M) {
+            i = nzc[k];
+            convert_chunk<FMT>(raw, i, T, f);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const float tx = __shfl_up_sync(0xffffffffu, ix, o);
-        const int ty = __shfl_up_sync(0xffffffffu, iy, o);
-        if (lane >= o) {
-            ix += tx;
-            iy += ty;
+            for (int j = 0; j < CB; ++j) {
+                n += f[j] != 0.f;
+                ks += f[j];
+            }
+        }
+        int incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (k < M && base + tot <= kTapNnz) {  // warp-uniform round total: the list is either complete or unused
+            int o = base + incl - n;
+#pragma unroll
+            for (int j = 0; j < CB; ++j)
+                if (f[j] != 0.f) {
+                    ebin[o] = i * CB + j;
+                    eval[o] = f[j];
+                    ++o;
+                }
+        }
+        base += tot;
+    }
+    __syncwarp();
+    K = warp_sum(ks);
+    nnz = base;
+}
+
+// Number of listed bins below t (the list is in bin order), counted by all lanes.
+__device__ __forceinline__ int entries_below(const int* ebin, int nnz, int t, int lane) {
+    int n = 0;
+    for (int e0 = 0; e0 < nnz; e0 += 32) {
+        const int e = e0 + lane;
+        n += __popc(__ballot_sync(0xffffffffu, e < nnz && ebin[e] < t));
+    }
+    return n;
+}
+
+// C on block b of a listed row, lane = candidate 32 b + lane: the listed bins from index e (the first one not
+// below the block's window) up to the end of the window, in bin order (that is, in tap order for the candidate).
+// Writes cs (0 past D) and returns the lane's C (0 past D).
+__device__ __forceinline__ float gather_block(const float* __restrict__ gs, const int* ebin, const float* eval, int nnz,
+                                             int e, float* cs, int b, int D, int L, int u0, int lane) {
+    const int c = 32 * b + lane;
+    const int whi = u0 + 32 * b + 31 + L - 1;
+    const int j0 = u0 + c;  // bin of tap 0 for this candidate
+    float acc = 0.f;
+    for (; e < nnz; ++e) {
+        const int t = ebin[e];
+        if (t > whi) break;
+        const int j = t - j0;
+        if (static_cast<unsigned>(j) < static_cast<unsigned>(L)) acc = fmaf(eval[e], gs[j], acc);
+    }
+    if (c >= D) acc = 0.f;
+    cs[c] = acc;
+    return acc;
+}
+
+// C on candidates [c_lo, c_hi] of a listed row, lane = tap: lane l owns the taps j = l + 32 k (k < NTG) and adds
+// z_t g_j into candidate t - u0 - j for each listed bin t in turn (bins whose windows miss the range are skipped).
+// The candidates of one bin are distinct across lanes and taps and the warp synchronises between bins, so every
+// C(d) is summed in bin order, i.e. in tap order, as by the gather. The range must be zero on entry. Returns max C.
+template <int NTG>
+__device__ __forceinline__ float scatter_range(const float* __restrict__ gs, const int* ebin, const float* eval,
+                                               int nnz, float* cs, int c_lo, int c_hi, int u0, int L, int lane) {
+    float g[NTG];
+#pragma unroll
+    for (int k = 0; k < NTG; ++k) g[k] = gs[lane + 32 * k];
+    const int off = -u0 - lane;
+    const unsigned span = static_cast<unsigned>(c_hi - c_lo);
+    float mx = 0.f;
+    for (int e = 0; e < nnz; ++e) {
+        const int t = ebin[e];
+        if (t - u0 - L + 1 > c_hi) break;  // this bin and every later one lie past the range
+        if (t - u0 < c_lo) continue;       // warp-uniform: the bin's window ends before the range
+        const int c = t + off;
+        const float z = eval[e];
+#pragma unroll
+        for (int k = 0; k < NTG; ++k) {
+            const int ck = c - 32 * k;
+            if (static_cast<unsigned>(ck - c_lo) <= span) {
+                const float v = fmaf(z, g[k], cs[ck]);
+                cs[ck] = v;
+                mx = fmaxf(mx, v);
+            }
+        }
+        __syncwarp();
+    }
+    return warp_max(mx);
+}
+
+// C on blocks [b0, b1] of a listed row; returns max C there. Up to three blocks are gathered (lane = candidate,
+// blocks that no listed bin reaches are zero-filled); a wider range is zero-filled and scattered (lane = tap).
+__device__ __forceinline__ float listed_range(const float* __restrict__ gs, const int* ebin, const float* eval, int nnz,
+                                             const float* bnd, float* cs, int b0, int b1, int D, int L, int u0,
+                                             int lane) {
+    if (b1 - b0 >= 3) {
+        zero_words(cs + 32 * b0, 8 * (b1 - b0 + 1), lane);
+        const int c_lo = 32 * b0, c_hi = min(32 * b1 + 31, D - 1);
+        switch ((L + 31) >> 5) {
+            case 1: return scatter_range<1>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
+            case 2: return scatter_range<2>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
+            case 3: return scatter_range<3>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
+            default: return scatter_range<4>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
         }
     }
-    float rx = ix - sx;  // exclusive offsets of this lane's segment
-    int ry = iy - sy;
-    for (int i = b; i < e; ++i) {
-        const float vx = x[i];
-        const int vy = y[i];
-        x[i] = rx;
-        y[i] = ry;
-        rx += vx;
-        ry += vy;
+    float mx = 0.f;
+    int e = entries_below(ebin, nnz, u0 + 32 * b0, lane);
+    for (int b = b0; b <= b1; ++b) {
+        if (bnd[b] > 0.f) mx = fmaxf(mx, gather_block(gs, ebin, eval, nnz, e, cs, b, D, L, u0, lane));
+        else cs[32 * b + lane] = 0.f;
+        const int next = u0 + 32 * (b + 1);  // entries below the next block's window are done with
+        while (e < nnz && ebin[e] < next) ++e;
     }
-    if (lane == 31) {
-        x[n] = ix;
-        y[n] = iy;
+    __syncwarp();
+    return warp_max(mx);
+}
+
+// Photons of the listed bins that reach each block: entry (t, z) adds z to the blocks holding candidates
+// t - u0 - L + 1 .. t - u0. bnd[0 .. NB) must be zero on entry.
+__device__ __forceinline__ void block_photons(const int* ebin, const float* eval, int nnz, float* bnd, int D, int L,
+                                              int u0, int lane) {
+    for (int e = lane; e < nnz; e += 32) {
+        const int chi = min(ebin[e] - u0, D - 1), clo = max(ebin[e] - u0 - L + 1, 0);
+        if (chi < clo) continue;
+        for (int b = clo >> 5; b <= (chi >> 5); ++b) atomicAdd(&bnd[b], eval[e]);
     }
     __syncwarp();
 }
 
-// ------------------------------------------------------------------------------------------------------------
-// Correlation C(d) for every candidate into cs[0 .. 32 NB); each routine returns max_d C(d) (warp-uniform)
-// ------------------------------------------------------------------------------------------------------------
-
 // Dense rows: a lane computes 8 consecutive candidates per 256-candidate super-block. Super-blocks start at
 // candidate -(u0 & 3) so every lane's window starts on a 4-bin boundary (candidates < 0 are dropped). Windows
 // may read up to 11 bins past the row: the staging buffer is zero there (bins T..pitch-1 are zeroed too).
+// Returns max C (warp-uniform).
 template <int FMT>
 __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const float* raw, float* cs, int D, int L,
                                             int u0, int lane) {
@@ -258,64 +386,19 @@ __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const 
     return warp_max(mx);
 }
 
-// Sparse rows (at most kTapNnz non-empty bins, listed in bin order): lane l owns the taps j = l + 32 k (k < 4) and
-// adds z_t g_j into candidate t - u0 - j for each listed bin t in turn. The candidates of one bin are distinct
-// across lanes and taps, and the warp synchronises between bins, so every C(d) is summed in bin order (the same
-// in every run). Taps j >= L hold g_j = 0. Returns max C (every partial sum is <= its final value).
-__device__ __forceinline__ float corr_taps(const float* __restrict__ gs, const int* ebin, const float* eval, int nnz,
-                                          float* cs, int NB, int D, int L, int u0, int lane) {
-    constexpr int KG = SPL_MAX_TAPS / 32;
-    zero_words(cs, NB * 8, lane);
-    float g[KG];
-#pragma unroll
-    for (int k = 0; k < KG; ++k) g[k] = gs[lane + 32 * k];
-    const int ntg = (L + 31) >> 5;
-    const int off = -u0 - lane;
-    float mx = 0.f;
-    for (int e = 0; e < nnz; ++e) {
-        const int c = ebin[e] + off;
-        const float z = eval[e];
-#pragma unroll
-        for (int k = 0; k < KG; ++k) {
-            const int ck = c - 32 * k;
-            if (k < ntg && static_cast<unsigned>(ck) < static_cast<unsigned>(D)) {
-                const float v = fmaf(z, g[k], cs[ck]);
-                cs[ck] = v;
-                mx = fmaxf(mx, v);
-            }
-        }
-        __syncwarp();
-    }
-    return warp_max(mx);
-}
-
-// C(d) for all candidates of one pixel (staged row in raw, non-empty-bin prefix over chunks in cpe). Returns
-// max C. `sparse`: the row has at most kTapNnz non-empty bins.
-template <int FMT, int CB>
-__device__ __forceinline__ float correlate(const float* __restrict__ gs, const float* raw, int* ebin, float* eval,
-                                           const int* cpe, float* cs, int nch, int T, bool empty, bool sparse,
+// C everywhere again after the linear-domain weights overwrote it (the rare fallback to the log-domain path):
+// out of line, so the hot loop's code stays small.
+template <int FMT>
+__device__ __noinline__ void recompute_all(const float* __restrict__ gs, const float* raw, const int* ebin,
+                                           const float* eval, int nnz, float* bnd, float* cs, bool empty, bool sparse,
                                            int NB, int D, int L, int u0, int lane) {
     if (empty) {
         zero_words(cs, NB * 8, lane);
-        return 0.f;
+    } else if (sparse) {
+        listed_range(gs, ebin, eval, nnz, bnd, cs, 0, NB - 1, D, L, u0, lane);
+    } else {
+        corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
     }
-    if (sparse) {
-        for (int i = lane; i < nch; i += 32) {  // compact the non-empty bins, in bin order
-            int o = cpe[i];
-            if (cpe[i + 1] == o) continue;
-            float f[CB];
-            convert_chunk<FMT>(raw, i, T, f);
-#pragma unroll
-            for (int k = 0; k < CB; ++k)
-                if (f[k] != 0.f) {
-                    ebin[o] = i * CB + k;
-                    eval[o++] = f[k];
-                }
-        }
-        __syncwarp();
-        return corr_taps(gs, ebin, eval, cpe[nch], cs, NB, D, L, u0, lane);
-    }
-    return corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -349,8 +432,7 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
     int* ebin = reinterpret_cast<int*>(base + sl.ebin);
     float* eval = base + sl.eval;
-    float* cps = base + sl.cps;
-    int* cpe = reinterpret_cast<int*>(base + sl.cpe);
+    float* bnd = base + sl.bnd;
     float* ubs = base + sl.ubs;
     float* cs = base + sl.cs;
     const long long P = static_cast<long long>(a.H) * a.W;
@@ -362,9 +444,16 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     }
 
     long long p = static_cast<long long>(blockIdx.x) * nwarps + warp;
+    // pixel coordinates of p and of the grid stride (P < 2^31), advanced without a division per pixel
+    int py = 0, px = 0;
+    if (p < P) {
+        py = static_cast<int>(p) / a.W;
+        px = static_cast<int>(p) - py * a.W;
+    }
+    const int sy = static_cast<int>(stride / a.W), sx = static_cast<int>(stride - static_cast<long long>(sy) * a.W);
     if (p < P) request_row(a, p, base + sl.raw, sl.nch, ESZ, lane);
     cp_async_commit();
-    Nbr nb_next = request_nbr(a, p, P, lane);
+    Nbr nb_next = request_nbr(a, p, py, px, P, lane);
 
     for (int buf = 0; p < P; p += stride, buf ^= 1) {
         const Nbr nb = nb_next;
@@ -374,47 +463,46 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         __syncwarp();
         {  // stage the next pixel's row into the other buffer and its neighbour states into registers
             const long long pn = p + stride;
+            px += sx;
+            py += sy;
+            if (px >= a.W) {
+                px -= a.W;
+                ++py;
+            }
             if (pn < P) request_row(a, pn, base + sl.raw + (buf ^ 1) * sl.rawsz, sl.nch, ESZ, lane);
             cp_async_commit();
-            nb_next = request_nbr(a, pn, P, lane);
+            nb_next = request_nbr(a, pn, py, px, P, lane);
         }
-        if (FMT != SPL_HIST_U16) {  // bins T .. pitch-1 are not data: make them zero for the dense windows
-            for (int t = T + lane; t < sl.nch * CB; t += 32) {
-                if (FMT == SPL_HIST_F32) raw[t] = 0.f;
-                else reinterpret_cast<unsigned short*>(raw)[t] = 0;
-            }
+        // bins T .. pitch-1 are not data: make them zero (the chunk test and the dense windows read them)
+        for (int t = T + lane; t < sl.nch * CB; t += 32) {
+            if (FMT == SPL_HIST_F32) raw[t] = 0.f;
+            else reinterpret_cast<unsigned short*>(raw)[t] = 0;
         }
+        __syncwarp();
 
-        // ---- 1. per-chunk photon and non-empty-bin counts of the staged row ----
+        // ---- 1. photons and non-empty bins of the staged row ----
         float K = 0.f;
         int nnz = 0;
         if (!faulty) {
-            for (int i = lane; i < sl.nch; i += 32) {
-                float f[CB];
-                convert_chunk<FMT>(raw, i, T, f);
-                float s = 0.f;
-                int c = 0;
-#pragma unroll
-                for (int k = 0; k < CB; ++k) {
-                    s += f[k];
-                    c += f[k] != 0.f;
-                }
-                cps[i] = s;
-                cpe[i] = c;
-                K += s;
-                nnz += c;
-            }
-            K = warp_sum(K);
-            nnz = static_cast<int>(warp_sum(static_cast<float>(nnz)));
-            __syncwarp();
-            warp_scan2(cps, cpe, sl.nch, lane);
+            const int M = nonempty_chunks(raw, sl.nch, reinterpret_cast<int*>(cs), lane);
+            count_and_list<FMT, CB>(raw, reinterpret_cast<const int*>(cs), M, T, ebin, eval, lane, K, nnz);
         }
         const bool empty = faulty || nnz == 0;
         const bool sparse = nnz <= kTapNnz;
 
-        // ---- 2. C(d) for every candidate ----
-        const float cmax =
-            correlate<FMT, CB>(gs, raw, ebin, eval, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane);
+        // ---- 2. C on every candidate: from the bin list (few non-empty bins; each block also gets the photons
+        // that reach it, its data bound) or by the dense sum (whose largest C bounds every block) ----
+        float cmax = 0.f;
+        if (empty) {
+            zero_words(cs, NB * 8, lane);
+        } else if (sparse) {
+            zero_words(bnd, (NB + 3) >> 2, lane);
+            block_photons(ebin, eval, nnz, bnd, D, L, u0, lane);
+            cmax = listed_range(gs, ebin, eval, nnz, bnd, cs, 0, NB - 1, D, L, u0, lane);
+        } else {
+            cmax = corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
+        }
+        auto ensure = [&](int, int) { return cmax; };
 
         if (COST_ONLY) {
             float best = -INFINITY;
@@ -462,14 +550,22 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         grid.L = L;
         grid.lam2 = a.lam2;
         grid.gmax = gmax;
+        const float lam2 = a.lam2;
+        const int ub_b = block_bounds(
+            grid, pr, ubs,
+            [&](int b) {
+                if (empty) return 0.f;
+                if (sparse) return lam2 * gmax * bnd[b] * 1.0001f;
+                return lam2 * cmax * 1.0001f;
+            },
+            lane);
         int bidx;
         float mu, var;
-        posterior(
-            grid, pr, cmax, empty, cs, ubs, [&](int s_bin, int e_bin) { return cps[e_bin / CB + 1] - cps[s_bin / CB]; },
-            [&]() {
-                correlate<FMT, CB>(gs, raw, ebin, eval, cpe, cs, sl.nch, T, empty, sparse, NB, D, L, u0, lane);
-            },
-            lane, bidx, mu, var);
+        posterior_eval(grid, pr, cs, ubs, ub_b, ensure,
+                       [&]() {
+                           recompute_all<FMT>(gs, raw, ebin, eval, nnz, bnd, cs, empty, sparse, NB, D, L, u0, lane);
+                       },
+                       lane, bidx, mu, var);
         if (lane == 0) {
             a.mu[p] = mu;
             a.var[p] = var;

@@ -99,13 +99,16 @@ __device__ __forceinline__ void build_prior(float w, float m, float v, int lane,
     pr.minv = INFINITY;
 #pragma unroll
     for (int i = 0; i < kMaxComp; ++i) {
-        const int src = lead ? __ffs(lead) - 1 : 0;
-        lead &= lead - 1;
-        pr.ca[i] = __shfl_sync(0xffffffffu, ca_l, src);
-        pr.ck[i] = __shfl_sync(0xffffffffu, ck_l, src);
-        pr.cm[i] = __shfl_sync(0xffffffffu, m, src);
-        const float vi = __shfl_sync(0xffffffffu, v, src);
-        if (i < pr.n) pr.minv = fminf(pr.minv, vi);
+        if (i < pr.n) {  // warp-uniform: only the distinct components are broadcast
+            const int src = __ffs(lead) - 1;
+            lead &= lead - 1;
+            pr.ca[i] = __shfl_sync(0xffffffffu, ca_l, src);
+            pr.ck[i] = __shfl_sync(0xffffffffu, ck_l, src);
+            pr.cm[i] = __shfl_sync(0xffffffffu, m, src);
+            pr.minv = fminf(pr.minv, __shfl_sync(0xffffffffu, v, src));
+        } else {
+            pr.ca[i] = pr.ck[i] = pr.cm[i] = 0.f;
+        }
     }
 }
 

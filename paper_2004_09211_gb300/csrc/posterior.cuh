@@ -112,22 +112,17 @@ __device__ __forceinline__ float corr_photons(const float* __restrict__ gs, cons
     return warp_max(mx);
 }
 
-// cs[0 .. D) holds C(d) on entry; cs[0 .. 32 NB) and ubs[0 .. NB) are scratch. count(s, e) returns an upper
-// bound of the photons in bins [s, e] (evaluated per lane). restore() writes C back into cs (needed only on
-// the rare fallback from the linear path). Outputs: index of the smallest maximiser, mean depth and variance.
-template <class Count, class Restore>
-__device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float cmax, bool empty, float* cs,
-                                          float* ubs, Count count, Restore restore, int lane, int& bidx_out,
-                                          float& mu_out, float& var_out) {
+// Per-block upper bounds of ell = lambda log2(e) C(d) + log2 f(d) into ubs[0 .. NB): dub(b) is an upper bound of
+// lambda log2(e) C over block b (evaluated per lane), the prior's part is log2_prior_bound. Returns the block with
+// the largest bound (warp-uniform; 0 if every bound is NaN).
+template <class DataBound>
+__device__ __forceinline__ int block_bounds(const Grid& g, const Prior& pr, float* ubs, DataBound dub, int lane) {
     const int D = g.D, NB = g.NB;
-    const float lam2 = g.lam2;
-    // per-block upper bounds of ell
     float ubest = -INFINITY;
     int ub_b = 0x7fffffff;
     for (int b = lane; b < NB; b += 32) {
         const int last = min(32 * b + 31, D - 1);
-        const float nb = empty ? 0.f : count(g.u0 + 32 * b, g.u0 + last + g.L - 1);
-        const float ub = lam2 * g.gmax * nb * 1.0001f +
+        const float ub = dub(b) +
                          log2_prior_bound(pr, static_cast<float>(g.dmin + 32 * b), static_cast<float>(g.dmin + last));
         ubs[b] = ub;
         if (ub > ubest) {
@@ -138,6 +133,21 @@ __device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float 
     warp_argmax(ubest, ub_b);
     if (ub_b >= NB) ub_b = 0;  // every bound was NaN (invalid inputs): keep the block index in range
     __syncwarp();
+    return ub_b;
+}
+
+// The pseudo-posterior from the block bounds: cs holds C on block ub_b on entry. The best value of that block is a
+// lower bound LB of the maximum; blocks whose bound is below LB - 64 are dropped. ensure(bfirst, blast) must then
+// put C into cs on every block of the kept range [bfirst, blast] (at least on the kept ones; a dropped block may
+// read as C = 0) and return max C over that range (warp-uniform). restore() writes C back on the kept range
+// (needed only on the rare fallback from the linear path, whose weights overwrite cs). Outputs: index of the
+// smallest maximiser, mean depth and variance.
+template <class Ensure, class Restore>
+__device__ __forceinline__ void posterior_eval(const Grid& g, const Prior& pr, float* cs, const float* ubs, int ub_b,
+                                               Ensure ensure, Restore restore, int lane, int& bidx_out,
+                                               float& mu_out, float& var_out) {
+    const int D = g.D, NB = g.NB;
+    const float lam2 = g.lam2;
 
     // exact best value of the block with the largest bound: a lower bound of the maximum, and its position
     float lb;
@@ -162,13 +172,15 @@ __device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float 
         }
     }
 
+    const float cmax = ensure(bfirst, blast);
+
     // ---- linear-domain weights over the range of kept blocks ----
     if ((blast - bfirst + 1) <= max(8, 2 * nsurv) && !(pr.minv < 1.5f)) {
         float sref = pr.n > 0 ? -INFINITY : 0.f;
 #pragma unroll
         for (int i = 0; i < kMaxComp; ++i)
             if (i < pr.n) sref = fmaxf(sref, pr.ca[i]);
-        const float xref = lam2 * cmax;  // lambda log2(e) max_d C(d)
+        const float xref = lam2 * cmax;  // lambda log2(e) max C over the kept range
         const int c_lo = 32 * bfirst, c_hi = min(32 * blast + 31, D - 1);
         const int run = (c_hi - c_lo + 32) >> 5;
         const int r0 = c_lo + lane * run, r1 = min(r0 + run, c_hi + 1);
@@ -260,6 +272,23 @@ __device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float 
     bidx_out = bidx;
     mu_out = static_cast<float>(g.dmin + bidx) + m1;
     var_out = fmaxf(s2 / s0 - m1 * m1, 0.f);
+}
+
+// The photon-list kernels' form: C already on every candidate (cmax its maximum, empty: no photons); count(s, e)
+// returns an upper bound of the photons in bins [s, e] (evaluated per lane).
+template <class Count, class Restore>
+__device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float cmax, bool empty, float* cs,
+                                          float* ubs, Count count, Restore restore, int lane, int& bidx_out,
+                                          float& mu_out, float& var_out) {
+    const int ub_b = block_bounds(
+        g, pr, ubs,
+        [&](int b) {
+            const int last = min(32 * b + 31, g.D - 1);
+            const float nb = empty ? 0.f : count(g.u0 + 32 * b, g.u0 + last + g.L - 1);
+            return g.lam2 * g.gmax * nb * 1.0001f;
+        },
+        lane);
+    posterior_eval(g, pr, cs, ubs, ub_b, [&](int, int) { return cmax; }, restore, lane, bidx_out, mu_out, var_out);
 }
 
 }  // namespace px
