@@ -82,6 +82,7 @@ def lib():
             L.orc_log_lik_ratio.argtypes = [P, d, d, ct.c_int, ct.c_double, ct.c_double]
             L.orc_log_lik_ratio.restype = ct.c_double
             L.orc_detect.argtypes = [P, d, d, ct.c_long, d, i32, d, d, u8, d, d, u8, d, d]
+            L.orc_estimate_msl.argtypes = [P, ct.c_int, d, d, ct.c_long, d, d, i32, d, d, d, d]
             _lib = L
     return _lib
 
@@ -192,6 +193,36 @@ def estimate_fine(q: Params, S: int, h, z, prior_mu=None, prior_var=None, want_e
         out["ell"] = ell.reshape(*shape, Kf)
     if want_cost:
         out["cost"] = cst.reshape(*shape, Kf)
+    return out
+
+
+def estimate_msl(q: Params, h_bands, z_bands, prior_mu=None, prior_var=None, want_ell=False, want_cost=False):
+    """Multispectral estimate (Appendix, Eq. div_MSL): h_bands [nb, L], z_bands [nb, H, W, T] (or [nb, P, T]).
+    Returns dict(argmax, mu, var[, M][, ell]) shaped like one band's pixels."""
+    hb = _d(h_bands).reshape(-1)
+    zb = _d(z_bands)
+    nb = zb.shape[0]
+    shape = zb.shape[1:-1]
+    P = int(np.prod(shape))
+    D = q.dmax - q.dmin + 1
+    L = hb.size // nb
+    assert L == q.L, "every band has L taps"
+    zf = np.ascontiguousarray(zb.reshape(nb, P, q.T))
+    pm = None if prior_mu is None else _d(prior_mu).reshape(-1)
+    pv = None if prior_var is None else _d(prior_var).reshape(-1)
+    a = np.empty(P, np.int32)
+    mu = np.empty(P)
+    var = np.empty(P)
+    M = np.empty((P, D)) if want_cost else None
+    ell = np.empty((P, D)) if want_ell else None
+    lib().orc_estimate_msl(ct.byref(q), nb, _ptr(hb, ct.c_double), _ptr(zf, ct.c_double), P, _ptr(pm, ct.c_double),
+                           _ptr(pv, ct.c_double), _ptr(a, ct.c_int32), _ptr(mu, ct.c_double), _ptr(var, ct.c_double),
+                           _ptr(M, ct.c_double), _ptr(ell, ct.c_double))
+    out = dict(argmax=a.reshape(shape), mu=mu.reshape(shape), var=var.reshape(shape))
+    if want_cost:
+        out["M"] = M.reshape(*shape, D)
+    if want_ell:
+        out["ell"] = ell.reshape(*shape, D)
     return out
 
 

@@ -48,6 +48,26 @@ def asymmetric_irf(L: int = 48, shape: float = 4.0, scale: float = 1.6, tail_tau
     return h, int(np.argmax(h))
 
 
+def band_irfs(nb: int, L: int = 48, peak: int = 12) -> np.ndarray:
+    """nb asymmetric IRFs of different widths and tails (one per spectral band), each L taps with its maximum moved
+    to tap `peak` (zero-padded on the left or cut on the right, then unit sum). Returns [nb, L] float32."""
+    out = np.zeros((nb, L), np.float32)
+    for b in range(nb):
+        h, pk = asymmetric_irf(L=L, shape=3.0 + 0.7 * b, scale=1.2 + 0.35 * b, tail_tau=6.0 + 3.0 * b,
+                               tail_weight=0.15 + 0.1 * b)
+        h = h.astype(np.float64)
+        g = np.zeros(L)
+        sh = peak - pk
+        if sh >= 0:
+            g[sh:] = h[:L - sh]
+        else:
+            g[:L + sh] = h[-sh:]
+        g /= g.sum()
+        out[b] = g.astype(np.float32)
+        assert int(np.argmax(out[b])) == peak
+    return out
+
+
 def stretched_irf(h: np.ndarray, L_new: int) -> tuple[np.ndarray, int]:
     """Resample an IRF onto L_new taps (linear interpolation), unit sum."""
     x_old = np.linspace(0.0, 1.0, len(h))

@@ -12,6 +12,7 @@ import os
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2004_09211_gb300 import synth
 
@@ -487,6 +488,115 @@ def test_intensity_rule_per_pixel(orc):
         rr, bb = _box_closed_form(z[p], int(dr[p]), L, peak)
         assert r_dr[p] == pytest.approx(rr, rel=1e-9, abs=1e-9)
         assert b_dr[p] == pytest.approx(bb, rel=1e-9, abs=1e-12)
+
+
+# ------------------------------------------------------------------------------------------------------
+# Multispectral data (Appendix, Eq. div_MSL): M(d) = prod_l C_l(d) / K_l
+# ------------------------------------------------------------------------------------------------------
+
+
+def _msl_inputs(seed, nb=3, H=3, W=4, T=220, L=24, peak=8, signal=25.0, bg=0.05):
+    hb = synth.band_irfs(nb, L, peak)
+    rng = _rng(seed)
+    dmin, dmax = peak, T - L + peak
+    depth = rng.integers(dmin + 3, dmax - 3, size=(H, W))
+    z = np.empty((nb, H, W, T))
+    for b in range(nb):
+        mean = synth.expected_counts(torch.from_numpy(depth), torch.full((H, W), signal, dtype=torch.float64), bg,
+                                     torch.from_numpy(hb[b]), peak, T)
+        z[b] = rng.poisson(mean.numpy())
+    return hb, peak, depth, z
+
+
+def test_msl_one_band_is_the_single_band_estimate(orc):
+    """With one band, M = C / K and lambda K M = lambda C: the single-band pseudo-posterior of Eq. approx_post."""
+    hb, peak, _, z = _msl_inputs(41, nb=1)
+    q = orc.params(z.shape[-1], hb.shape[1], peak, beta=0.6)
+    rng = _rng(42)
+    pm = rng.uniform(q.dmin, q.dmax, size=z.shape[1:3])
+    pv = rng.uniform(10, 400, size=z.shape[1:3])
+    for prior in (None, (pm, pv)):
+        a = orc.estimate_msl(q, hb, z, *(prior or (None, None)))
+        e = orc.estimate(q, hb[0], z[0], *(prior or (None, None)))
+        assert np.array_equal(a["argmax"], e["argmax"])
+        np.testing.assert_allclose(a["mu"], e["mu"], rtol=1e-12)
+        np.testing.assert_allclose(a["var"], e["var"], rtol=1e-9)
+
+
+def test_msl_photon_list_form(orc):
+    """Eq. div_MSL is written over the photons' times of arrival: prod_l (1/K_l) sum_k h_l[y_{l,k} - d + peak]^beta,
+    evaluated here photon by photon from lists drawn from the histograms, against the oracle's histogram form."""
+    hb, peak, _, z = _msl_inputs(43, nb=3)
+    nb, H, W, T = z.shape
+    L = hb.shape[1]
+    beta = 0.45
+    q = orc.params(T, L, peak, beta=beta)
+    M = orc.estimate_msl(q, hb, z, want_cost=True)["M"]
+    d = np.arange(q.dmin, q.dmax + 1)
+    for y in range(H):
+        for x in range(W):
+            ref = np.ones(d.size)
+            for b in range(nb):
+                ys = np.repeat(np.arange(T), z[b, y, x].astype(int))
+                if ys.size == 0:
+                    continue
+                j = ys[None, :] - d[:, None] + peak
+                inside = (j >= 0) & (j < L)
+                g = np.where(inside, hb[b].astype(np.float64)[np.clip(j, 0, L - 1)], 0.0) ** beta
+                ref *= g.sum(axis=1) / ys.size
+            np.testing.assert_allclose(M[y, x], ref, rtol=1e-12, atol=1e-300)
+
+
+def test_msl_identical_bands(orc):
+    """nb copies of one band: M = (C / K)^nb, so the minimum-divergence estimate is the single band's, and the log
+    pseudo-posterior is lambda nb K (C / K)^nb (the data's K counted once per band)."""
+    hb, peak, _, z = _msl_inputs(44, nb=1)
+    T, L = z.shape[-1], hb.shape[1]
+    beta = 0.5
+    q = orc.params(T, L, peak, beta=beta)
+    one = orc.estimate(q, hb[0], z[0], want_ell=True)
+    lam = (beta + 1) / beta
+    for nb in (2, 3):
+        a = orc.estimate_msl(q, np.repeat(hb, nb, 0), np.repeat(z, nb, 0), want_ell=True)
+        assert np.array_equal(a["argmax"], one["argmax"])
+        K = z[0].sum(-1, keepdims=True)
+        C = one["ell"] / lam
+        np.testing.assert_allclose(a["ell"], lam * nb * K * (C / K) ** nb, rtol=1e-10)
+
+
+@pytest.mark.parametrize("beta", [0.2, 0.7, 1.0])
+def test_msl_noiseless_templates_are_recovered(orc, beta):
+    """Each band holds A_l s_{l,d*} with its own IRF and amplitude, no background: every factor C_l / K_l peaks
+    strictly at d* (Hoelder, as for one band), so the product does too."""
+    nb, L, peak, T = 4, 24, 8, 180
+    hb = synth.band_irfs(nb, L, peak).astype(np.float64)
+    q = orc.params(T, L, peak, beta=beta)
+    rng = _rng(45)
+    for trial in range(6):
+        ds = int(rng.integers(q.dmin, q.dmax + 1))
+        z = np.zeros((nb, 1, 1, T))
+        for b in range(nb):
+            z[b, 0, 0, ds - peak:ds - peak + L] = rng.uniform(1e3, 1e5) * hb[b]
+        a = orc.estimate_msl(q, hb, z)
+        assert int(a["argmax"][0, 0]) == ds
+
+
+def test_msl_empty_band_and_band_order(orc):
+    """A band without photons contributes no factor; the bands' order does not matter."""
+    hb, peak, _, z = _msl_inputs(46, nb=3)
+    q = orc.params(z.shape[-1], hb.shape[1], peak, beta=0.5)
+    base = orc.estimate_msl(q, hb, z, want_cost=True)
+    ze = np.concatenate([z, np.zeros_like(z[:1])])
+    he = np.concatenate([hb, synth.band_irfs(4, hb.shape[1], peak)[3:]])
+    e = orc.estimate_msl(q, he, ze, want_cost=True)
+    np.testing.assert_array_equal(e["M"], base["M"])
+    perm = [2, 0, 1]
+    r = orc.estimate_msl(q, hb[perm], z[perm], want_cost=True)
+    np.testing.assert_allclose(r["M"], base["M"], rtol=1e-13)
+    assert np.array_equal(r["argmax"], base["argmax"])
+    zero = orc.estimate_msl(q, hb, np.zeros_like(z))
+    prior_free = (q.dmin + q.dmax) / 2.0
+    np.testing.assert_allclose(zero["mu"], prior_free, rtol=1e-12)
 
 
 # ------------------------------------------------------------------------------------------------------
