@@ -121,14 +121,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="video", choices=["video", "batched", "diff", "mixed", "video_tc", "detect",
-                                                              "pd_curves", "fine", "alu_peaks"],
+                                                              "pd_curves", "fine", "alu_peaks", "msl"],
                     help="video (default, the headline line); batched: 64 photon-list sequences in one launch per "
                          "frame; diff: differentiable filter forward + backward; mixed: 1024x1024 FP16 frames "
                          "through the tensor-core filter step; video_tc: the video job through the tensor-core "
                          "filter step on FP16 copies of its frames, beside the FP32 path; detect: the video job "
                          "with the presence decision on the device (detection surrogate + Eq. prior_detect); "
                          "pd_curves: the single-pixel p_d experiment of Sec. IV-A (Gaussian IRF, five betas); "
-                         "fine: single-frame estimates on the sub-bin grid; alu_peaks: measured FP32 FMA, packed "
+                         "fine: single-frame estimates on the sub-bin grid; msl: multispectral estimate (4 bands); "
+                         "alu_peaks: measured FP32 FMA, packed "
                          "FMA and ex2 throughput (the denominators of the ALU rooflines)")
     return ap.parse_args()
 
@@ -1184,6 +1185,72 @@ def mixed_cpu_baseline(spl, synth, h, hd, peak, sc, dev):
                                  "max_rel": float((np.abs(d) / np.abs(m)).max())}}
 
 
+MSL_BANDS, MSL_SEED, MSL_SBR = 4, 7, 0.2
+
+
+def msl(args):
+    """Multispectral estimate (Appendix, Eq. div_MSL): 256 x 256 pixels, 4 bands, T = 1500, 48-tap band IRFs of
+    different widths and tails (maxima aligned), beta = 0.5, the video scene's first frame (tilted plane + 3
+    objects), 5-25 signal photons per pixel in each band (the video scene's 1-5, times 5, times per-band gains 0.8-1.2)
+    and the same SBR, 0.2, in every band (the paper's multispectral experiment uses the same SBR and signal level in
+    all bands; at this photon level one band alone often misses the surface). One step = one
+    spl_depth_estimate_msl launch over the frame, without a prior (the minimum-divergence estimate of the paper's
+    multispectral experiment); the histograms (4 x 197 MB) stay resident. Also reported: the depth RMSE of the
+    4-band estimate and of band 0 alone (spl_depth_estimate) against the ground truth."""
+    import paper_2004_09211_gb300 as spl
+    from paper_2004_09211_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spl.load_library()
+    nb, peak = MSL_BANDS, 12
+    hb = synth.band_irfs(nb, L, peak)
+    sc = synth.moving_scene(H, W, 1, peak + 8, T - L + peak - 8, MSL_SEED)
+    gen = torch.Generator(device=dev).manual_seed(MSL_SEED)
+    pitch = synth.pad_pitch(T)
+    P = H * W
+    gains = (0.8, 1.0, 1.2, 0.9)
+    z = torch.empty(nb, P, pitch, dtype=torch.uint16, device=dev)
+    depth = torch.from_numpy(sc.depth[0]).to(dev)
+    for b in range(nb):
+        sig = torch.from_numpy(sc.signal[0]).to(dev) * (5.0 * gains[b])
+        mean = synth.expected_counts(depth, sig, float(sig.mean()) / (MSL_SBR * T), torch.from_numpy(hb[b]).to(dev),
+                                     peak, T)
+        z[b] = synth.pitched(synth.poisson_histograms(mean, gen).reshape(P, T), pitch)
+    hd = torch.from_numpy(hb).to(dev)
+    prm = spl.make_params(H, W, T, L, peak, beta=0.5)
+    out = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), mu=torch.empty(P, device=dev),
+               var=torch.empty(P, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        spl.spl_depth_estimate_msl(prm, z, hd, out=out)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            spl.spl_depth_estimate_msl(prm, z, hd, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    gt = depth.reshape(-1).float()
+    rmse = float((out["argmax"].float() - gt).pow(2).mean().sqrt())
+    one = spl.spl_depth_estimate(prm, z[0].contiguous(), hd[0].contiguous())
+    torch.cuda.synchronize(dev)
+    rmse1 = float((one["argmax"].float() - gt).pow(2).mean().sqrt())
+    peaks = _peaks()
+    alg = P * (nb * 2 * T + 12)
+    line = {"metric": "pixel-estimates/s", "value": P / (ms / 1e3), "unit": "pixel-estimates/s (4 bands each)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"multispectral {H}x{W}, {nb} bands, T={T}, L={L}, 5-25 signal photons, "
+                                   f"SBR {MSL_SBR}, beta 0.5, no prior",
+                       "pixels": P, "bands": nb, "l2": f"inputs larger than L2 ({nb} x 197 MB), no flush"},
+            "rmse_bins": {"msl_argmax": rmse, "band0_alone_argmax": rmse1},
+            "roofline": hbm_roofline(peaks, alg, ms / 1e3, None, "k_estimate_msl<u16> (one launch)"),
+            "gpu_launches": args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def alu_peaks(args):
     """Measured arithmetic throughput of this GPU: FFMA, packed f32x2 FMA and MUFU ex2 (spl_probe_throughput),
     as operations per clock per SM (from the blocks' own clock64 counts) and per second (CUDA events), at 4 and 8
@@ -1253,6 +1320,8 @@ def main():
         fine(args)
     elif args.workload == "alu_peaks":
         alu_peaks(args)
+    elif args.workload == "msl":
+        msl(args)
     else:
         native(args)
 

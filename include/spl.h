@@ -147,6 +147,29 @@ SPL_API spl_status spl_depth_estimate_fine(const spl_params* prm, int S, const s
                                            const float* prior_mu, const float* prior_var, int32_t* argmax_fine,
                                            float* mu, float* var, void* stream);
 
+/* Most spectral bands spl_depth_estimate_msl accepts. */
+#define SPL_MAX_BANDS 8
+
+/*
+ * spl_depth_estimate_msl -- depth from multispectral data (Appendix, Eq. div_MSL): nbands wavelengths recorded at
+ *   once by independent detectors, band l with its own IRF h + l * L (all bands have L taps and their maximum at
+ *   tap `peak`, and share beta). The beta-divergence between the product of the bands' empirical ToA distributions
+ *   and the product model is, up to a constant, -lambda M(d) with
+ *     M(d) = prod_l C_l(d) / K_l,   C_l(d) = sum_t z_l[t] h_l[t - d + peak]^beta,   K_l = photons of band l
+ *   (a product over bands of normalised sums). A band without photons contributes no factor.
+ *   Pseudo-posterior (a reading: the paper defines the minimum-divergence estimator for these data, not the scale
+ *   of a pseudo-likelihood): f(d) exp(lambda K M(d)) with K = sum_l K_l, which for one band is the pseudo-posterior
+ *   of spl_depth_estimate. f = N(prior_mu[p], prior_var[p]) or uniform (prior_mu NULL); without a prior the argmax
+ *   is the minimum-divergence estimate.
+ *   z: histograms of every band, band l's row of pixel p at element (l * P + p) * pitch of z->data (same layout
+ *   rules as spl_hist). h: [nbands][L] device. nbands in 1..SPL_MAX_BANDS.
+ *   Outputs: argmax [P] (nullable: smallest maximiser of the log pseudo-posterior), mu, var [P] (its mean and
+ *   variance), cost [P][D] (nullable: M(dmin + k)).
+ */
+SPL_API spl_status spl_depth_estimate_msl(const spl_params* prm, int nbands, const spl_hist* z, const float* h,
+                                          const float* prior_mu, const float* prior_var, int32_t* argmax, float* mu,
+                                          float* var, float* cost, void* stream);
+
 /*
  * spl_filter_step -- one frame of the online filter (one outer iteration of Algorithm 1).
  *   Prior (Eq. predict): for each pixel p, a Gaussian mixture over the 3x3 stencil with weights nu. Stencil

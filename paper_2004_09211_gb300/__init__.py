@@ -208,6 +208,33 @@ def spl_depth_estimate_fine(prm: spl_params, S: int, z: torch.Tensor, h: torch.T
     return o
 
 
+def spl_depth_estimate_msl(prm: spl_params, z: torch.Tensor, h: torch.Tensor, prior_mu=None, prior_var=None,
+                           want_cost: bool = False, out: dict | None = None, stream=None) -> dict:
+    """Multispectral estimate (Appendix, Eq. div_MSL). z: [nbands, P, pitch] (or [nbands, H, W, pitch]) histograms,
+    h: [nbands, L] IRFs. Returns dict(argmax, mu, var[, cost])."""
+    if not isinstance(z, torch.Tensor) or z.dim() < 2 or not z.is_contiguous():
+        raise TypeError("z must be a contiguous CUDA tensor [nbands, ..., pitch]")
+    nb = int(z.shape[0])
+    P, D = _P(prm), _D(prm)
+    if h.numel() != nb * prm.L:
+        raise ValueError(f"h must hold nbands * L = {nb} * {prm.L} taps")
+    o = dict(out or {})
+    o.setdefault("argmax", _empty((P,), torch.int32, z))
+    o.setdefault("mu", _empty((P,), torch.float32, z))
+    o.setdefault("var", _empty((P,), torch.float32, z))
+    if want_cost:
+        o.setdefault("cost", _empty((P, D), torch.float32, z))
+    hz = _hist(prm, z[0])
+    hz.data = z.data_ptr()
+    lib = _abi.load()
+    _abi.check(lib.spl_depth_estimate_msl(
+        ct.byref(prm), nb, ct.byref(hz), _dev(h, "h", torch.float32, nb * prm.L),
+        _dev(prior_mu, "prior_mu", torch.float32, P), _dev(prior_var, "prior_var", torch.float32, P),
+        _dev(o.get("argmax"), "argmax", torch.int32, P), _dev(o["mu"], "mu", torch.float32, P),
+        _dev(o["var"], "var", torch.float32, P), _dev(o.get("cost"), "cost", torch.float32, P * D), _stream(stream)))
+    return o
+
+
 def spl_filter_step(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor, var_in: torch.Tensor,
                     present_in=None, faulty=None, present_now=None, intensity: bool = True,
                     out: dict | None = None, stream=None, _entry: str = "spl_filter_step") -> dict:

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "SPL_OK", 1: "SPL_EINVAL", 2: "SPL_ENOMEM", 3: "SPL_ECUDA", 4
 SPL_HIST_U16, SPL_HIST_F16, SPL_HIST_F32 = 0, 1, 2
 SPL_MAX_TAPS = 128
 SPL_MAX_BINS = 8192
+SPL_MAX_BANDS = 8
 
 
 class spl_params(ct.Structure):
@@ -61,6 +62,7 @@ SIGNATURES = {
     "spl_depth_estimate": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_filter_step": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_depth_estimate_fine": (ct.c_int, [_P, ct.c_int, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "spl_depth_estimate_msl": (ct.c_int, [_P, ct.c_int, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_filter_step_detect": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                           _vp, _vp]),
     "spl_filter_step_tc": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),

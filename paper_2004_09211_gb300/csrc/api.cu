@@ -185,6 +185,42 @@ spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, const fl
     return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_depth_estimate launch");
 }
 
+spl_status spl_depth_estimate_msl(const spl_params* prm, int nbands, const spl_hist* z, const float* h,
+                                  const float* prior_mu, const float* prior_var, int32_t* argmax, float* mu, float* var,
+                                  float* cost, void* stream) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, false);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(nbands >= 1 && nbands <= SPL_MAX_BANDS, "nbands must be in 1..%d (got %d)", SPL_MAX_BANDS, nbands);
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(mu != nullptr && var != nullptr, "mu and var outputs are required");
+    SPL_REQUIRE((prior_mu == nullptr) == (prior_var == nullptr), "give both prior_mu and prior_var or neither");
+    MslArgs a;
+    memset(&a, 0, sizeof(a));
+    a.z = z->data;
+    a.pitch = z->pitch;
+    a.fmt = z->fmt;
+    a.h = h;
+    a.nbands = nbands;
+    a.H = prm->H;
+    a.W = prm->W;
+    a.T = prm->T;
+    a.L = prm->L;
+    a.peak = prm->peak;
+    a.dmin = prm->dmin;
+    a.D = prm->dmax - prm->dmin + 1;
+    a.beta = prm->beta;
+    a.lam2 = static_cast<float>((static_cast<double>(prm->beta) + 1.0) / prm->beta * 1.4426950408889634);
+    a.pmu = prior_mu;
+    a.pvar = prior_var;
+    a.argmax = argmax;
+    a.mu = mu;
+    a.var = var;
+    a.cost = cost;
+    return cuda_status(launch_estimate_msl(a, static_cast<cudaStream_t>(stream)), "spl_depth_estimate_msl launch");
+}
+
 spl_status spl_depth_estimate_fine(const spl_params* prm, int S, const spl_hist* z, const float* h,
                                    const float* prior_mu, const float* prior_var, int32_t* argmax_fine, float* mu,
                                    float* var, void* stream) {

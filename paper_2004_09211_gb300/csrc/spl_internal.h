@@ -47,6 +47,24 @@ struct EstimateArgs {
     uint8_t* present_out;   // pi_out > 0.5 (nullable)
 };
 
+// One launch of the multispectral estimate (msl.cu): band l's row of pixel p is row l * P + p of z.
+struct MslArgs {
+    const void* z;
+    long long pitch;
+    int fmt;
+    const float* h;  // [nbands][L]
+    int nbands;
+    int H, W, T, L, peak, dmin, D;
+    float beta;
+    float lam2;      // lambda * log2(e)
+    const float* pmu;
+    const float* pvar;
+    int* argmax;
+    float* mu;
+    float* var;
+    float* cost;     // [P][D] M(d), nullable
+};
+
 // Launch geometry chosen on the host for one launch.
 struct Geometry {
     int warps_per_cta;
@@ -65,6 +83,8 @@ cudaError_t launch_estimate(const EstimateArgs& a, bool cost_only, cudaStream_t 
 // Sub-bin grid (fine.cu): S steps per bin; argmax_k receives fine indices. Shared memory per warp: fine_warp_bytes.
 cudaError_t launch_estimate_fine(const EstimateArgs& a, int S, int* argmax_k, cudaStream_t s);
 size_t fine_warp_bytes(int T, int D, int S);
+cudaError_t launch_estimate_msl(const MslArgs& a, cudaStream_t s);
+size_t msl_warp_bytes(int T, int D);
 cudaError_t launch_state_init(int P, float m, float v, float* mu, float* var, cudaStream_t s);
 cudaError_t launch_pi_propagate(int H, int W, const float* nu, const float* pi_in, const uint8_t* faulty,
                                 float* pi_out, cudaStream_t s);
