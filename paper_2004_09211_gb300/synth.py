@@ -111,6 +111,15 @@ class MovingScene:
     signal: np.ndarray  # [N, H, W] float64
     dlo: int
     dhi: int
+    plane: np.ndarray = None  # [H, W] int64: the background plane's depth bin (where no object covers a pixel)
+
+    def static_mask(self, n: int) -> np.ndarray:
+        """Pixels that show the background plane in every frame 0 .. n (no object ever covered them)."""
+        return np.all(self.depth[:n + 1] == self.plane, axis=0)
+
+    def object_mask(self, n: int) -> np.ndarray:
+        """Pixels covered by a moving object in frame n."""
+        return self.depth[n] != self.plane
 
 
 def moving_scene(H: int, W: int, N: int, dlo: int, dhi: int, seed: int, n_objects: int = 3,
@@ -157,7 +166,7 @@ def moving_scene(H: int, W: int, N: int, dlo: int, dhi: int, seed: int, n_object
             if o["d"] < dlo or o["d"] > dhi:
                 o["vd"] = -o["vd"]
                 o["d"] = min(max(o["d"], dlo), dhi)
-    return MovingScene(depth, signal, dlo, dhi)
+    return MovingScene(depth, signal, dlo, dhi, np.clip(np.rint(plane), dlo, dhi).astype(np.int64))
 
 
 # --------------------------------------------------------------------------------------------------------
