@@ -50,29 +50,30 @@ WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.
 # compiles; the pseudo-posterior code lives in posterior.cuh, apart from the helpers in pixel.cuh, so that a change
 # to it voids exactly the captures of the kernels that call it (the depth and photon-list kernels).
 TRAFFIC_CAPTURES = {
-    # one filter step of the video job: mean over frames 0-3 of the nine runs (36 launches of each kernel;
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum)
+    # one filter step of the video job: the depth launch of frame 1 of each of the nine runs (nine captures of one
+    # launch each, mean) plus one intensity launch (ncu dram__bytes_read.sum + dram__bytes_write.sum and
+    # smsp__inst_executed.sum)
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "posterior.cuh", "intensity.cu"),
-                   "sha256": "a36f7c2d6073825af831149b14a907d3ccc97952a1dbc9d6c34201d1536f89a1",
-                   "bytes_per_pixel": (198.45e6 + 15.43e6) / 65536,
-                   "inst_per_pixel": (376.12e6 + 17.46e6) / 65536},
+                   "sha256": "22025118640148994099e30833995a84a537b0d6b300dea1a057c752c571b224",
+                   "bytes_per_pixel": (197.76e6 + 3.45e6 + 15.60e6) / 65536,
+                   "inst_per_pixel": (369.11e6 + 25.01e6) / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh"),
-                    "sha256": "3504d8aa37f4119a2212c012d4174919f373cb7607b8affd5b6daa0919628dce",
-                    "bytes_per_pixel": (542.29e6 + 17.20e6) / 65536,
+                    "sha256": "4b91b965a951a7a579e6b8795932c4705fd37b0ae2963e43304adc5e2c2fd601",
+                    "bytes_per_pixel": (537.63e6 + 3.65e6 + 17.20e6) / 65536,
                     # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture
-                    # of a 256 x 256 frame of the mixed workload
-                    "inst_per_pixel": (343.21e6 + 16.98e6) / 65536},
+                    # of frame 2 of a 256 x 256 run of the mixed workload
+                    "inst_per_pixel": (343.85e6 + 17.01e6) / 65536},
     # one launch of the photon-list kernel over all 64 sequences of the batched workload (7 050 240 pixels)
     "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh"),
-                "sha256": "873cefe879aacd19fac8786189689c74b59cd3aecd920ba6d05a93ffebf97ea1",
-                "bytes_per_pixel": (457.70e6 + 124.52e6) / 7050240,
-                "inst_per_pixel": 26806.0e6 / 7050240},
-    # backward launches of the differentiable filter (128 x 128 frames, T = 1024): mean over the 20 launches of
-    # one reverse sweep
+                "sha256": "585ff8de6b0e1a71af734418f99a1c28ee91fca076e604241645070f396834e2",
+                "bytes_per_pixel": (457.30e6 + 124.85e6) / 7050240,
+                "inst_per_pixel": 32877.47e6 / 7050240},
+    # backward launches of the differentiable filter (128 x 128 frames, T = 1024): mean of three of the 20 launches
+    # of one reverse sweep (they differ by 0.04 %)
     "k_diff_backward": {"sources": ("grad.cu", "pixel.cuh"),
-                        "sha256": "fd28dbf3cf434019c64740b88d2361f59afca9c1cf8a8b4957c5a45ade4cc97c",
+                        "sha256": "64352bebe7a4e6a4bbe5d67e3ed6cad8e1956beba898ab517d765fe1f099a408",
                         "bytes_per_pixel": (34.11e6 + 0.0) / 16384,
-                        "inst_per_pixel": 261.2e6 / 16384},
+                        "inst_per_pixel": 260.18e6 / 16384},
 }
 
 
@@ -98,15 +99,23 @@ def hbm_roofline(peaks, alg_bytes, launch_s, traffic, kernel, **extra):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s", **extra}
 
 
+# Measured on GB300 (bench.py --workload alu_peaks, profiles/alu_peaks_gb300.md): FP32 FMA instructions issue at
+# 124.5 lanes per clock per SM (3.89 warp-instructions per clock per SM, one per scheduler), packed f32x2 FMAs at
+# 127.0 operations (no gain: the FMA pipe takes two cycles per packed instruction) and ex2.approx at 31.9.
+MEASURED_WARP_ISSUE_PER_CLK_SM = 124.5 / 32
+
+
 def issue_roofline(dev, peaks, inst, launch_s, source):
     """The instruction-issue roof of a launch: `inst` warp-instructions (from its capture) over `launch_s` seconds
-    against 4 warp-instructions per clock per SM at the maximum SM clock; None without a valid capture."""
+    against the measured FFMA issue rate (3.89 warp-instructions per clock per SM) at the maximum SM clock; None
+    without a valid capture."""
     if inst is None:
         return None
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = 4.0 * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = MEASURED_WARP_ISSUE_PER_CLK_SM * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     return {"achieved": inst / launch_s, "peak": peak, "unit": "warp-instructions/s",
-            "frac": inst / launch_s / peak, "inst_per_launch": inst, "source": source}
+            "frac": inst / launch_s / peak, "inst_per_launch": inst, "source": source,
+            "peak_source": "measured FFMA issue rate (bench.py --workload alu_peaks) x SMs x max SM clock"}
 
 
 def parse():
@@ -372,10 +381,12 @@ def native(args):
     inst = capture_traffic("k_estimate", P, "inst_per_pixel")
     if inst is not None:
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        issue_peak = 4.0 * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        issue_peak = MEASURED_WARP_ISSUE_PER_CLK_SM * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         roofline["issue"] = {"achieved": inst / avg_kernel_s, "peak": issue_peak, "unit": "warp-instructions/s",
                              "frac": inst / avg_kernel_s / issue_peak, "inst_per_step": inst,
-                             "source": "ncu smsp__inst_executed.sum, mean of frames 0-3 of the nine runs"}
+                             "peak_source": "measured FFMA issue rate (bench.py --workload alu_peaks)",
+                             "source": "ncu smsp__inst_executed.sum, depth launch of frame 1 of each of the nine runs "
+                                       "(mean) plus one intensity launch"}
 
     # depth RMSE of every run's last frame (untimed pass), and the run the oracle checks below: SBR 0.1, beta 0.5
     keep_run = SBRS.index(0.1) * len(BETAS) + BETAS.index(0.5)
@@ -1261,7 +1272,7 @@ def mixed(args):
     inst = capture_traffic("k_filter_tc", P, "inst_per_pixel")
     if inst is not None:
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        issue_peak = 4.0 * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        issue_peak = MEASURED_WARP_ISSUE_PER_CLK_SM * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         roofline["issue"] = {"achieved": inst / frame_s, "peak": issue_peak, "unit": "warp-instructions/s",
                              "frac": inst / frame_s / issue_peak, "inst_per_step": inst,
                              "source": "ncu smsp__inst_executed.sum of one 256 x 256 step, scaled by the pixels"}
@@ -1523,13 +1534,18 @@ def alu_peaks(args):
                                     "ops_per_clk_sm": ops / nsm / float(cy.mean()),
                                     "cycles_spread": float(cy.max() / cy.min())})
                 best = max(res, key=lambda r: r["ops_per_s"])
-                out[f"{name}_bps{bps}"] = {"ops_per_clk_sm": round(statistics.median(r["ops_per_clk_sm"] for r in res), 2),
-                                           "ops_per_s_best": best["ops_per_s"],
-                                           "implied_mhz": best["ops_per_s"] / nsm /
-                                           statistics.median(r["ops_per_clk_sm"] for r in res) / 1e6}
+                out[f"{name}_bps{bps}"] = {"ops_per_s_best": best["ops_per_s"],
+                                           "per_block_clock64_ops_per_clk_sm":
+                                               round(statistics.median(r["ops_per_clk_sm"] for r in res), 2)}
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz") or float(_peaks().get("sm_max_mhz", 2070.0))
+    for v in out.values():  # per clock per SM at the SM clock sampled during the runs
+        v["ops_per_clk_sm"] = round(v["ops_per_s_best"] / nsm / (mhz * 1e6), 2)
     line = {"metric": "arithmetic throughput (operations per clock per SM, per second)", "workload": "alu_peaks",
-            "n_sm": nsm, "results": out, "clocks": clk.summary(), "steps": args.steps, "warmup": args.warmup,
-            "note": "an FMA counts as one operation (two flops); an f32x2 instruction as two operations"}
+            "n_sm": nsm, "results": out, "clocks": clocks, "steps": args.steps, "warmup": args.warmup,
+            "note": "an FMA counts as one operation (two flops); an f32x2 instruction as two operations; "
+                    "ops_per_clk_sm divides the event-timed rate by the sampled SM clock (the per-block clock64 "
+                    "figure counts each block's own cycles, which start and end at different times)"}
     print(json.dumps(line))
 
 
