@@ -241,40 +241,11 @@ __device__ __forceinline__ void count_and_list(const float* raw, const int* nzc,
     nnz = base;
 }
 
-// Number of listed bins below t (the list is in bin order), counted by all lanes.
-__device__ __forceinline__ int entries_below(const int* ebin, int nnz, int t, int lane) {
-    int n = 0;
-    for (int e0 = 0; e0 < nnz; e0 += 32) {
-        const int e = e0 + lane;
-        n += __popc(__ballot_sync(0xffffffffu, e < nnz && ebin[e] < t));
-    }
-    return n;
-}
-
-// C on block b of a listed row, lane = candidate 32 b + lane: the listed bins from index e (the first one not
-// below the block's window) up to the end of the window, in bin order (that is, in tap order for the candidate).
-// Writes cs (0 past D) and returns the lane's C (0 past D).
-__device__ __forceinline__ float gather_block(const float* __restrict__ gs, const int* ebin, const float* eval, int nnz,
-                                             int e, float* cs, int b, int D, int L, int u0, int lane) {
-    const int c = 32 * b + lane;
-    const int whi = u0 + 32 * b + 31 + L - 1;
-    const int j0 = u0 + c;  // bin of tap 0 for this candidate
-    float acc = 0.f;
-    for (; e < nnz; ++e) {
-        const int t = ebin[e];
-        if (t > whi) break;
-        const int j = t - j0;
-        if (static_cast<unsigned>(j) < static_cast<unsigned>(L)) acc = fmaf(eval[e], gs[j], acc);
-    }
-    if (c >= D) acc = 0.f;
-    cs[c] = acc;
-    return acc;
-}
-
 // C on candidates [c_lo, c_hi] of a listed row, lane = tap: lane l owns the taps j = l + 32 k (k < NTG) and adds
 // z_t g_j into candidate t - u0 - j for each listed bin t in turn (bins whose windows miss the range are skipped).
 // The candidates of one bin are distinct across lanes and taps and the warp synchronises between bins, so every
-// C(d) is summed in bin order, i.e. in tap order, as by the gather. The range must be zero on entry. Returns max C.
+// C(d) is summed in bin order, i.e. in tap order, as by the dense sum. The range must be zero on entry. Returns max
+// C.
 template <int NTG>
 __device__ __forceinline__ float scatter_range(const float* __restrict__ gs, const int* ebin, const float* eval,
                                                int nnz, float* cs, int c_lo, int c_hi, int u0, int L, int lane) {
@@ -304,31 +275,16 @@ __device__ __forceinline__ float scatter_range(const float* __restrict__ gs, con
     return warp_max(mx);
 }
 
-// C on blocks [b0, b1] of a listed row; returns max C there. Up to three blocks are gathered (lane = candidate,
-// blocks that no listed bin reaches are zero-filled); a wider range is zero-filled and scattered (lane = tap).
-__device__ __forceinline__ float listed_range(const float* __restrict__ gs, const int* ebin, const float* eval, int nnz,
-                                             const float* bnd, float* cs, int b0, int b1, int D, int L, int u0,
-                                             int lane) {
-    if (b1 - b0 >= 3) {
-        zero_words(cs + 32 * b0, 8 * (b1 - b0 + 1), lane);
-        const int c_lo = 32 * b0, c_hi = min(32 * b1 + 31, D - 1);
-        switch ((L + 31) >> 5) {
-            case 1: return scatter_range<1>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
-            case 2: return scatter_range<2>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
-            case 3: return scatter_range<3>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
-            default: return scatter_range<4>(gs, ebin, eval, nnz, cs, c_lo, c_hi, u0, L, lane);
-        }
+// C on every candidate of a listed row (zero-filled, then scattered lane = tap); returns max C.
+__device__ __forceinline__ float listed_all(const float* __restrict__ gs, const int* ebin, const float* eval, int nnz,
+                                           float* cs, int NB, int D, int L, int u0, int lane) {
+    zero_words(cs, NB * 8, lane);
+    switch ((L + 31) >> 5) {
+        case 1: return scatter_range<1>(gs, ebin, eval, nnz, cs, 0, D - 1, u0, L, lane);
+        case 2: return scatter_range<2>(gs, ebin, eval, nnz, cs, 0, D - 1, u0, L, lane);
+        case 3: return scatter_range<3>(gs, ebin, eval, nnz, cs, 0, D - 1, u0, L, lane);
+        default: return scatter_range<4>(gs, ebin, eval, nnz, cs, 0, D - 1, u0, L, lane);
     }
-    float mx = 0.f;
-    int e = entries_below(ebin, nnz, u0 + 32 * b0, lane);
-    for (int b = b0; b <= b1; ++b) {
-        if (bnd[b] > 0.f) mx = fmaxf(mx, gather_block(gs, ebin, eval, nnz, e, cs, b, D, L, u0, lane));
-        else cs[32 * b + lane] = 0.f;
-        const int next = u0 + 32 * (b + 1);  // entries below the next block's window are done with
-        while (e < nnz && ebin[e] < next) ++e;
-    }
-    __syncwarp();
-    return warp_max(mx);
 }
 
 // Photons of the listed bins that reach each block: entry (t, z) adds z to the blocks holding candidates
@@ -390,12 +346,12 @@ __device__ __forceinline__ float corr_dense(const float* __restrict__ gs, const 
 // out of line, so the hot loop's code stays small.
 template <int FMT>
 __device__ __noinline__ void recompute_all(const float* __restrict__ gs, const float* raw, const int* ebin,
-                                           const float* eval, int nnz, float* bnd, float* cs, bool empty, bool sparse,
-                                           int NB, int D, int L, int u0, int lane) {
+                                           const float* eval, int nnz, float* cs, bool empty, bool sparse, int NB,
+                                           int D, int L, int u0, int lane) {
     if (empty) {
         zero_words(cs, NB * 8, lane);
     } else if (sparse) {
-        listed_range(gs, ebin, eval, nnz, bnd, cs, 0, NB - 1, D, L, u0, lane);
+        listed_all(gs, ebin, eval, nnz, cs, NB, D, L, u0, lane);
     } else {
         corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
     }
@@ -498,11 +454,10 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
         } else if (sparse) {
             zero_words(bnd, (NB + 3) >> 2, lane);
             block_photons(ebin, eval, nnz, bnd, D, L, u0, lane);
-            cmax = listed_range(gs, ebin, eval, nnz, bnd, cs, 0, NB - 1, D, L, u0, lane);
+            cmax = listed_all(gs, ebin, eval, nnz, cs, NB, D, L, u0, lane);
         } else {
             cmax = corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
         }
-        auto ensure = [&](int, int) { return cmax; };
 
         if (COST_ONLY) {
             float best = -INFINITY;
@@ -561,9 +516,9 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
             lane);
         int bidx;
         float mu, var;
-        posterior_eval(grid, pr, cs, ubs, ub_b, ensure,
+        posterior_eval(grid, pr, cmax, cs, ubs, ub_b,
                        [&]() {
-                           recompute_all<FMT>(gs, raw, ebin, eval, nnz, bnd, cs, empty, sparse, NB, D, L, u0, lane);
+                           recompute_all<FMT>(gs, raw, ebin, eval, nnz, cs, empty, sparse, NB, D, L, u0, lane);
                        },
                        lane, bidx, mu, var);
         if (lane == 0) {

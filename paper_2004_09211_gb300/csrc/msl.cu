@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_estimate_msl(const MslArgs a) {
         int bidx;
         float mu, var;
         posterior_eval(
-            grid, pr, cs, ubs, ub_b, [&](int, int) { return mmax; },
+            grid, pr, mmax, cs, ubs, ub_b,
             [&]() {  // rare fallback: M again on every candidate
                 for (int c = lane; c < NB * 32; c += 32) cs[c] = 1.f;
                 __syncwarp();

@@ -1,13 +1,16 @@
-// Pseudo-posterior moments on the integer depth grid, shared by the histogram kernel (estimate.cu) and the
-// photon-list kernels (batch.cu, noalloc.cu):
+// Pseudo-posterior moments on the integer depth grid, shared by the histogram kernel (estimate.cu), the photon-list
+// kernels (batch.cu, noalloc.cu) and the multispectral kernel (msl.cu):
 //
-//   posterior       Eq. approx_post + Eq. KL_div: argmax, mean and variance of the pseudo-posterior on the
+//   block_bounds    per-block upper bounds of the log pseudo-posterior (the data part supplied by the caller).
+//   posterior_eval  Eq. approx_post + Eq. KL_div: argmax, mean and variance of the pseudo-posterior on the
 //                   integer grid, from C(d) already in shared memory, with bound-based block pruning and the
 //                   linear-domain evaluation described below.
+//   posterior       the two together, with the photon-count data bound of the photon-list kernels.
+//   corr_photons    C(d) from a photon list (the photon-sum form of Eq. beta_div2).
 //
 // Pruning. Candidates are grouped in blocks of 32. Each block gets an upper bound of ell = lambda log2(e) C(d)
-// + log2 f(d): lambda log2(e) max(g) times the photons in the block's window, plus the prior's largest value
-// on the block. The block with the largest bound is evaluated exactly; its best value LB is a lower bound of
+// + log2 f(d): an upper bound of the data part (lambda log2(e) max(g) times the photons in the block's window, or
+// the largest C of a densely correlated row), plus the prior's largest value on the block. The block with the largest bound is evaluated exactly; its best value LB is a lower bound of
 // the maximum, and every block whose bound is below LB - 64 is dropped: its weights are below 2^-64 of the
 // maximum, so the moments move by less than 8192^3 * 2^-64 < 3e-8 bins^2. The argmax always lies in a kept
 // block.
@@ -136,15 +139,13 @@ __device__ __forceinline__ int block_bounds(const Grid& g, const Prior& pr, floa
     return ub_b;
 }
 
-// The pseudo-posterior from the block bounds: cs holds C on block ub_b on entry. The best value of that block is a
-// lower bound LB of the maximum; blocks whose bound is below LB - 64 are dropped. ensure(bfirst, blast) must then
-// put C into cs on every block of the kept range [bfirst, blast] (at least on the kept ones; a dropped block may
-// read as C = 0) and return max C over that range (warp-uniform). restore() writes C back on the kept range
-// (needed only on the rare fallback from the linear path, whose weights overwrite cs). Outputs: index of the
-// smallest maximiser, mean depth and variance.
-template <class Ensure, class Restore>
-__device__ __forceinline__ void posterior_eval(const Grid& g, const Prior& pr, float* cs, const float* ubs, int ub_b,
-                                               Ensure ensure, Restore restore, int lane, int& bidx_out,
+// The pseudo-posterior from the block bounds: cs holds C on every candidate (cmax its largest value). The best
+// value of block ub_b is a lower bound LB of the maximum; blocks whose bound is below LB - 64 are dropped.
+// restore() writes C back on the kept range (needed only on the rare fallback from the linear path, whose weights
+// overwrite cs). Outputs: index of the smallest maximiser, mean depth and variance.
+template <class Restore>
+__device__ __forceinline__ void posterior_eval(const Grid& g, const Prior& pr, float cmax, float* cs, const float* ubs,
+                                               int ub_b, Restore restore, int lane, int& bidx_out,
                                                float& mu_out, float& var_out) {
     const int D = g.D, NB = g.NB;
     const float lam2 = g.lam2;
@@ -172,7 +173,6 @@ __device__ __forceinline__ void posterior_eval(const Grid& g, const Prior& pr, f
         }
     }
 
-    const float cmax = ensure(bfirst, blast);
 
     // ---- linear-domain weights over the range of kept blocks ----
     if ((blast - bfirst + 1) <= max(8, 2 * nsurv) && !(pr.minv < 1.5f)) {
@@ -180,7 +180,7 @@ __device__ __forceinline__ void posterior_eval(const Grid& g, const Prior& pr, f
 #pragma unroll
         for (int i = 0; i < kMaxComp; ++i)
             if (i < pr.n) sref = fmaxf(sref, pr.ca[i]);
-        const float xref = lam2 * cmax;  // lambda log2(e) max C over the kept range
+        const float xref = lam2 * cmax;  // lambda log2(e) max_d C(d)
         const int c_lo = 32 * bfirst, c_hi = min(32 * blast + 31, D - 1);
         const int run = (c_hi - c_lo + 32) >> 5;
         const int r0 = c_lo + lane * run, r1 = min(r0 + run, c_hi + 1);
@@ -288,7 +288,7 @@ __device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float 
             return g.lam2 * g.gmax * nb * 1.0001f;
         },
         lane);
-    posterior_eval(g, pr, cs, ubs, ub_b, [&](int, int) { return cmax; }, restore, lane, bidx_out, mu_out, var_out);
+    posterior_eval(g, pr, cmax, cs, ubs, ub_b, restore, lane, bidx_out, mu_out, var_out);
 }
 
 }  // namespace px
