@@ -54,9 +54,9 @@ TRAFFIC_CAPTURES = {
     # launch each, mean) plus one intensity launch (ncu dram__bytes_read.sum + dram__bytes_write.sum and
     # smsp__inst_executed.sum)
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "posterior.cuh", "intensity.cu"),
-                   "sha256": "22025118640148994099e30833995a84a537b0d6b300dea1a057c752c571b224",
-                   "bytes_per_pixel": (197.76e6 + 3.45e6 + 15.60e6) / 65536,
-                   "inst_per_pixel": (369.11e6 + 25.01e6) / 65536},
+                   "sha256": "e3a111e7d297c262dfea2694c6580cfd80c40f6be6ade02ab860ee87845029ce",
+                   "bytes_per_pixel": (197.75e6 + 3.49e6 + 15.60e6) / 65536,
+                   "inst_per_pixel": (368.24e6 + 25.01e6) / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh"),
                     "sha256": "4b91b965a951a7a579e6b8795932c4705fd37b0ae2963e43304adc5e2c2fd601",
                     "bytes_per_pixel": (537.63e6 + 3.65e6 + 17.20e6) / 65536,
@@ -65,8 +65,8 @@ TRAFFIC_CAPTURES = {
                     "inst_per_pixel": (343.85e6 + 17.01e6) / 65536},
     # one launch of the photon-list kernel over all 64 sequences of the batched workload (7 050 240 pixels)
     "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh"),
-                "sha256": "585ff8de6b0e1a71af734418f99a1c28ee91fca076e604241645070f396834e2",
-                "bytes_per_pixel": (457.30e6 + 124.85e6) / 7050240,
+                "sha256": "e014f5ee9513edfa67181adc990848f68d18e585f22b7c4255979bfc41bbf4e5",
+                "bytes_per_pixel": (459.59e6 + 124.96e6) / 7050240,
                 "inst_per_pixel": 32877.47e6 / 7050240},
     # backward launches of the differentiable filter (128 x 128 frames, T = 1024): mean of three of the 20 launches
     # of one reverse sweep (they differ by 0.04 %)

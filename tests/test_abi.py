@@ -192,3 +192,39 @@ def test_detect_argument_checks():
     st = lib.spl_filter_step_detect(ct.byref(bad), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
                                     0x6000, 0xa000, 0x9000, None, 0x7000, 0x8000, None)
     assert st == _abi.SPL_EINVAL
+
+
+def test_multispectral_argument_checks():
+    """spl_depth_estimate_msl: nbands in 1..SPL_MAX_BANDS, mu and var required, prior both or neither, the single-band
+    parameter and layout checks; all decided on the host."""
+    lib = _abi.load()
+    prm = make_params(4, 4, 64, 25, 12)
+    hz = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 64)
+    #                    prm, nbands, z, h, prior_mu, prior_var, argmax, mu, var, cost, stream
+    for nb in (0, _abi.SPL_MAX_BANDS + 1):
+        st = lib.spl_depth_estimate_msl(ct.byref(prm), nb, ct.byref(hz), 0x2000, None, None, None, 0x3000, 0x4000,
+                                        None, None)
+        assert st == _abi.SPL_EINVAL and "nbands" in lib.spl_last_error().decode()
+    st = lib.spl_depth_estimate_msl(ct.byref(prm), 2, ct.byref(hz), 0x2000, None, None, None, None, 0x4000, None, None)
+    assert st == _abi.SPL_EINVAL and "mu and var" in lib.spl_last_error().decode()
+    st = lib.spl_depth_estimate_msl(ct.byref(prm), 2, ct.byref(hz), 0x2000, 0x5000, None, None, 0x3000, 0x4000, None,
+                                    None)
+    assert st == _abi.SPL_EINVAL and "prior_mu and prior_var" in lib.spl_last_error().decode()
+    st = lib.spl_depth_estimate_msl(ct.byref(prm), 2, ct.byref(hz), None, None, None, None, 0x3000, 0x4000, None, None)
+    assert st == _abi.SPL_EINVAL and "h is NULL" in lib.spl_last_error().decode()
+    bad = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 68)  # 136-byte rows
+    st = lib.spl_depth_estimate_msl(ct.byref(prm), 2, ct.byref(bad), 0x2000, None, None, None, 0x3000, 0x4000, None,
+                                    None)
+    assert st == _abi.SPL_EINVAL and "16 bytes" in lib.spl_last_error().decode()
+    out = make_params(4, 4, 64, 25, 12, dmin=5)
+    st = lib.spl_depth_estimate_msl(ct.byref(out), 2, ct.byref(hz), 0x2000, None, None, None, 0x3000, 0x4000, None,
+                                    None)
+    assert st == _abi.SPL_EINVAL and "full-support" in lib.spl_last_error().decode()
+
+
+def test_throughput_probe_size_query():
+    """spl_probe_throughput answers its size query on the host (no launch without buffers) and rejects bad kinds."""
+    lib = _abi.load()
+    nb, opt = ct.c_int(0), ct.c_longlong(0)
+    assert lib.spl_probe_throughput(7, 4, 16, None, None, ct.byref(nb), ct.byref(opt), None) == _abi.SPL_EINVAL
+    assert lib.spl_probe_throughput(0, 0, 16, None, None, ct.byref(nb), ct.byref(opt), None) == _abi.SPL_EINVAL

@@ -119,3 +119,28 @@ def test_noalloc_rejects_more_sequences_than_its_fixed_scratch():
     st = lib.spl_batch_step_noalloc(host, 0x1000, n, 32, None, None)
     assert st == _abi.SPL_EINVAL
     assert "capacity" in lib.spl_last_error().decode()
+
+
+def test_noalloc_refuses_a_device_descriptor_wider_than_its_host_copy():
+    """The host copy of the descriptors sizes the kernel's shared-memory slices and the kernel reads the device copy:
+    a device descriptor with more candidates than any host descriptor is refused on the device (its outputs set to
+    NaN, SPL_BATCH_DESC_MISMATCH raised) instead of overrunning the slice; the other sequences are unaffected."""
+    lib = _abi.load()
+    seqs = _sequences()
+    mine = [_buffers(q) for q in seqs]
+    frames = [_frame(q, *mine[i], 0) for i, q in enumerate(seqs)]
+    host, dev = _desc_arrays(seqs, frames)
+    Ds = [q["prm"].dmax - q["prm"].dmin + 1 for q in seqs]
+    w = int(np.argmax(Ds))  # the widest sequence: its host copy is made to claim 41 candidates
+    host[w].prm.dmax = host[w].prm.dmin + 40
+    assert Ds[w] > max([41] + [d for i, d in enumerate(Ds) if i != w])
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    st = lib.spl_batch_step_noalloc(host, dev.data_ptr(), len(seqs), 32, status.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert st == _abi.SPL_OK, lib.spl_last_error()
+    torch.cuda.synchronize()
+    assert int(status.item()) & _abi.SPL_BATCH_DESC_MISMATCH
+    assert torch.isnan(mine[w][0]["mu"][1]).all()
+    for i in range(len(seqs)):
+        if i != w:
+            assert torch.isfinite(mine[i][0]["mu"][1]).all()
