@@ -8,7 +8,8 @@ each sequence filtered with beta = 0.2, 0.5 and 1.0 (9 runs), uint16 histograms.
 9 runs x 50 frames of spl_filter_step (prior from the previous frame, pseudo-posterior, moments,
 background/reflectivity) = 29.5 M pixel-frames. Histograms are generated on the device before timing and
 stay resident (29.6 GB; every frame is 197 MB, larger than the 129 MB L2, so no flush is needed between
-iterations).
+iterations). spl_filter_step takes uint16 frames through the tensor cores (counts converted to FP16 on chip,
+exact below 1024); the same job is also timed through spl_filter_step_fp32, the FP32 CUDA-core kernel.
 
 Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead, on a bounded sample of
 the same workload, on the host cores.
@@ -79,9 +80,11 @@ TRAFFIC_CAPTURES = {
 
 def capture_traffic(kernel: str, pixels: int, key: str = "bytes_per_pixel"):
     """Traffic (or, key="inst_per_pixel", warp-instructions) per launch of `kernel` over `pixels` pixels from its
-    capture, or None if the sources changed since."""
+    capture, or None if it has none or the sources changed since."""
     import hashlib
-    cap = TRAFFIC_CAPTURES[kernel]
+    cap = TRAFFIC_CAPTURES.get(kernel)
+    if cap is None:
+        return None
     h = hashlib.sha256()
     for f in cap["sources"]:
         with open(os.path.join(ROOT, "paper_2004_09211_gb300", "csrc", f), "rb") as fh:
@@ -357,40 +360,42 @@ def native(args):
     ms = start.elapsed_time(stop)
     ms, value = replica_throughput(ms, units, args.steps, world, dev if dist else None)
 
-    # roofline of the dominant kernel (the fused filter step): algorithmic bytes per pixel-frame =
-    # histogram row (2 T) + previous state (mu, var) + outputs (mu, var, argmax, refl, bg). The steps of
-    # different runs overlap on the streams, so the time per step is the job's time over its steps.
+    # the same job on the FP32 CUDA-core kernel (spl_filter_step_fp32), the plain path the route is measured against
+    for _ in range(args.warmup):
+        run_job(spl, prms, hd, videos, states, outs, stream, lanes=lanes, step=spl.spl_filter_step_fp32)
+    barrier()
+    start.record(stream)
+    for _ in range(args.steps):
+        run_job(spl, prms, hd, videos, states, outs, stream, lanes=lanes, step=spl.spl_filter_step_fp32)
+    stop.record(stream)
+    barrier()
+    ms32, value32 = replica_throughput(start.elapsed_time(stop), units, args.steps, world, dev if dist else None)
+
+    # rooflines of one filter step (time per step = job time / steps: the runs' steps overlap on the streams).
+    # Algorithmic bytes per pixel-frame: histogram row (2 T) + previous state (mu, var) + outputs (mu, var,
+    # argmax, refl, bg).
     alg_bytes = P * (2 * T + 8 + 20)
     n_steps = len(SBRS) * len(BETAS) * frames * args.steps
-    avg_kernel_s = ms / n_steps / 1e3
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = alg_bytes / avg_kernel_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": capture_traffic("k_estimate", P),
-                "kernel": "k_estimate<u16> + k_intensity4 (one spl_filter_step; time per step = job time / steps, "
-                          f"the runs' steps overlapping on {JOB_STREAMS} streams)",
-                "alg_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": avg_kernel_s * 1e3,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
-    # the binding limit: instruction issue (4 warp-instructions per clock per SM), from the captured count
-    inst = capture_traffic("k_estimate", P, "inst_per_pixel")
-    if inst is not None:
-        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        issue_peak = MEASURED_WARP_ISSUE_PER_CLK_SM * nsm * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        roofline["issue"] = {"achieved": inst / avg_kernel_s, "peak": issue_peak, "unit": "warp-instructions/s",
-                             "frac": inst / avg_kernel_s / issue_peak, "inst_per_step": inst,
-                             "peak_source": "measured FFMA issue rate (bench.py --workload alu_peaks)",
-                             "source": "ncu smsp__inst_executed.sum, depth launch of frame 1 of each of the nine runs "
-                                       "(mean) plus one intensity launch"}
+    peaks = _peaks()
+    step_s, step32_s = ms / n_steps / 1e3, ms32 / n_steps / 1e3
+    roofline = hbm_roofline(
+        peaks, alg_bytes, step_s, capture_traffic("k_filter_tc_u16", P),
+        "k_filter_tc<u16> + k_estimate_redo + k_intensity4 (one spl_filter_step; time per step = job time / steps, "
+        f"the runs' steps overlapping on {JOB_STREAMS} streams)")
+    roofline["issue"] = issue_roofline(dev, peaks, capture_traffic("k_filter_tc_u16", P, "inst_per_pixel"), step_s,
+                                       "ncu smsp__inst_executed.sum of the three launches of one filter step, frame 1 "
+                                       "of each of the nine runs (mean)")
+    roofline32 = hbm_roofline(
+        peaks, alg_bytes, step32_s, capture_traffic("k_estimate", P),
+        "k_estimate<u16> + k_intensity4 (one spl_filter_step_fp32; time per step = job time / steps)")
+    roofline32["issue"] = issue_roofline(dev, peaks, capture_traffic("k_estimate", P, "inst_per_pixel"), step32_s,
+                                         "ncu smsp__inst_executed.sum, depth launch of frame 1 of each of the nine "
+                                         "runs (mean) plus one intensity launch")
 
     # depth RMSE of every run's last frame (untimed pass), and the run the oracle checks below: SBR 0.1, beta 0.5
     keep_run = SBRS.index(0.1) * len(BETAS) + BETAS.index(0.5)
     rmse, kept = job_rmse(spl, prms, hd, videos, sc, frames, dev, keep=(keep_run, CROP_FRAMES - 1))
+    rmse32, _ = job_rmse(spl, prms, hd, videos, sc, frames, dev, step=spl.spl_filter_step_fp32)
 
     e2e = None
     if not args.no_e2e:
@@ -418,12 +423,17 @@ def native(args):
         line = {
             "metric": "pixel-frames/s", "value": value, "unit": "pixel-frames/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16 counts -> f16 on chip (exact below 1024) x f16 hi/lo taps -> f32 (tensor); f32 epilogue",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "pixels": P, "frames": frames, "T": T, "L": L,
                        "sequences": len(SBRS), "betas": list(BETAS), "hist": "uint16",
                        "pixel_frames_per_step": units, "l2": "inputs larger than L2 (197 MB per frame), no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "fp32_path": {"value": value32, "ms_per_step": ms32 / args.steps, "dtype": "f32",
+                          "entry": "spl_filter_step_fp32", "roofline": roofline32,
+                          "depth_rmse_last_frame": rmse32},
             "cpu_baseline": cpu, "depth_rmse_last_frame": rmse,
         }
         print(json.dumps(line), flush=True)
@@ -695,7 +705,7 @@ def batched(args):
 
     # depth RMSE of the batched step at the last frame (the graph replays left every sequence's last state), and
     # the same sequences through the plain FP32 histogram path: histograms built from the same photon lists
-    # (outside the timed region), one spl_filter_step per sequence and frame, timed frame by frame
+    # (outside the timed region), one spl_filter_step_fp32 per sequence and frame, timed frame by frame
     def pooled(parts):
         out = {}
         for k in ("all", "static", "objects", "uncovered"):
@@ -734,8 +744,9 @@ def batched(args):
         torch.cuda.synchronize(dev)
         e0.record()
         for i, q in enumerate(seqs):
-            spl.spl_filter_step(q["prm"], hists[i], q["h"], plain_mu[i][n & 1], plain_var[i][n & 1],
-                                out=dict(mu=plain_mu[i][(n + 1) & 1], var=plain_var[i][(n + 1) & 1], **q["outs"]))
+            spl.spl_filter_step_fp32(q["prm"], hists[i], q["h"], plain_mu[i][n & 1], plain_var[i][n & 1],
+                                     out=dict(mu=plain_mu[i][(n + 1) & 1], var=plain_var[i][(n + 1) & 1],
+                                              **q["outs"]))
         e1.record()
         torch.cuda.synchronize(dev)
         ms_plain += e0.elapsed_time(e1)
@@ -748,7 +759,7 @@ def batched(args):
     plain = {"value": units / (ms_plain / 1e3), "ms_per_step": ms_plain,
              "histogram_bytes_per_frame": hist_bytes, "depth_rmse_last_frame": rmse_plain,
              "max_rel_mu_vs_batched": rel,
-             "note": "the same 64 sequences and photons as uint16 histograms through spl_filter_step (one launch "
+             "note": "the same 64 sequences and photons as uint16 histograms through spl_filter_step_fp32 (one launch "
                      "pair per sequence and frame, 640 per step), histograms built outside the timed region"}
     # roofline of k_batch: algorithmic bytes per launch (one frame of every sequence) = 4 B per photon (bin
     # index) + 32 B per pixel (list offset, previous state, new state, argmax, refl, bg); its average launch time
@@ -853,7 +864,7 @@ def diff(args):
 
 def video_tc(args):
     """The video job (the headline workload) through spl_filter_step_tc on FP16 copies of its uint16 frames (the
-    counts are small integers, exact in FP16), timed like the headline, beside spl_filter_step on the original
+    counts are small integers, exact in FP16), timed like the headline, beside spl_filter_step_fp32 on the original
     frames. Also reported: the depth RMSE of both paths against the ground truth at every run's last frame."""
     import paper_2004_09211_gb300 as spl
     torch.cuda.set_device(0)
@@ -886,7 +897,7 @@ def video_tc(args):
     with ClockSampler(0) as clk:
         ms_tc, rmse_tc = timed(spl.spl_filter_step_tc, videos16)
     flags = spl.spl_tc_status()
-    ms_32, rmse_32 = timed(spl.spl_filter_step, videos)
+    ms_32, rmse_32 = timed(spl.spl_filter_step_fp32, videos)
     runs = [f"SBR {sb} beta {b}" for sb in SBRS for b in BETAS]
     # roofline of one filter step (tensor-core depth launch + intensity launch): FP16 row (2 T) + previous state
     # (8 B) + outputs (20 B) per pixel; time per step = job time / steps (no capture of this workload)
@@ -913,7 +924,7 @@ def detect(args):
     """The video job with the presence decision of Algorithm 1 on the device: per frame spl_filter_step_detect
     (depth, moments and the detection surrogate with the intensity rule) and spl_pi_propagate (Eq. prior_detect
     for the next frame), the decision feeding the next frame's present_in. Timed like the headline, beside the
-    plain spl_filter_step job. Every pixel of this scene has a surface, so the fraction declared present at each
+    plain spl_filter_step_fp32 job. Every pixel of this scene has a surface, so the fraction declared present at each
     run's last frame is the detection rate; the false-alarm rate is measured on one background-only frame per
     SBR (same background level, pi0 = 0.5)."""
     import paper_2004_09211_gb300 as spl
@@ -982,7 +993,7 @@ def detect(args):
             mu, var = states[vi][bi]
             o = spl.spl_filter_step_detect(prm, zbg, hd, mu[frames & 1], var[frames & 1], stream=stream)
             p_fa[f"SBR {sbr} beta {BETAS[bi]}"] = float(o["present"].float().mean())
-    ms_plain = timed(lambda: run_job(spl, prms, hd, videos, states, outs, stream))
+    ms_plain = timed(lambda: run_job(spl, prms, hd, videos, states, outs, stream, step=spl.spl_filter_step_fp32))
     # roofline of one detect step (depth launch + detecting intensity launch + pi propagation): uint16 row (2 T) +
     # previous state (8 B) + present_in (1 B) + pi0 (4 B) + outputs mu, var, argmax, refl, bg, pi, present (25 B)
     # + the propagation's pi read and pi0 write (8 B) per pixel; time per step = job time / steps
@@ -1165,7 +1176,7 @@ def mixed(args):
     pixel-frame), beta = 0.5, FP16 counts (exact up to 2048). One step = the 20 frames through
     spl_filter_step_tc. Every frame is generated on the device (seeded per frame) before its filter step; CUDA
     events bracket each step and the step time is their sum, so generation is outside the timed region (each
-    frame is 8.6 GB, far larger than L2). Also measured: spl_filter_step (FP32 CUDA cores) on the same FP16
+    frame is 8.6 GB, far larger than L2). Also measured: spl_filter_step_fp32 (FP32 CUDA cores) on the same FP16
     frames, the depth RMSE of both against the ground truth, the tensor-core data term against an FP64
     evaluation of its definition on a crop, and (CPU baseline leg) the FP64 oracle on crops with the
     tensor-core filter's depths compared to it."""
@@ -1225,7 +1236,7 @@ def mixed(args):
     ms = statistics.mean(r[0] for r in runs)
     rmse_tc = runs[-1][1]
     flags = spl.spl_tc_status()
-    ms_fp32, rmse_fp32 = run(spl.spl_filter_step)
+    ms_fp32, rmse_fp32 = run(spl.spl_filter_step_fp32)
 
     # data term against an FP64 evaluation of its definition (C(d) = sum_j h_j^beta z[d - peak + j]) on a crop
     gen_frame(0)
@@ -1289,7 +1300,7 @@ def mixed(args):
                                 "tc_last_frame": rmse_tc[-1], "fp32_last_frame": rmse_fp32[-1],
                                 "equal": abs(rt - rf) <= max(0.01, 0.01 * rf),
                                 "last_frame_split": {"tc": split[spl.spl_filter_step_tc],
-                                                     "fp32": split[spl.spl_filter_step]}},
+                                                     "fp32": split[spl.spl_filter_step_fp32]}},
             "cost_error_vs_fp64": cost_error, "status_flags": flags, "roofline": roofline,
             "gpu_launches": 2 * N * args.steps, "clocks": clk.summary(), "cpu_baseline": cpu, "e2e": None}
     print(json.dumps(line), flush=True)

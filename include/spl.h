@@ -183,11 +183,29 @@ SPL_API spl_status spl_depth_estimate_msl(const spl_params* prm, int nbands, con
  *   as in spl_depth_estimate. present_in, faulty, present_now may be NULL (all present / none faulty).
  *   argmax, refl, bg are nullable (refl and bg both or neither). Faulty pixels get refl = bg = 0.
  *   mu_out/var_out must not alias mu_in/var_in (neighbours read the previous frame); use two buffers.
+ *   Arithmetic. With uint16 histograms (SPL_HIST_U16) the data term C(d) is formed on the tensor cores as in
+ *   spl_filter_step_tc: each landed tile of counts is converted to FP16 on chip (exact: counts below 1024),
+ *   the taps h^beta are split into high and low FP16 parts (about 22 significant bits) and the products are
+ *   accumulated in FP32; the rest is FP32. A 128-pixel block holding a count of 1024 or more is computed
+ *   instead by the FP32 kernel of spl_filter_step_fp32, in a second launch that reads the same inputs. A
+ *   bounded internal wait of the tensor-core kernel that runs out sets flag 1 of spl_tc_status (the outputs
+ *   are then incomplete). FP16 and FP32 histograms go through the FP32 kernel. The results meet the same
+ *   tolerances against the FP64 definition either way (1e-4 relative on mu, var, refl, bg).
  */
 SPL_API spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
                            const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
                            const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
                            float* refl, float* bg, void* stream);
+
+/*
+ * spl_filter_step_fp32 -- spl_filter_step with every format on the FP32 CUDA-core kernel (the data term as FP32
+ *   products and sums, warp per pixel): the plain path that the tensor-core route of uint16 histograms is
+ *   measured against. Same arguments, outputs and rules as spl_filter_step.
+ */
+SPL_API spl_status spl_filter_step_fp32(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                                        const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                                        const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
+                                        float* refl, float* bg, void* stream);
 
 /*
  * spl_filter_step_detect -- spl_filter_step with the presence decision of Algorithm 1 made on the device

@@ -18,7 +18,7 @@ from ._abi import (SPL_BATCH_BAD_BIN, SPL_BATCH_TOO_MANY, SPL_HIST_F16, SPL_HIST
                    SPL_MAX_BINS, SPL_MAX_PHOTONS, SPL_MAX_TAPS, SplError, spl_hist, spl_params, spl_seq_frame)
 
 __all__ = ["make_params", "spl_version", "spl_last_error", "spl_depth_cost", "spl_depth_estimate", "spl_depth_estimate_fine",
-           "spl_filter_step", "spl_filter_step_detect", "spl_filter_step_tc", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
+           "spl_filter_step", "spl_filter_step_fp32", "spl_filter_step_detect", "spl_filter_step_tc", "spl_state_init", "spl_pi_propagate", "spl_batch_create", "spl_batch_destroy",
            "spl_batch_set", "spl_batch_step", "spl_batch_tune", "spl_batch_info", "spl_batch_status",
            "spl_diff_scratch_size", "spl_diff_forward", "spl_diff_backward", "FilterLoss", "spl_depth_cost_tc",
            "spl_tc_status", "SplError",
@@ -284,6 +284,14 @@ def spl_filter_step_detect(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu
         _dev(o["refl"], "refl", torch.float32, P), _dev(o["bg"], "bg", torch.float32, P),
         _stream(stream)))
     return o
+
+
+def spl_filter_step_fp32(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor,
+                         var_in: torch.Tensor, present_in=None, faulty=None, present_now=None, intensity: bool = True,
+                         out: dict | None = None, stream=None) -> dict:
+    """spl_filter_step on the FP32 CUDA-core kernel for every histogram format (the plain path)."""
+    return spl_filter_step(prm, z, h, mu_in, var_in, present_in, faulty, present_now, intensity, out, stream,
+                           _entry="spl_filter_step_fp32")
 
 
 def spl_filter_step_tc(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor, var_in: torch.Tensor,

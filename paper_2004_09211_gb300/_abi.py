@@ -66,6 +66,7 @@ SIGNATURES = {
     "spl_filter_step_detect": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                           _vp, _vp]),
     "spl_filter_step_tc": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "spl_filter_step_fp32": (ct.c_int, [_P, _Hh, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "spl_state_init": (ct.c_int, [_P, _vp, _vp, _vp]),
     "spl_pi_propagate": (ct.c_int, [_P, _vp, _vp, _vp, _vp]),
     "spl_batch_create": (ct.c_int, [_P, ct.c_int, ct.c_int, ct.POINTER(ct.c_void_p)]),

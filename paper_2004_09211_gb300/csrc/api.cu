@@ -114,6 +114,50 @@ EstimateArgs base_args(const spl_params* q, const spl_hist* z, const float* h) {
 }  // namespace
 }  // namespace spl
 
+namespace spl {
+namespace {
+
+// The filter step of spl_filter_step / spl_filter_step_fp32: uint16 histograms on the tensor cores when tc is set
+// (falling back to the FP32 kernel only for a shape the tensor-core kernel cannot hold), else the FP32 kernel.
+spl_status filter_step(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                       const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                       const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax, float* refl,
+                       float* bg, void* stream, bool tc) {
+    g_err[0] = 0;
+    spl_status st = check_params(prm, true);
+    if (st != SPL_OK) return st;
+    if ((st = check_hist(prm, z)) != SPL_OK) return st;
+    SPL_REQUIRE(h != nullptr, "h is NULL");
+    SPL_REQUIRE(mu_in && var_in && mu_out && var_out, "mu_in, var_in, mu_out and var_out are required");
+    SPL_REQUIRE(mu_out != mu_in && var_out != var_in && mu_out != var_in && var_out != mu_in,
+                "outputs must not alias the previous-frame state");
+    SPL_REQUIRE((refl == nullptr) == (bg == nullptr), "give both refl and bg or neither");
+    EstimateArgs a = base_args(prm, z, h);
+    a.prior_mode = PRIOR_STENCIL;
+    a.pmu = mu_in;
+    a.pvar = var_in;
+    a.present_in = present_in;
+    a.faulty = faulty;
+    a.present_now = present_now;
+    a.argmax = argmax;
+    a.mu = mu_out;
+    a.var = var_out;
+    a.refl = refl;
+    a.bg = bg;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tc && z->fmt == SPL_HIST_U16) {
+        unsigned* status = tc_status_ptr();
+        SPL_REQUIRE(status != nullptr, "no device status word (no CUDA device?)");
+        const cudaError_t e = launch_filter_tc(a, status, s);
+        if (e != cudaErrorInvalidConfiguration) return cuda_status(e, "spl_filter_step launch");
+        cudaGetLastError();  // nothing was launched: clear the configuration error, take the FP32 kernel
+    }
+    return cuda_status(launch_estimate(a, false, s), "spl_filter_step launch");
+}
+
+}  // namespace
+}  // namespace spl
+
 using namespace spl;
 
 extern "C" {
@@ -251,28 +295,16 @@ spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float
                            const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
                            const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
                            float* refl, float* bg, void* stream) {
-    g_err[0] = 0;
-    spl_status st = check_params(prm, true);
-    if (st != SPL_OK) return st;
-    if ((st = check_hist(prm, z)) != SPL_OK) return st;
-    SPL_REQUIRE(h != nullptr, "h is NULL");
-    SPL_REQUIRE(mu_in && var_in && mu_out && var_out, "mu_in, var_in, mu_out and var_out are required");
-    SPL_REQUIRE(mu_out != mu_in && var_out != var_in && mu_out != var_in && var_out != mu_in,
-                "outputs must not alias the previous-frame state");
-    SPL_REQUIRE((refl == nullptr) == (bg == nullptr), "give both refl and bg or neither");
-    EstimateArgs a = base_args(prm, z, h);
-    a.prior_mode = PRIOR_STENCIL;
-    a.pmu = mu_in;
-    a.pvar = var_in;
-    a.present_in = present_in;
-    a.faulty = faulty;
-    a.present_now = present_now;
-    a.argmax = argmax;
-    a.mu = mu_out;
-    a.var = var_out;
-    a.refl = refl;
-    a.bg = bg;
-    return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_filter_step launch");
+    return filter_step(prm, z, h, mu_in, var_in, present_in, faulty, present_now, mu_out, var_out, argmax, refl, bg,
+                       stream, true);
+}
+
+spl_status spl_filter_step_fp32(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
+                                const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
+                                const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
+                                float* refl, float* bg, void* stream) {
+    return filter_step(prm, z, h, mu_in, var_in, present_in, faulty, present_now, mu_out, var_out, argmax, refl, bg,
+                       stream, false);
 }
 
 spl_status spl_filter_step_detect(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,

@@ -535,6 +535,123 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
     cp_async_wait_all();  // no copy may still target this CTA's shared memory when it exits
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// Pixels set aside by the tensor-core filter step on uint16 histograms
+// ------------------------------------------------------------------------------------------------------------
+
+// The tensor-core kernel converts uint16 counts to FP16 exactly only below 1024; a 128-pixel block holding a
+// larger count gets mu = NaN instead of its results. This kernel computes those pixels again with the steps of
+// k_estimate (without its prefetching: the case is rare), one warp per pixel. A warp tests the mu of 32
+// consecutive pixels at once and takes the marked ones in turn, so a frame with none costs one load per pixel.
+__global__ void __launch_bounds__(256) k_estimate_redo(const EstimateArgs a) {
+    constexpr int FMT = SPL_HIST_U16, CB = 8;
+    extern __shared__ __align__(16) float dyn[];
+    __shared__ __align__(16) float gs[SPL_MAX_TAPS + 4];
+    __shared__ float s_gmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int j = threadIdx.x; j < SPL_MAX_TAPS + 4; j += blockDim.x) {
+        const float hj = j < a.L ? a.h[j] : 0.f;
+        gs[j] = hj > 0.f ? powf(hj, a.beta) : 0.f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float g = 0.f;
+        for (int j = lane; j < a.L; j += 32) g = fmaxf(g, gs[j]);
+        g = warp_max(g);
+        if (lane == 0) s_gmax = g;
+    }
+    __syncthreads();
+    const float gmax = s_gmax;
+    const int T = a.T, L = a.L, D = a.D, u0 = a.dmin - a.peak, NB = (D + 31) >> 5;
+    const Slice sl = make_slice(T, D, CB);
+    float* base = dyn + static_cast<size_t>(warp) * sl.words;
+    int* ebin = reinterpret_cast<int*>(base + sl.ebin);
+    float* eval = base + sl.eval;
+    float* bnd = base + sl.bnd;
+    float* ubs = base + sl.ubs;
+    float* cs = base + sl.cs;
+    float* raw = base + sl.raw;
+    if (lane < 4) reinterpret_cast<float4*>(raw + sl.nch * 4)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long P = static_cast<long long>(a.H) * a.W;
+    for (long long g0 = (static_cast<long long>(blockIdx.x) * nwarps + warp) * 32; g0 < P;
+         g0 += static_cast<long long>(gridDim.x) * nwarps * 32) {
+        unsigned marked = __ballot_sync(0xffffffffu, g0 + lane < P && isnan(a.mu[g0 + lane]));
+        while (marked) {
+            const long long p = g0 + __ffs(marked) - 1;
+            marked &= marked - 1;
+            const int py = static_cast<int>(p / a.W), px = static_cast<int>(p - static_cast<long long>(py) * a.W);
+            request_row(a, p, raw, sl.nch, 2, lane);
+            cp_async_commit();
+            const Nbr nb = request_nbr(a, p, py, px, P, lane);
+            cp_async_wait_all();
+            __syncwarp();
+            for (int t = T + lane; t < sl.nch * CB; t += 32) reinterpret_cast<unsigned short*>(raw)[t] = 0;
+            __syncwarp();
+            const bool faulty = __shfl_sync(0xffffffffu, nb.faulty, 0) != 0;
+            float K = 0.f;
+            int nnz = 0;
+            if (!faulty) {
+                const int M = nonempty_chunks(raw, sl.nch, reinterpret_cast<int*>(cs), lane);
+                count_and_list<FMT, CB>(raw, reinterpret_cast<const int*>(cs), M, T, ebin, eval, lane, K, nnz);
+            }
+            const bool empty = faulty || nnz == 0;
+            const bool sparse = nnz <= kTapNnz;
+            float cmax = 0.f;
+            if (empty) {
+                zero_words(cs, NB * 8, lane);
+            } else if (sparse) {
+                zero_words(bnd, (NB + 3) >> 2, lane);
+                block_photons(ebin, eval, nnz, bnd, D, L, u0, lane);
+                cmax = listed_all(gs, ebin, eval, nnz, cs, NB, D, L, u0, lane);
+            } else {
+                cmax = corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
+            }
+            Prior pr;
+            {
+                float w = 0.f, m = 0.f, v = 1.f;
+                if (lane < 9) {  // the filter step's prior (Eq. predict)
+                    w = a.nu[lane];
+                    m = nb.info ? nb.m : a.flat_m;
+                    v = (nb.info ? nb.v : a.flat_v) + a.sigma_rw2;
+                }
+                build_prior(w, m, v, lane, pr);
+            }
+            Grid grid;
+            grid.D = D;
+            grid.NB = NB;
+            grid.dmin = a.dmin;
+            grid.u0 = u0;
+            grid.L = L;
+            grid.lam2 = a.lam2;
+            grid.gmax = gmax;
+            const float lam2 = a.lam2;
+            const int ub_b = block_bounds(
+                grid, pr, ubs,
+                [&](int b) {
+                    if (empty) return 0.f;
+                    if (sparse) return lam2 * gmax * bnd[b] * 1.0001f;
+                    return lam2 * cmax * 1.0001f;
+                },
+                lane);
+            int bidx;
+            float mu, var;
+            posterior_eval(grid, pr, cmax, cs, ubs, ub_b,
+                                  [&]() {
+                                      recompute_all<FMT>(gs, raw, ebin, eval, nnz, cs, empty, sparse, NB, D, L, u0,
+                                                         lane);
+                                  },
+                                  lane, bidx, mu, var);
+            if (lane == 0) {
+                a.mu[p] = mu;
+                a.var[p] = var;
+                if (a.argmax) a.argmax[p] = a.dmin + bidx;
+                if (a.refl) a.bg[p] = K;
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // Bytes of dynamic shared memory one warp needs.
 size_t warp_bytes(const EstimateArgs& a) {
     const int cb = a.fmt == SPL_HIST_F32 ? 4 : 8;
@@ -583,6 +700,36 @@ cudaError_t launch_t(const EstimateArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// The pixels the tensor-core filter step set aside (uint16 input): a persistent grid of up to 8 warps per CTA and
+// resident CTAs on every SM, each warp testing 32 pixels at a time.
+cudaError_t launch_estimate_redo(const EstimateArgs& a, cudaStream_t s) {
+    const size_t per_warp = warp_bytes(a);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::atomic<int> configured[64];
+    if (dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute(k_estimate_redo, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured[dev].store(1, std::memory_order_release);
+    }
+    int nsm = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int wpc = static_cast<int>((220 * 1024) / per_warp);
+    if (wpc > 8) wpc = 8;
+    if (wpc < 1) return cudaErrorInvalidConfiguration;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate_redo, wpc * 32, per_warp * wpc);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long P = static_cast<long long>(a.H) * a.W;
+    long long ctas = (P + 32LL * wpc - 1) / (32LL * wpc);
+    const long long cap = static_cast<long long>(nsm) * per_sm;
+    if (ctas > cap) ctas = cap;
+    k_estimate_redo<<<static_cast<unsigned>(ctas), wpc * 32, per_warp * wpc, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_estimate(const EstimateArgs& a, bool cost_only, cudaStream_t s) {
     cudaError_t e;

@@ -94,8 +94,12 @@ cudaError_t launch_cost_tc(const spl_params* q, const void* z, long long pitch, 
                            int* argmax, unsigned* status, cudaStream_t s);
 // Intensity step of Sec. II-E after a depth kernel that left each pixel's photon count in a.bg (intensity.cu).
 cudaError_t launch_intensity(const EstimateArgs& a, cudaStream_t s);
-// Filter step with the data term on the tensor cores (tcfilter.cu); a.z holds FP16 histograms.
+// Filter step with the data term on the tensor cores (tcfilter.cu); a.z holds FP16 or uint16 histograms (then
+// followed by launch_estimate_redo). Returns cudaErrorInvalidConfiguration, before launching anything, when the
+// shape does not fit the kernel's shared memory.
 cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream_t s);
+// The FP32 filter step on the pixels that the uint16 tensor-core step marked with mu = NaN (estimate.cu).
+cudaError_t launch_estimate_redo(const EstimateArgs& a, cudaStream_t s);
 unsigned* tc_status_ptr();
 cudaError_t tc_status_read(unsigned* out);
 

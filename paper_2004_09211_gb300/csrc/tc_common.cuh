@@ -180,16 +180,17 @@ inline EncodeTiled encode_fn() {
     return fn;
 }
 
-// Tensor map of FP16 histograms [P][pitch] (T valid bins per row) read in boxes of 64 bins x 128 pixels with
-// the 128-byte swizzle; bins >= T, pixels >= P and negative bins read as zero.
-inline cudaError_t hist_map(CUtensorMap* map, const void* z, long long pitch, int T, long long P) {
+// Tensor map of 16-bit histograms [P][pitch] (T valid bins per row; FP16, or uint16 counts when u16) read in
+// boxes of 64 bins x 128 pixels with the 128-byte swizzle; bins >= T, pixels >= P and negative bins read as zero.
+inline cudaError_t hist_map(CUtensorMap* map, const void* z, long long pitch, int T, long long P, bool u16 = false) {
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {static_cast<cuuint64_t>(T), static_cast<cuuint64_t>(P)};
     const cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch) * 2};
     const cuuint32_t box[2] = {64, 128};
     const cuuint32_t estr[2] = {1, 1};
-    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(z), dims, strides, box, estr,
+    if (enc(map, u16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(z),
+            dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;

@@ -1,5 +1,5 @@
-// One frame of the online filter (Algorithm 1) with the data term on the tensor cores: FP16 histograms in, the
-// same outputs as spl_filter_step out, nothing per candidate written to memory.
+// One frame of the online filter (Algorithm 1) with the data term on the tensor cores: FP16 or uint16 histograms
+// in, the same outputs as the FP32 filter step out, nothing per candidate written to memory.
 //
 // Data term. C(d) = sum_j g_j z[d - peak + j] (Eq. beta_div2) for 128 pixels x 64 candidates per tile, as the
 // banded-Toeplitz product of tc.cu: C[p, 64 t + n] = sum_k Z[p, a0 + 64 t + k] G[k, n] with G[k, n] =
@@ -11,7 +11,9 @@
 //   warp 4  TMA producer: the 64-bin slabs of a 128-pixel block, origin x0 <= 0 so that every bin of [0, T) and
 //           every candidate window is covered, into a ring of R slabs (128-byte swizzled; zero fill outside).
 //   warp 5  MMA issuer: per slab the count MMA; once a tile's last slab has landed, the tile's MMAs into one of
-//           two accumulators; each slab goes back to the producer as soon as no later tile reads it.
+//           two accumulators; each slab goes back to the producer as soon as no later tile reads it. With uint16
+//           histograms the whole warp first converts each landed slab to FP16 in place (convert_slab: exact for
+//           counts below 1024) and notes whether the block holds a larger count.
 //   warps 0-3 epilogue, thread = pixel = TMEM lane:
 //     prior   Eq. predict from the 3x3 neighbour states, equal Gaussians merged (as the warp kernel does);
 //     tiles   ell(d) = lambda log2(e) C(d) + log2 f(d) in log2 units. A lower bound of max ell is the prior at its
@@ -21,7 +23,9 @@
 //             into running (weight, mean, second central moment) with a shared exponent reference, the chunk's
 //             own moments taken about its best candidate (the pairwise update of Chan, Golub and LeVeque), so
 //             no step subtracts large nearly equal numbers.
-//     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax; the photon count K goes to bg.
+//     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax; the photon count K goes to bg. A
+//             uint16 block holding a count of 1024 or more gets mu = NaN instead: FP16 would not carry its counts
+//             exactly, and the FP32 kernel computes those pixels again (k_estimate_redo, estimate.cu).
 // A second launch (intensity.cu) then runs the intensity MLE of Sec. II-E on the template at round-half-even(mu)
 // with that K and writes refl and bg.
 // All mbarrier waits are bounded (status bit 0 on time-out; the roles then stop, in-flight copies and MMAs are
@@ -400,10 +404,32 @@ __device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmi
     }
 }
 
+// One landed slab of uint16 counts (kSlabBytes, any swizzle: elements convert in place) to FP16, by the whole warp.
+// For u < 1024 the FP16 number with bits 0x6400 | u is exactly 1024 + u, so one OR and one packed FP16 subtraction
+// of 1024 give u exactly, two bins at a time. Returns nonzero (on the lanes that saw one) when a count is 1024 or
+// more: bits 10-15 of its 16-bit half are set.
+__device__ __forceinline__ unsigned convert_slab(unsigned char* slab, int lane) {
+    uint4* v = reinterpret_cast<uint4*>(slab);
+    unsigned big = 0;
+#pragma unroll 4
+    for (int i = lane; i < static_cast<int>(kSlabBytes / 16); i += 32) {
+        uint4 w = v[i];
+        big |= (w.x | w.y | w.z | w.w) & 0xFC00FC00u;
+        unsigned r[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r[k]) : "r"(r[k] | 0x64006400u), "r"(0x64006400u));
+        v[i] = make_uint4(r[0], r[1], r[2], r[3]);
+    }
+    return big;
+}
+
+template <bool U16>
 __global__ void __launch_bounds__(kThreads, 2)
     k_filter_tc(const __grid_constant__ CUtensorMap zmap, const EstimateArgs a, const TcGeom g, unsigned* status) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bar[2 * kMaxRing + 9];
+    __shared__ __align__(8) unsigned long long bar[2 * kMaxRing + 11];
+    __shared__ int s_ovf[2];  // uint16 input: the block (by parity) holds a count >= 1024
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float s_g[SPL_MAX_TAPS];
@@ -419,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const unsigned accf0 = smem_u32(&bar[2 * kMaxRing]), acce0 = smem_u32(&bar[2 * kMaxRing + 2]);
     const unsigned cntf0 = smem_u32(&bar[2 * kMaxRing + 4]), cnte0 = smem_u32(&bar[2 * kMaxRing + 6]);
     const unsigned drain = smem_u32(&bar[2 * kMaxRing + 8]);
+    const unsigned ovf0 = smem_u32(&bar[2 * kMaxRing + 9]);  // s_ovf of a block written (uint16 input)
     volatile int* stop = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -440,6 +467,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             mbar_init(cnte0 + 8 * i, 4);
         }
         mbar_init(drain, 1);
+        mbar_init(ovf0, 1);
+        mbar_init(ovf0 + 8, 1);
+        s_ovf[0] = s_ovf[1] = 0;
         abort_flag = 0;
     }
     __syncthreads();
@@ -483,20 +513,35 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (unsigned i = cnt > ring ? cnt - ring : 0; i < cnt; ++i) wait_quiet(full0 + 8 * (i % ring), (i / ring) & 1u);
         }
     } else if (warp == 5) {
-        // ================= MMA issuer =================
-        if (lane == 0) {
-            unsigned gs = 0, rel = 0, tcount = 0, blk = 0;
-            bool ok = true;
-            for (int pt = blockIdx.x; pt < g.npt && ok; pt += gridDim.x, ++blk) {
-                const unsigned base_s = gs;
-                const uint32_t dcnt = tmem + kCntCol + 16u * (blk & 1u);
-                if (blk >= 2 && !(ok = wait_bounded(cnte0 + 8 * (blk & 1u), ((blk >> 1) - 1) & 1u, stop, status)))
+        // ================= MMA issuer (lane 0); with uint16 input the warp converts each slab first =================
+        unsigned gs = 0, rel = 0, tcount = 0, blk = 0;
+        bool ok = true;
+        for (int pt = blockIdx.x; pt < g.npt && ok; pt += gridDim.x, ++blk) {
+            const unsigned base_s = gs;
+            const uint32_t dcnt = tmem + kCntCol + 16u * (blk & 1u);
+            if (blk >= 2) {
+                if (lane == 0) ok = wait_bounded(cnte0 + 8 * (blk & 1u), ((blk >> 1) - 1) & 1u, stop, status);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    ok = false;
                     break;
+                }
+            }
+            fence_after();
+            unsigned big = 0;
+            for (int s = 0; s < g.S; ++s, ++gs) {
+                if (lane == 0) ok = wait_bounded(full0 + 8 * (gs % ring), (gs / ring) & 1u, stop, status);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    ok = false;
+                    break;
+                }
                 fence_after();
-                for (int s = 0; s < g.S; ++s, ++gs) {
-                    if (!(ok = wait_bounded(full0 + 8 * (gs % ring), (gs / ring) & 1u, stop, status))) break;
-                    fence_after();
-                    const unsigned aslab = ringA + (gs % ring) * kSlabBytes;
+                const unsigned aslab = ringA + (gs % ring) * kSlabBytes;
+                if (U16) {  // in place, then made visible to the tensor cores (async proxy) before lane 0 issues
+                    big |= convert_slab(gbase + (aslab - base), lane);
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    __syncwarp();
+                }
+                if (lane == 0) {
 #pragma unroll
                     for (int kk = 0; kk < kSlab; kk += 16)
                         mma_f16<kIdescCnt>(dcnt, desc_sw128(aslab + 2 * kk), desc_sw128(Bone + 2 * kk),
@@ -504,39 +549,56 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const int t = s - g.mlead - g.nslab + 1;
                     if (t >= 0 && t < g.ntiles) {
                         const unsigned acc = tcount & 1u, use = tcount >> 1;
-                        if (use > 0 && !(ok = wait_bounded(acce0 + 8 * acc, (use - 1) & 1u, stop, status))) break;
-                        fence_after();
-                        const uint32_t d = tmem + acc * kN;
-                        for (int j = 0; j < g.nslab; ++j) {
-                            const unsigned sj = base_s + g.mlead + t + j;
-                            const unsigned sl = ringA + (sj % ring) * kSlabBytes;
-                            const int k_end = min(kSlab * (j + 1), g.kw);
-                            for (int k = kSlab * j; k < k_end; k += 16) {
-                                const unsigned koff = (k - kSlab * j) * 2;
-                                const uint64_t ad = desc_sw128(sl + koff);
-                                mma_f16<kIdescTile>(d, ad, desc_sw128(Bhi + j * kBSlabBytes + koff), k > 0 ? 1u : 0u);
-                                mma_f16<kIdescTile>(d, ad, desc_sw128(Blo + j * kBSlabBytes + koff), 1u);
+                        if (use > 0) ok = wait_bounded(acce0 + 8 * acc, (use - 1) & 1u, stop, status);
+                        if (ok) {
+                            fence_after();
+                            const uint32_t d = tmem + acc * kN;
+                            for (int j = 0; j < g.nslab; ++j) {
+                                const unsigned sj = base_s + g.mlead + t + j;
+                                const unsigned sl = ringA + (sj % ring) * kSlabBytes;
+                                const int k_end = min(kSlab * (j + 1), g.kw);
+                                for (int k = kSlab * j; k < k_end; k += 16) {
+                                    const unsigned koff = (k - kSlab * j) * 2;
+                                    const uint64_t ad = desc_sw128(sl + koff);
+                                    mma_f16<kIdescTile>(d, ad, desc_sw128(Bhi + j * kBSlabBytes + koff),
+                                                        k > 0 ? 1u : 0u);
+                                    mma_f16<kIdescTile>(d, ad, desc_sw128(Blo + j * kBSlabBytes + koff), 1u);
+                                }
                             }
+                            mma_commit(accf0 + 8 * acc);
+                            ++tcount;
                         }
-                        mma_commit(accf0 + 8 * acc);
-                        ++tcount;
                     }
-                    // slabs that no later tile of the block reads go back to the producer
-                    const int tn = max(0, s - g.mlead - g.nslab + 2);
-                    const unsigned need = tn < g.ntiles ? base_s + g.mlead + tn : gs + 1;
-                    const unsigned lim = min(need, gs + 1);
-                    for (; rel < lim; ++rel) mma_commit(empty0 + 8 * (rel % ring));
+                    if (ok) {  // slabs that no later tile of the block reads go back to the producer
+                        const int tn = max(0, s - g.mlead - g.nslab + 2);
+                        const unsigned need = tn < g.ntiles ? base_s + g.mlead + tn : gs + 1;
+                        const unsigned lim = min(need, gs + 1);
+                        for (; rel < lim; ++rel) mma_commit(empty0 + 8 * (rel % ring));
+                    }
                 }
-                if (!ok) break;
-                mma_commit(cntf0 + 8 * (blk & 1u));
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    ok = false;
+                    break;
+                }
             }
+            if (!ok) break;
+            if (U16) {  // the block's flag, published by the barrier the epilogue waits on before reading it
+                const unsigned any = __any_sync(0xffffffffu, big != 0);
+                if (lane == 0) {
+                    s_ovf[blk & 1u] = any ? 1 : 0;
+                    mbar_arrive(ovf0 + 8 * (blk & 1u));
+                }
+            }
+            if (lane == 0) mma_commit(cntf0 + 8 * (blk & 1u));
+        }
+        if (lane == 0) {
             mma_commit(drain);
             wait_quiet(drain, 0);
         }
     } else {
         // ================= epilogue: thread = pixel = TMEM lane =================
         const long long P = static_cast<long long>(a.H) * a.W;
-        const int D = a.D, T = a.T, L = a.L, dmin = a.dmin;
+        const int D = a.D, dmin = a.dmin;
         const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
         unsigned tcount = 0, blk = 0;
         bool ok = true;
@@ -603,15 +665,25 @@ __global__ void __launch_bounds__(kThreads, 2)
             fence_after();
             const float K = tmem_ld1(lane_base + kCntCol + 16u * (blk & 1u));
             tmem_wait_ld();
+            int redo = 0;
+            if (U16) {  // read before the count accumulator is released (the issuer then rewrites the flag)
+                ok = __all_sync(0xffffffffu, wait_bounded(ovf0 + 8 * (blk & 1u), (blk >> 1) & 1u, stop, status));
+                if (!ok) break;
+                redo = *reinterpret_cast<volatile int*>(&s_ovf[blk & 1u]);
+            }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(cnte0 + 8 * (blk & 1u));
             // outputs; the photon count goes to bg, where the intensity launch reads it
             if (valid) {
-                a.mu[p] = static_cast<float>(dmin) + st.mu;
-                a.var[p] = st.M2 / st.W;
-                if (a.argmax) a.argmax[p] = dmin + st.bidx;
-                if (a.refl) a.bg[p] = K;
+                if (redo) {
+                    a.mu[p] = NAN;  // k_estimate_redo computes this pixel again
+                } else {
+                    a.mu[p] = static_cast<float>(dmin) + st.mu;
+                    a.var[p] = st.M2 / st.W;
+                    if (a.argmax) a.argmax[p] = dmin + st.bidx;
+                    if (a.refl) a.bg[p] = K;
+                }
             }
         }
     }
@@ -713,13 +785,19 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
     g.ring = ring;
     const size_t smem = fixed + static_cast<size_t>(ring) * kSlabBytes;
 
+    const bool u16 = a.fmt == SPL_HIST_U16;
     CUtensorMap map;
-    if ((e = hist_map(&map, a.z, a.pitch, a.T, P)) != cudaSuccess) return e;
-    if ((e = prepare_kernel(dev, 0, reinterpret_cast<const void*>(k_filter_tc), smem)) != cudaSuccess) return e;
+    if ((e = hist_map(&map, a.z, a.pitch, a.T, P, u16)) != cudaSuccess) return e;
+    const void* kern = u16 ? reinterpret_cast<const void*>(k_filter_tc<true>)
+                           : reinterpret_cast<const void*>(k_filter_tc<false>);
+    if ((e = prepare_kernel(dev, u16 ? 1 : 0, kern, smem)) != cudaSuccess) return e;
     const long long want = static_cast<long long>(nsm) * per_sm;
     const int grid = static_cast<int>(g.npt < want ? g.npt : want);
-    k_filter_tc<<<grid, kThreads, smem, s>>>(map, a, g, status);
-    if ((e = cudaGetLastError()) != cudaSuccess || !a.refl) return e;
+    if (u16) k_filter_tc<true><<<grid, kThreads, smem, s>>>(map, a, g, status);
+    else k_filter_tc<false><<<grid, kThreads, smem, s>>>(map, a, g, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (u16 && (e = launch_estimate_redo(a, s)) != cudaSuccess) return e;
+    if (!a.refl) return cudaSuccess;
     return launch_intensity(a, s);
 }
 

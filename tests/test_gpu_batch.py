@@ -155,7 +155,7 @@ def test_batch_graph_replay_and_tuning_reproduce_eager():
 
 
 def test_batch_equals_histogram_kernel():
-    """The photon-list kernel and the histogram kernel agree on the same data (different summation order)."""
+    """The photon-list kernel and the FP32 histogram kernel agree on the same data (different summation order)."""
     seqs = _make_frames(_seq_specs()[:3], N=2, seed=9)
     res, _, _ = _run(seqs, 2)
     for i, q in enumerate(seqs):
@@ -166,7 +166,7 @@ def test_batch_equals_histogram_kernel():
             off, bins = q["frames"][n]
             z = synth.csr_to_histograms(off, bins, q["T"])
             zt = synth.pitched(torch.from_numpy(z.astype(np.int32)).to(torch.uint16), synth.pad_pitch(q["T"])).to(DEV)
-            o = spl.spl_filter_step(prm, zt, hd, mu, var)
+            o = spl.spl_filter_step_fp32(prm, zt, hd, mu, var)
             torch.cuda.synchronize()
             check_close(o["mu"].cpu().numpy(), res[n][i]["mu_out"], f"seq {i} frame {n} mu", rtol=1e-5)
             check_close(o["var"].cpu().numpy(), res[n][i]["var_out"], f"seq {i} frame {n} var", rtol=1e-4,

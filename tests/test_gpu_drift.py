@@ -6,6 +6,9 @@ next frame's prior (Eq. predict), so FP32 rounding could accumulate along the se
 states are compared at the filter's tolerances (relative 1e-4; variance floor 1e-6 bins^2), and the largest
 relative difference over the whole sequence is printed (run with -s).
 
+Both arithmetic paths of the filter step run the chain: spl_filter_step (uint16 histograms: the data term on the
+tensor cores) and spl_filter_step_fp32 (the FP32 CUDA-core kernel), each against the same oracle chain.
+
 Two regimes, 3000 frames each, 8 x 8 pixels, the 48-tap asymmetric IRF, beta = 0.5, sigma_RW^2 = 3, the cross
 weights with nu0 = 0.5:
   * the paper's first real-data sequence: T = 153 bins, about 55 signal and 35 background photons per pixel and
@@ -63,33 +66,40 @@ def test_long_sequence_drift(orc, T, signal, sbr, seed):
     pitch = synth.pad_pitch(T)
     zd = synth.pitched(torch.from_numpy(z.reshape(N, P, T).astype(np.int32)).to(torch.uint16), pitch).to(DEV)
     hd = torch.from_numpy(h).to(DEV)
-    mus = torch.empty(N + 1, P, device=DEV)
-    vars_ = torch.empty(N + 1, P, device=DEV)
-    spl.spl_state_init(prm, mus[0], vars_[0])
-    for k in range(N):
-        spl.spl_filter_step(prm, zd[k], hd, mus[k], vars_[k], intensity=False,
-                            out=dict(mu=mus[k + 1], var=vars_[k + 1]))
-    torch.cuda.synchronize()
-    gm, gv = mus.cpu().numpy().astype(np.float64), vars_.cpu().numpy().astype(np.float64)
+    chains = {}
+    for name, step in (("tensor-core route", spl.spl_filter_step), ("FP32 kernel", spl.spl_filter_step_fp32)):
+        mus = torch.empty(N + 1, P, device=DEV)
+        vars_ = torch.empty(N + 1, P, device=DEV)
+        spl.spl_state_init(prm, mus[0], vars_[0])
+        for k in range(N):
+            step(prm, zd[k], hd, mus[k], vars_[k], intensity=False, out=dict(mu=mus[k + 1], var=vars_[k + 1]))
+        torch.cuda.synchronize()
+        chains[name] = (mus.cpu().numpy().astype(np.float64), vars_.cpu().numpy().astype(np.float64))
+    assert spl.spl_tc_status() == 0
 
     q = orc.params(T, L, peak, beta=beta, sigma_rw2=s2, nu=synth.cross_weights(0.5))
     m, v = orc.state_init(q, H, W)
-    worst_m = worst_v = 0.0
-    worst_frame = 0
-    bad = []
+    stats = {name: dict(worst_m=0.0, worst_v=0.0, worst_frame=0, bad=[]) for name in chains}
     for k in range(N):
         e = orc.filter_step(q, h, z[k].astype(np.float64), m, v)
-        m, v = e["mu"], e["var"]
-        em = np.abs(gm[k + 1] - m.reshape(-1)) / np.abs(m.reshape(-1))
-        ev = np.abs(gv[k + 1] - v.reshape(-1)) / (np.abs(v.reshape(-1)) + 1e-2)
-        if em.max() > worst_m or ev.max() > worst_v:
-            worst_frame = k
-        worst_m, worst_v = max(worst_m, em.max()), max(worst_v, ev.max())
-        okm = np.abs(gm[k + 1] - m.reshape(-1)) <= 1e-4 * np.abs(m.reshape(-1))
-        okv = np.abs(gv[k + 1] - v.reshape(-1)) <= 1e-4 * np.abs(v.reshape(-1)) + 1e-6
-        if not (okm.all() and okv.all()) and len(bad) < 5:
-            bad.append((k, int(np.argmin(okm & okv))))
-    med_var = float(np.median(gv[N]))
-    print(f"\ndrift T={T} signal={signal} SBR={sbr}: {N} frames, largest relative difference mu {worst_m:.3g}, "
-          f"var {worst_v:.3g} (frame {worst_frame}); median variance at the end {med_var:.3g} bins^2")
-    assert not bad, f"first frames/pixels outside the tolerance: {bad}; largest mu {worst_m:.3g}, var {worst_v:.3g}"
+        m, v = e["mu"].reshape(-1), e["var"].reshape(-1)
+        for name, (gm, gv) in chains.items():
+            st = stats[name]
+            em = np.abs(gm[k + 1] - m) / np.abs(m)
+            ev = np.abs(gv[k + 1] - v) / (np.abs(v) + 1e-2)
+            if em.max() > st["worst_m"] or ev.max() > st["worst_v"]:
+                st["worst_frame"] = k
+            st["worst_m"], st["worst_v"] = max(st["worst_m"], em.max()), max(st["worst_v"], ev.max())
+            okm = np.abs(gm[k + 1] - m) <= 1e-4 * np.abs(m)
+            okv = np.abs(gv[k + 1] - v) <= 1e-4 * np.abs(v) + 1e-6
+            if not (okm.all() and okv.all()) and len(st["bad"]) < 5:
+                st["bad"].append((k, int(np.argmin(okm & okv))))
+        m, v = m.reshape(H, W), v.reshape(H, W)
+    for name, (gm, gv) in chains.items():
+        st = stats[name]
+        print(f"\ndrift T={T} signal={signal} SBR={sbr}, {name}: {N} frames, largest relative difference mu "
+              f"{st['worst_m']:.3g}, var {st['worst_v']:.3g} (frame {st['worst_frame']}); median variance at the end "
+              f"{float(np.median(gv[N])):.3g} bins^2")
+    for name, st in stats.items():
+        assert not st["bad"], (f"{name}: first frames/pixels outside the tolerance: {st['bad']}; largest mu "
+                               f"{st['worst_m']:.3g}, var {st['worst_v']:.3g}")

@@ -194,7 +194,7 @@ def test_filter_tc_agrees_with_fp32_path():
     m2, v2 = m1.clone(), v1.clone()
     for z in zs:
         zt = _gpu_hist(z, T, torch.float16)
-        a = spl.spl_filter_step(prm, zt, hd, m1, v1)
+        a = spl.spl_filter_step_fp32(prm, zt, hd, m1, v1)
         b = spl.spl_filter_step_tc(prm, zt, hd, m2, v2)
         torch.cuda.synchronize()
         check_close(_np(b["mu"]), _np(a["mu"]), "mu tc vs fp32", rtol=1e-4)
