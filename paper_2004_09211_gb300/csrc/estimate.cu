@@ -542,13 +542,22 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
 // The tensor-core kernel converts uint16 counts to FP16 exactly only below 1024; a 128-pixel block holding a
 // larger count gets mu = NaN instead of its results. This kernel computes those pixels again with the steps of
 // k_estimate (without its prefetching: the case is rare), one warp per pixel. A warp tests the mu of 32
-// consecutive pixels at once and takes the marked ones in turn, so a frame with none costs one load per pixel.
+// consecutive pixels at once and takes the marked ones in turn; a CTA whose pixels hold no mark returns before
+// any set-up, so a frame with none costs one load per pixel.
 __global__ void __launch_bounds__(256) k_estimate_redo(const EstimateArgs a) {
     constexpr int FMT = SPL_HIST_U16, CB = 8;
     extern __shared__ __align__(16) float dyn[];
     __shared__ __align__(16) float gs[SPL_MAX_TAPS + 4];
     __shared__ float s_gmax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const long long P = static_cast<long long>(a.H) * a.W;
+    {  // the CTA's pixels first: nothing marked (the usual case) means nothing to set up
+        int any = 0;
+        for (long long g0 = (static_cast<long long>(blockIdx.x) * nwarps + warp) * 32; g0 < P && !any;
+             g0 += static_cast<long long>(gridDim.x) * nwarps * 32)
+            any = __any_sync(0xffffffffu, g0 + lane < P && isnan(a.mu[g0 + lane]));
+        if (!__syncthreads_or(any)) return;
+    }
     for (int j = threadIdx.x; j < SPL_MAX_TAPS + 4; j += blockDim.x) {
         const float hj = j < a.L ? a.h[j] : 0.f;
         gs[j] = hj > 0.f ? powf(hj, a.beta) : 0.f;
@@ -572,7 +581,6 @@ __global__ void __launch_bounds__(256) k_estimate_redo(const EstimateArgs a) {
     float* cs = base + sl.cs;
     float* raw = base + sl.raw;
     if (lane < 4) reinterpret_cast<float4*>(raw + sl.nch * 4)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const long long P = static_cast<long long>(a.H) * a.W;
     for (long long g0 = (static_cast<long long>(blockIdx.x) * nwarps + warp) * 32; g0 < P;
          g0 += static_cast<long long>(gridDim.x) * nwarps * 32) {
         unsigned marked = __ballot_sync(0xffffffffu, g0 + lane < P && isnan(a.mu[g0 + lane]));

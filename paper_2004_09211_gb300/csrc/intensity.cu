@@ -100,15 +100,53 @@ __device__ __forceinline__ float group8_sum(float v) {
     return v;
 }
 
-// The solve for four pixels per warp, one per group of 8 lanes (lane s of a group holds bins s + 8 q, q < 8, so
-// L <= 64). The groups iterate together (the shuffles are warp-wide) until every group has converged; a
-// converged group keeps its f. need == false: the group only takes part (f = 0). Returns the signal fraction f.
-__device__ __forceinline__ float fraction_g8(const float* zj, const float* aj, float K, int L, int T, bool need) {
+// Packs the group's bins with photons (z > 0) to the front: lane s of the group then holds packed entries s + 8 q
+// (zeros past the group's count). Every sum of the solve runs over bins with photons only, so afterwards it needs
+// ceil(n / 8) entries per lane instead of 8; the count is returned as the largest over the warp's four groups
+// (warp-uniform). buf: 128 floats of shared memory per group.
+__device__ __forceinline__ int pack_group8(float* zj, float* aj, float* buf, int sl) {
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cnt += zj[q] > 0.f ? 1 : 0;
+    int inc = cnt;  // inclusive prefix over the group's lanes
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o, 8);
+        if (sl >= o) inc += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 7, 8);
+    int k = inc - cnt;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (zj[q] > 0.f) {
+            buf[2 * k] = zj[q];
+            buf[2 * k + 1] = aj[q];
+            ++k;
+        }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int e = sl + 8 * q;
+        const bool in = e < total;
+        zj[q] = in ? buf[2 * e] : 0.f;
+        aj[q] = in ? buf[2 * e + 1] : 0.f;
+    }
+    __syncwarp();
+    return static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>((total + 7) >> 3)));
+}
+
+// The solve for four pixels per warp, one per group of 8 lanes (lane s of a group holds its bins with photons, as
+// packed by pack_group8, in entries q < nq). The groups iterate together (the shuffles are warp-wide) until every
+// group has converged; a converged group keeps its f. need == false: the group only takes part (f = 0). Returns
+// the signal fraction f.
+__device__ __forceinline__ float fraction_g8(const float* zj, const float* aj, int nq, float K, int L, int T,
+                                             bool need) {
     const float u = 1.f / static_cast<float>(T);
     float kin = 0.f, za = 0.f, p1 = 0.f;
     bool zero_tap = false;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+        if (q >= nq) break;
         kin += zj[q];
         za = fmaf(zj[q], aj[q], za);
         if (zj[q] > 0.f) {
@@ -141,6 +179,7 @@ __device__ __forceinline__ float fraction_g8(const float* zj, const float* aj, f
         float gs = 0.f, gp = 0.f;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
+            if (q >= nq) break;
             if (zj[q] > 0.f) {
                 const float e = __fdividef(aj[q] - u, fmaf(f, aj[q] - u, u));
                 gs = fmaf(zj[q], e, gs);
@@ -170,12 +209,14 @@ __device__ __forceinline__ float fraction_g8(const float* zj, const float* aj, f
 }
 
 // Maximised log-likelihood ratio of the group's window at signal fraction f (0 when need == false):
-// sum_{z_t > 0} z_t log(1 - f + T f a_t) + K_out log(1 - f). Warp-collective.
-__device__ __forceinline__ float llr_g8(const float* zj, const float* aj, float f, float K, int T, bool need) {
+// sum_{z_t > 0} z_t log(1 - f + T f a_t) + K_out log(1 - f), over the packed entries q < nq. Warp-collective.
+__device__ __forceinline__ float llr_g8(const float* zj, const float* aj, int nq, float f, float K, int T,
+                                        bool need) {
     const float tf = static_cast<float>(T) * f, of = 1.f - f;
     float s = 0.f, kin = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+        if (q >= nq) break;
         kin += zj[q];
         if (zj[q] > 0.f) s = fmaf(zj[q], logf(fmaf(tf, aj[q], of)), s);
     }
@@ -212,9 +253,11 @@ template <int FMT, bool DETECT>
 __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
     __shared__ float as[SPL_MAX_TAPS];
     __shared__ float s_hsum, s_hvar;
+    __shared__ float s_pack[8][4][128];  // per warp and group: the packed (z, a) pairs
     const float hsum = template_table(a, as, &s_hsum, &s_hvar);
     const float hvar = s_hvar;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, sl = lane & 7;
+    float* pbuf = s_pack[warp][grp];
     const long long P = static_cast<long long>(a.H) * a.W;
     const long long stride = 4LL * gridDim.x * (blockDim.x >> 5);
     for (long long p0 = 4LL * (static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + warp); p0 < P; p0 += stride) {
@@ -232,7 +275,8 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
             zj[q] = need && j < a.L ? hist_value<FMT>(a.z, a.pitch, p, t0 + j) : 0.f;
             aj[q] = j < a.L ? as[j] : 0.f;
         }
-        const float f = fraction_g8(zj, aj, K, a.L, a.T, need);
+        int nq = pack_group8(zj, aj, pbuf, sl);
+        const float f = fraction_g8(zj, aj, nq, K, a.L, a.T, need);
         const float r = f * K / hsum, b = (1.f - f) * K * (1.f / static_cast<float>(a.T));
         float llr = 0.f;
         if (DETECT) {  // the evidence with the template at the pseudo-posterior mode
@@ -245,12 +289,15 @@ __global__ void __launch_bounds__(256) k_intensity4(const EstimateArgs a) {
                     for (int q = 0; q < 8; ++q) {
                         const int j = sl + 8 * q;
                         zj[q] = j < a.L ? hist_value<FMT>(a.z, a.pitch, p, t1 + j) : 0.f;
+                        aj[q] = j < a.L ? as[j] : 0.f;
                     }
                 }
-                const float f1 = fraction_g8(zj, aj, K, a.L, a.T, again);
+                const int nq1 = pack_group8(zj, aj, pbuf, sl);  // every group repacks (warp-collective)
+                nq = nq1;
+                const float f1 = fraction_g8(zj, aj, nq, K, a.L, a.T, again);
                 if (again) fm = f1;
             }
-            llr = llr_g8(zj, aj, fm, K, a.T, need);
+            llr = llr_g8(zj, aj, nq, fm, K, a.T, need);
         }
         if (valid && sl == 0) write_pixel<DETECT>(a, p, faulty, present, K, hsum, hvar, r, b, llr);
         __syncwarp();
