@@ -51,19 +51,26 @@ WORKLOAD = "video 256x256x50 frames, T=1500, 48-tap asymmetric IRF, SBR {0.01,0.
 # compiles; the pseudo-posterior code lives in posterior.cuh, apart from the helpers in pixel.cuh, so that a change
 # to it voids exactly the captures of the kernels that call it (the depth and photon-list kernels).
 TRAFFIC_CAPTURES = {
-    # one filter step of the video job: the depth launch of frame 1 of each of the nine runs (nine captures of one
-    # launch each, mean) plus one intensity launch (ncu dram__bytes_read.sum + dram__bytes_write.sum and
-    # smsp__inst_executed.sum)
+    # one FP32 filter step of the video job (spl_filter_step_fp32): the depth launch of frame 1 of each of the nine
+    # runs (nine captures of one launch each, mean) plus the intensity launch (mean of the same nine frames)
+    # (ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum)
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "posterior.cuh", "intensity.cu"),
-                   "sha256": "e3a111e7d297c262dfea2694c6580cfd80c40f6be6ade02ab860ee87845029ce",
-                   "bytes_per_pixel": (197.75e6 + 3.49e6 + 15.60e6) / 65536,
-                   "inst_per_pixel": (368.24e6 + 25.01e6) / 65536},
+                   "sha256": "3360ba4d0c9c713162f8fa1b90b9e08fb21ec6f1ebc55fce92aee98be64e9a8f",
+                   "bytes_per_pixel": (201.24e6 + 15.52e6) / 65536,
+                   "inst_per_pixel": (368.24e6 + 14.85e6) / 65536},
+    # one uint16 filter step of the video job (spl_filter_step): the tensor-core launch, the redo launch and the
+    # intensity launch of frame 1 of each of the nine runs (mean)
+    "k_filter_tc_u16": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh", "estimate.cu",
+                                    "posterior.cuh"),
+                        "sha256": "dbc276ca433594cc7faba76ed94c44fd51640e9cb2eb12f659577ed2db8dca72",
+                        "bytes_per_pixel": 221.73e6 / 65536,
+                        "inst_per_pixel": 151.59e6 / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh"),
-                    "sha256": "4b91b965a951a7a579e6b8795932c4705fd37b0ae2963e43304adc5e2c2fd601",
-                    "bytes_per_pixel": (537.63e6 + 3.65e6 + 17.20e6) / 65536,
+                    "sha256": "822e47827c851ef9b23f136f85cc5ce229ada120d82354fe8333713ec4feffe6",
+                    "bytes_per_pixel": (537.633e6 + 3.613e6 + 17.199e6) / 65536,
                     # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture
                     # of frame 2 of a 256 x 256 run of the mixed workload
-                    "inst_per_pixel": (343.85e6 + 17.01e6) / 65536},
+                    "inst_per_pixel": (348.01e6 + 14.004e6) / 65536},
     # one launch of the photon-list kernel over all 64 sequences of the batched workload (7 050 240 pixels)
     "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh"),
                 "sha256": "e014f5ee9513edfa67181adc990848f68d18e585f22b7c4255979bfc41bbf4e5",
@@ -247,7 +254,8 @@ def run_job(spl, prms, hd, videos, states, outs, stream, ev=None, step=None, lan
             if ev is not None:
                 ev[1].append(torch.cuda.Event(enable_timing=True))
                 ev[1][-1].record(st)
-            launches += 2  # the depth kernel and the intensity kernel
+            # spl_filter_step on uint16 frames: tensor-core kernel, redo scan, intensity; otherwise depth, intensity
+            launches += 3 if step is spl.spl_filter_step else 2
     if lanes:
         for s_, _ in lanes:
             done = torch.cuda.Event()
