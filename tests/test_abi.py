@@ -80,23 +80,25 @@ def test_unsupported_sizes_reported():
     assert st == _abi.SPL_EUNSUPPORTED and "not supported" in msg
 
 
-def test_filter_argument_checks():
+@pytest.mark.parametrize("entry", ["spl_filter_step", "spl_filter_step_fp32"])
+def test_filter_argument_checks(entry):
     lib = _abi.load()
+    fn = getattr(lib, entry)
     prm = make_params(4, 4, 64, 25, 12, sigma_rw2=0.0)
     hz = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 64)
-    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
-                             0x6000, None, None, None, None)
+    st = fn(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000, 0x6000, None, None, None,
+            None)
     assert st == _abi.SPL_EINVAL and "sigma_rw2" in lib.spl_last_error().decode()
     prm = make_params(4, 4, 64, 25, 12, nu=[0] * 9)
-    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
-                             0x6000, None, None, None, None)
+    st = fn(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000, 0x6000, None, None, None,
+            None)
     assert st == _abi.SPL_EINVAL and "sum to 0" in lib.spl_last_error().decode()
     prm = make_params(4, 4, 64, 25, 12)
-    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x3000,
-                             0x6000, None, None, None, None)
+    st = fn(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x3000, 0x6000, None, None, None,
+            None)
     assert st == _abi.SPL_EINVAL and "alias" in lib.spl_last_error().decode()
-    st = lib.spl_filter_step(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
-                             0x6000, None, 0x7000, None, None)
+    st = fn(ct.byref(prm), ct.byref(hz), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000, 0x6000, None, 0x7000, None,
+            None)
     assert st == _abi.SPL_EINVAL and "refl and bg" in lib.spl_last_error().decode()
 
 
