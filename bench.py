@@ -72,10 +72,10 @@ TRAFFIC_CAPTURES = {
                     # of frame 2 of a 256 x 256 run of the mixed workload
                     "inst_per_pixel": (348.01e6 + 14.004e6) / 65536},
     # one launch of the photon-list kernel over all 64 sequences of the batched workload (7 050 240 pixels)
-    "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh"),
-                "sha256": "e014f5ee9513edfa67181adc990848f68d18e585f22b7c4255979bfc41bbf4e5",
-                "bytes_per_pixel": (459.59e6 + 124.96e6) / 7050240,
-                "inst_per_pixel": 32877.47e6 / 7050240},
+    "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh", "photons.cuh"),
+                "sha256": "f5824f43b6da8a5ca1affa3ab6ee1fddeaaaffe7532ae91505600800b054a963",
+                "bytes_per_pixel": (458.96e6 + 124.82e6) / 7050240,
+                "inst_per_pixel": 33720.18e6 / 7050240},
     # backward launches of the differentiable filter (128 x 128 frames, T = 1024): mean of three of the 20 launches
     # of one reverse sweep (they differ by 0.04 %)
     "k_diff_backward": {"sources": ("grad.cu", "pixel.cuh"),

@@ -6,7 +6,7 @@
 // work-queue head (one atomicAdd by lane 0), loads that sequence's IRF into its own shared-memory tables,
 // and processes the tile's pixels one at a time with the same per-pixel arithmetic as the histogram kernel
 // (pixel.cuh, posterior.cuh). The data term uses the photon-sum form of Eq. beta_div2:
-// C(d) = sum_k g[y_k - d + peak], formed lane = tap (corr_photons).
+// C(d) = sum_k g[y_k - d + peak], formed lane = tap from the list in global memory (corr_photon_list, photons.cuh).
 // The queue head is reset by a memset on the launch stream before every step, so a step is a memset node and
 // a kernel node in a CUDA graph. The plan (unit list, descriptor tables, queue heads, status word) is
 // allocated once at creation; nothing is allocated per step.
@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "pixel.cuh"
+#include "photons.cuh"
 #include "posterior.cuh"
 #include "spl_internal.h"
 
@@ -38,7 +39,7 @@ struct Unit {
 
 // Per-warp shared-memory slice for a batch whose largest candidate count is maxD (offsets in words).
 struct BSlice {
-    int gs, as, ph, ubs, cs, words;
+    int gs, as, bnd, ubs, cs, words;  // taps h^beta, template, per-block photon counts, bounds, C
 };
 
 __host__ __device__ __forceinline__ int r4(int x) { return (x + 3) & ~3; }
@@ -48,8 +49,8 @@ __host__ __device__ __forceinline__ BSlice make_bslice(int maxD) {
     const int nb = (maxD + 31) / 32;
     s.gs = 0;
     s.as = s.gs + SPL_MAX_TAPS + 4;
-    s.ph = s.as + SPL_MAX_TAPS;
-    s.ubs = s.ph + SPL_MAX_PHOTONS;
+    s.bnd = s.as + SPL_MAX_TAPS;
+    s.ubs = s.bnd + r4(nb);
     s.cs = s.ubs + r4(nb);
     s.words = s.cs + (nb * 32 > SPL_MAX_TAPS ? nb * 32 : SPL_MAX_TAPS);  // cs doubles as the window histogram
     return s;
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, 
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
     float* gs = base + sl.gs;
     float* as = base + sl.as;
-    int* ph = reinterpret_cast<int*>(base + sl.ph);
+    float* bnd = base + sl.bnd;
     float* ubs = base + sl.ubs;
     float* cs = base + sl.cs;
 
@@ -121,28 +122,13 @@ __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, 
                 }
                 continue;
             }
-            // photon bins of this pixel -> shared memory; out-of-range bins are dropped and reported
+            // C(d) for every candidate, and the photons that reach each block; out-of-range bins are dropped and
+            // reported
+            const int* pbins = f.bins + off0;
             int nk = 0;
             bool bad = false;
-            for (int k0 = 0; k0 < K; k0 += 32) {
-                const int k = k0 + lane;
-                int y = -1;
-                if (k < K) {
-                    y = f.bins[off0 + k];
-                    if (y < 0 || y >= T) {
-                        bad = true;
-                        y = -1;
-                    }
-                }
-                const unsigned ok = __ballot_sync(0xffffffffu, y >= 0);
-                if (y >= 0) ph[nk + __popc(ok & ((1u << lane) - 1u))] = y;
-                nk += __popc(ok);
-            }
-            if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, SPL_BATCH_BAD_BIN);
-            __syncwarp();
-
-            // C(d) for every candidate
-            const float cmax = corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane);
+            const float cmax = corr_photon_list(gs, pbins, K, T, cs, bnd, NB, D, L, u0, lane, nk, bad);
+            if (bad && lane == 0) atomicOr(status, SPL_BATCH_BAD_BIN);
 
             // prior from the previous frame's states of this sequence (Eq. predict)
             Prior pr;
@@ -169,18 +155,19 @@ __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, 
                 build_prior(w, m, v, lane, pr);
             }
 
-            const bool empty = nk == 0;
+            const bool empty_row = nk == 0;
             int bidx;
             float mu, var;
-            posterior(
-                grid, pr, cmax, empty, cs, ubs,
-                [&](int s_bin, int e_bin) {
-                    int n = 0;
-                    for (int k = 0; k < nk; ++k) n += (ph[k] >= s_bin) & (ph[k] <= e_bin);
-                    return static_cast<float>(n);
-                },
-                [&]() { corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane); },
-                lane, bidx, mu, var);
+            const int ub_b = block_bounds(
+                grid, pr, ubs, [&](int b) { return empty_row ? 0.f : grid.lam2 * grid.gmax * bnd[b] * 1.0001f; },
+                lane);
+            posterior_eval(grid, pr, cmax, cs, ubs, ub_b,
+                           [&]() {  // rare fallback: C again, in the same order
+                               int n2 = 0;
+                               bool b2 = false;
+                               corr_photon_list(gs, pbins, K, T, cs, nullptr, NB, D, L, u0, lane, n2, b2);
+                           },
+                           lane, bidx, mu, var);
             if (lane == 0) {
                 f.mu_out[p] = mu;
                 f.var_out[p] = var;
@@ -203,10 +190,7 @@ __global__ void __launch_bounds__(256) k_batch(const DevSeq* __restrict__ seqs, 
                     float* zwin = cs;  // the candidate scratch is free again: window histogram
                     for (int j = lane; j < SPL_MAX_TAPS; j += 32) zwin[j] = 0.f;
                     __syncwarp();
-                    for (int k = lane; k < nk; k += 32) {
-                        const int j = ph[k] - t0;
-                        if (j >= 0 && j < L) atomicAdd(&zwin[j], 1.f);
-                    }
+                    window_photons(pbins, K, T, t0, L, zwin, lane);
                     __syncwarp();
                     float zj[SPL_MAX_TAPS / 32], aj[SPL_MAX_TAPS / 32];
 #pragma unroll

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "pixel.cuh"
+#include "photons.cuh"
 #include "posterior.cuh"
 #include "spl_internal.h"
 
@@ -28,7 +29,7 @@ using namespace px;
 static __device__ __align__(256) unsigned g_noalloc_scratch[2 + SPL_NOALLOC_MAX_SEQ];
 
 struct NSlice {
-    int gs, as, ph, ubs, cs, words;
+    int gs, as, bnd, ubs, cs, words;  // taps h^beta, template, per-block photon counts, bounds, C
 };
 
 __host__ __device__ __forceinline__ NSlice make_nslice(int maxD) {
@@ -36,8 +37,8 @@ __host__ __device__ __forceinline__ NSlice make_nslice(int maxD) {
     const int nb = (maxD + 31) / 32;
     s.gs = 0;
     s.as = s.gs + SPL_MAX_TAPS + 4;
-    s.ph = s.as + SPL_MAX_TAPS;
-    s.ubs = s.ph + SPL_MAX_PHOTONS;
+    s.bnd = s.as + SPL_MAX_TAPS;
+    s.ubs = s.bnd + ((nb + 3) & ~3);
     s.cs = s.ubs + ((nb + 3) & ~3);
     s.words = s.cs + (nb * 32 > SPL_MAX_TAPS ? nb * 32 : SPL_MAX_TAPS);  // cs doubles as the window histogram
     return s;
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
     float* base = dyn + static_cast<size_t>(warp) * sl.words;
     float* gs = base + sl.gs;
     float* as = base + sl.as;
-    int* ph = reinterpret_cast<int*>(base + sl.ph);
+    float* bnd = base + sl.bnd;
     float* ubs = base + sl.ubs;
     float* cs = base + sl.cs;
     const unsigned* prefix = scratch + 1;
@@ -154,26 +155,13 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
                 }
                 continue;
             }
+            // C(d) for every candidate, and the photons that reach each block; out-of-range bins are dropped and
+            // reported
+            const int* pbins = f.bins + off0;
             int nk = 0;
             bool bad = false;
-            for (int k0 = 0; k0 < K; k0 += 32) {
-                const int k = k0 + lane;
-                int y = -1;
-                if (k < K) {
-                    y = f.bins[off0 + k];
-                    if (y < 0 || y >= T) {
-                        bad = true;
-                        y = -1;
-                    }
-                }
-                const unsigned ok = __ballot_sync(0xffffffffu, y >= 0);
-                if (y >= 0) ph[nk + __popc(ok & ((1u << lane) - 1u))] = y;
-                nk += __popc(ok);
-            }
-            if (__any_sync(0xffffffffu, bad) && lane == 0 && status) atomicOr(status, SPL_BATCH_BAD_BIN);
-            __syncwarp();
-
-            const float cmax = corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane);
+            const float cmax = corr_photon_list(gs, pbins, K, T, cs, bnd, NB, D, L, u0, lane, nk, bad);
+            if (bad && lane == 0 && status) atomicOr(status, SPL_BATCH_BAD_BIN);
 
             Prior pr;
             {
@@ -201,15 +189,17 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
 
             int bidx;
             float mu, var;
-            posterior(
-                grid, pr, cmax, nk == 0, cs, ubs,
-                [&](int s_bin, int e_bin) {
-                    int n = 0;
-                    for (int k = 0; k < nk; ++k) n += (ph[k] >= s_bin) & (ph[k] <= e_bin);
-                    return static_cast<float>(n);
-                },
-                [&]() { corr_photons(gs, ph, nk, cs, NB, D, L, u0, lane); },
-                lane, bidx, mu, var);
+            const bool empty_row = nk == 0;
+            const int ub_b = block_bounds(
+                grid, pr, ubs, [&](int b) { return empty_row ? 0.f : grid.lam2 * grid.gmax * bnd[b] * 1.0001f; },
+                lane);
+            posterior_eval(grid, pr, cmax, cs, ubs, ub_b,
+                           [&]() {  // rare fallback: C again, in the same order
+                               int n2 = 0;
+                               bool b2 = false;
+                               corr_photon_list(gs, pbins, K, T, cs, nullptr, NB, D, L, u0, lane, n2, b2);
+                           },
+                           lane, bidx, mu, var);
             if (lane == 0) {
                 f.mu_out[p] = mu;
                 f.var_out[p] = var;
@@ -231,10 +221,7 @@ __global__ void __launch_bounds__(256) k_noalloc_batch(const spl_seq_desc* __res
                     float* zwin = cs;
                     for (int j = lane; j < SPL_MAX_TAPS; j += 32) zwin[j] = 0.f;
                     __syncwarp();
-                    for (int k = lane; k < nk; k += 32) {
-                        const int j = ph[k] - t0;
-                        if (j >= 0 && j < L) atomicAdd(&zwin[j], 1.f);
-                    }
+                    window_photons(pbins, K, T, t0, L, zwin, lane);
                     __syncwarp();
                     float zj[SPL_MAX_TAPS / 32], aj[SPL_MAX_TAPS / 32];
 #pragma unroll

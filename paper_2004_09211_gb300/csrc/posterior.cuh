@@ -1,12 +1,10 @@
-// Pseudo-posterior moments on the integer depth grid, shared by the histogram kernel (estimate.cu), the photon-list
-// kernels (batch.cu, noalloc.cu) and the multispectral kernel (msl.cu):
+// Pseudo-posterior moments on the integer depth grid, shared by the histogram kernels (estimate.cu), the photon-list
+// kernels (batch.cu, noalloc.cu; their data term is in photons.cuh) and the multispectral kernel (msl.cu):
 //
 //   block_bounds    per-block upper bounds of the log pseudo-posterior (the data part supplied by the caller).
 //   posterior_eval  Eq. approx_post + Eq. KL_div: argmax, mean and variance of the pseudo-posterior on the
 //                   integer grid, from C(d) already in shared memory, with bound-based block pruning and the
 //                   linear-domain evaluation described below.
-//   posterior       the two together, with the photon-count data bound of the photon-list kernels.
-//   corr_photons    C(d) from a photon list (the photon-sum form of Eq. beta_div2).
 //
 // Pruning. Candidates are grouped in blocks of 32. Each block gets an upper bound of ell = lambda log2(e) C(d)
 // + log2 f(d): an upper bound of the data part (lambda log2(e) max(g) times the photons in the block's window, or
@@ -28,7 +26,6 @@
 #pragma once
 
 #include "pixel.cuh"
-#include "spl.h"
 
 namespace spl {
 namespace px {
@@ -83,36 +80,6 @@ __device__ __forceinline__ void lin_run(const Grid& g, const Prior& pr, float* c
             dd += 1.f;
         }
     }
-}
-
-// C over every candidate from a pixel's photon list (the photon-sum form of Eq. beta_div2; used by the photon-list
-// kernels of batch.cu and noalloc.cu), lane = tap: lane l
-// owns taps l + 32 k, and each photon y in list order adds g_j to candidate y - u0 - j for its taps. The
-// candidates of one photon are distinct across lanes and taps and the warp synchronises between photons, so
-// each C(d) is summed in photon order. Returns max C.
-__device__ __forceinline__ float corr_photons(const float* __restrict__ gs, const int* ph, int nk, float* cs, int NB,
-                                             int D, int L, int u0, int lane) {
-    constexpr int KG = SPL_MAX_TAPS / 32;
-    zero_words(cs, NB * 8, lane);
-    float g[KG];
-#pragma unroll
-    for (int k = 0; k < KG; ++k) g[k] = gs[lane + 32 * k];
-    const int ntg = (L + 31) >> 5;
-    float mx = 0.f;
-    for (int e = 0; e < nk; ++e) {
-        const int c = ph[e] - u0 - lane;
-#pragma unroll
-        for (int k = 0; k < KG; ++k) {
-            const int ck = c - 32 * k;
-            if (k < ntg && static_cast<unsigned>(ck) < static_cast<unsigned>(D)) {
-                const float v = cs[ck] + g[k];
-                cs[ck] = v;
-                mx = fmaxf(mx, v);
-            }
-        }
-        __syncwarp();
-    }
-    return warp_max(mx);
 }
 
 // Per-block upper bounds of ell = lambda log2(e) C(d) + log2 f(d) into ubs[0 .. NB): dub(b) is an upper bound of
@@ -272,23 +239,6 @@ __device__ __forceinline__ void posterior_eval(const Grid& g, const Prior& pr, f
     bidx_out = bidx;
     mu_out = static_cast<float>(g.dmin + bidx) + m1;
     var_out = fmaxf(s2 / s0 - m1 * m1, 0.f);
-}
-
-// The photon-list kernels' form: C already on every candidate (cmax its maximum, empty: no photons); count(s, e)
-// returns an upper bound of the photons in bins [s, e] (evaluated per lane).
-template <class Count, class Restore>
-__device__ __forceinline__ void posterior(const Grid& g, const Prior& pr, float cmax, bool empty, float* cs,
-                                          float* ubs, Count count, Restore restore, int lane, int& bidx_out,
-                                          float& mu_out, float& var_out) {
-    const int ub_b = block_bounds(
-        g, pr, ubs,
-        [&](int b) {
-            const int last = min(32 * b + 31, g.D - 1);
-            const float nb = empty ? 0.f : count(g.u0 + 32 * b, g.u0 + last + g.L - 1);
-            return g.lam2 * g.gmax * nb * 1.0001f;
-        },
-        lane);
-    posterior_eval(g, pr, cmax, cs, ubs, ub_b, restore, lane, bidx_out, mu_out, var_out);
 }
 
 }  // namespace px
