@@ -227,7 +227,9 @@ SPL_API spl_status spl_filter_step_fp32(const spl_params* prm, const spl_hist* z
  *   absent, refl = bg = 0 (Sec. III-B).
  *   Arguments as spl_filter_step, with present_now replaced by pi0; outputs argmax (required here), pi [P]
  *   float (required), present_out [P] uint8 (nullable: 1 where pi > 0.5, usable as the next frame's
- *   present_in), refl and bg (required). pi must not alias pi0.
+ *   present_in), refl and bg (required). pi must not alias pi0. The depth step's arithmetic is that of
+ *   spl_filter_step (uint16 histograms on the tensor cores, other formats on the FP32 kernel); the presence
+ *   decision is made in the intensity launch that follows either.
  */
 SPL_API spl_status spl_filter_step_detect(const spl_params* prm, const spl_hist* z, const float* h,
                                           const float* mu_in, const float* var_in, const uint8_t* present_in,

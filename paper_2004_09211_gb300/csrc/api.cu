@@ -117,6 +117,20 @@ EstimateArgs base_args(const spl_params* q, const spl_hist* z, const float* h) {
 namespace spl {
 namespace {
 
+// Launches one filter step: uint16 histograms through the tensor-core kernel when tc is set (its redo and intensity
+// launches follow), falling back to the FP32 kernel only for a shape the tensor-core kernel cannot hold (nothing is
+// launched then); every other format through the FP32 kernel.
+spl_status launch_step(const EstimateArgs& a, cudaStream_t s, bool tc, const char* what) {
+    if (tc && a.fmt == SPL_HIST_U16) {
+        unsigned* status = tc_status_ptr();
+        SPL_REQUIRE(status != nullptr, "no device status word (no CUDA device?)");
+        const cudaError_t e = launch_filter_tc(a, status, s);
+        if (e != cudaErrorInvalidConfiguration) return cuda_status(e, what);
+        cudaGetLastError();  // nothing was launched: clear the configuration error, take the FP32 kernel
+    }
+    return cuda_status(launch_estimate(a, false, s), what);
+}
+
 // The filter step of spl_filter_step / spl_filter_step_fp32: uint16 histograms on the tensor cores when tc is set
 // (falling back to the FP32 kernel only for a shape the tensor-core kernel cannot hold), else the FP32 kernel.
 spl_status filter_step(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
@@ -144,15 +158,7 @@ spl_status filter_step(const spl_params* prm, const spl_hist* z, const float* h,
     a.var = var_out;
     a.refl = refl;
     a.bg = bg;
-    const cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (tc && z->fmt == SPL_HIST_U16) {
-        unsigned* status = tc_status_ptr();
-        SPL_REQUIRE(status != nullptr, "no device status word (no CUDA device?)");
-        const cudaError_t e = launch_filter_tc(a, status, s);
-        if (e != cudaErrorInvalidConfiguration) return cuda_status(e, "spl_filter_step launch");
-        cudaGetLastError();  // nothing was launched: clear the configuration error, take the FP32 kernel
-    }
-    return cuda_status(launch_estimate(a, false, s), "spl_filter_step launch");
+    return launch_step(a, static_cast<cudaStream_t>(stream), tc, "spl_filter_step launch");
 }
 
 }  // namespace
@@ -337,7 +343,7 @@ spl_status spl_filter_step_detect(const spl_params* prm, const spl_hist* z, cons
     a.pi0 = pi0;
     a.pi_out = pi;
     a.present_out = present_out;
-    return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_filter_step_detect launch");
+    return launch_step(a, static_cast<cudaStream_t>(stream), true, "spl_filter_step_detect launch");
 }
 
 spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
