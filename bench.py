@@ -55,16 +55,16 @@ TRAFFIC_CAPTURES = {
     # runs (nine captures of one launch each, mean) plus the intensity launch (mean of the same nine frames)
     # (ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum)
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "posterior.cuh", "intensity.cu"),
-                   "sha256": "3360ba4d0c9c713162f8fa1b90b9e08fb21ec6f1ebc55fce92aee98be64e9a8f",
-                   "bytes_per_pixel": (201.24e6 + 15.52e6) / 65536,
+                   "sha256": "5bae563cc5ba802d1c6630c86231778757af44605e34d5c7708197c4392920eb",
+                   "bytes_per_pixel": (201.16e6 + 15.52e6) / 65536,
                    "inst_per_pixel": (368.24e6 + 14.85e6) / 65536},
     # one uint16 filter step of the video job (spl_filter_step): the tensor-core launch, the redo launch and the
     # intensity launch of frame 1 of each of the nine runs (mean)
     "k_filter_tc_u16": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh", "estimate.cu",
                                     "posterior.cuh"),
-                        "sha256": "dbc276ca433594cc7faba76ed94c44fd51640e9cb2eb12f659577ed2db8dca72",
-                        "bytes_per_pixel": 221.73e6 / 65536,
-                        "inst_per_pixel": 151.59e6 / 65536},
+                        "sha256": "2d0309315ca0a597401844aec69788500c655c436f5c3fa694ba5fdbc275c561",
+                        "bytes_per_pixel": 221.70e6 / 65536,
+                        "inst_per_pixel": 151.60e6 / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh"),
                     "sha256": "822e47827c851ef9b23f136f85cc5ce229ada120d82354fe8333713ec4feffe6",
                     "bytes_per_pixel": (537.633e6 + 3.613e6 + 17.199e6) / 65536,
