@@ -1153,15 +1153,18 @@ def pd_curves(args):
     peaks = _peaks()
     launch_s = ms / len(PD_BETAS) / 1e3
     roofline = hbm_roofline(peaks, P * (2 * PD_T + 8 + 12), launch_s, None,
-                            "k_estimate<u16> (one spl_depth_estimate over all cells of one beta)",
+                            "k_filter_tc<u16> + k_estimate_redo (one spl_depth_estimate over all cells of one beta)",
                             note="traffic not captured for this workload")
     line = {"metric": "pixel-estimates/s", "value": P * len(PD_BETAS) / (ms / 1e3), "unit": "pixel-estimates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16 counts -> f16 on chip (exact below 1024) x f16 hi/lo taps -> f32 (tensor); f32 epilogue",
+            "data": "synthetic",
             "config": {"workload": "single-pixel p_d experiment (Sec. IV-A, Gaussian IRF FWHM 28, T=1500, prior "
                                    "N(600, 2500), eta 28): 25 SBR x 13 MSC x 2000 histograms per beta",
                        "sbr_grid": sbr.tolist(), "msc_grid": msc.tolist(), "betas": list(PD_BETAS), "pixels": P},
-            "curves": out, "gpu_launches": len(PD_BETAS) * args.steps, "clocks": clk.summary(),
+            # per call: the tensor-core depth launch and the redo scan (no intensity)
+            "curves": out, "gpu_launches": 2 * len(PD_BETAS) * args.steps, "clocks": clk.summary(),
             "roofline": roofline, "e2e": None}
     print(json.dumps(line), flush=True)
 

@@ -124,6 +124,10 @@ SPL_API spl_status spl_tc_status(uint32_t* flags);
  *   estimate under Eq. lik_bg_poisson with the template at round-half-even(mu). present may be NULL
  *   (every pixel present).
  *   prior_var must be > 0 where given.
+ *   Arithmetic as spl_filter_step: uint16 frames of at least 128 pixels per SM on the tensor cores (counts
+ *   converted to FP16 on chip, exact below 1024; a 128-pixel block with a larger count, or a pixel whose data term
+ *   exceeds 1024 bits, goes to the FP32 kernel), other frames on the FP32 kernel; a bounded wait of the
+ *   tensor-core kernel that runs out sets flag 1 of spl_tc_status.
  */
 SPL_API spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, const float* h, const float* prior_mu,
                               const float* prior_var, const uint8_t* present, int32_t* argmax, float* mu,
@@ -183,14 +187,16 @@ SPL_API spl_status spl_depth_estimate_msl(const spl_params* prm, int nbands, con
  *   as in spl_depth_estimate. present_in, faulty, present_now may be NULL (all present / none faulty).
  *   argmax, refl, bg are nullable (refl and bg both or neither). Faulty pixels get refl = bg = 0.
  *   mu_out/var_out must not alias mu_in/var_in (neighbours read the previous frame); use two buffers.
- *   Arithmetic. With uint16 histograms (SPL_HIST_U16) the data term C(d) is formed on the tensor cores as in
- *   spl_filter_step_tc: each landed tile of counts is converted to FP16 on chip (exact: counts below 1024),
- *   the taps h^beta are split into high and low FP16 parts (about 22 significant bits) and the products are
- *   accumulated in FP32; the rest is FP32. A 128-pixel block holding a count of 1024 or more is computed
- *   instead by the FP32 kernel of spl_filter_step_fp32, in a second launch that reads the same inputs. A
- *   bounded internal wait of the tensor-core kernel that runs out sets flag 1 of spl_tc_status (the outputs
- *   are then incomplete). FP16 and FP32 histograms go through the FP32 kernel. The results meet the same
- *   tolerances against the FP64 definition either way (1e-4 relative on mu, var, refl, bg).
+ *   Arithmetic. uint16 histograms (SPL_HIST_U16) of at least 128 pixels per SM (19456 on a 152-SM GPU) go
+ *   through the tensor cores as in spl_filter_step_tc: each landed tile of counts is converted to FP16 on chip
+ *   (exact: counts below 1024), the taps h^beta are split into high and low FP16 parts (about 22 significant
+ *   bits) and the products are accumulated in FP32; the rest is FP32. A 128-pixel block holding a count of 1024
+ *   or more, and a pixel whose data term lambda log2(e) max C exceeds 1024 bits (beyond it the tensor cores'
+ *   rounding bound on ell passes 1e-3 bits), are computed instead by the FP32 kernel of spl_filter_step_fp32, in
+ *   a second launch that reads the same inputs. A bounded internal wait of the tensor-core kernel that runs out
+ *   sets flag 1 of spl_tc_status (the outputs are then incomplete). Smaller frames, and FP16 and FP32
+ *   histograms, go through the FP32 kernel. The results meet the same tolerances against the FP64 definition
+ *   either way (1e-4 relative on mu, var, refl, bg).
  */
 SPL_API spl_status spl_filter_step(const spl_params* prm, const spl_hist* z, const float* h, const float* mu_in,
                            const float* var_in, const uint8_t* present_in, const uint8_t* faulty,
@@ -228,7 +234,7 @@ SPL_API spl_status spl_filter_step_fp32(const spl_params* prm, const spl_hist* z
  *   Arguments as spl_filter_step, with present_now replaced by pi0; outputs argmax (required here), pi [P]
  *   float (required), present_out [P] uint8 (nullable: 1 where pi > 0.5, usable as the next frame's
  *   present_in), refl and bg (required). pi must not alias pi0. The depth step's arithmetic is that of
- *   spl_filter_step (uint16 histograms on the tensor cores, other formats on the FP32 kernel); the presence
+ *   spl_filter_step (large uint16 frames on the tensor cores, other frames on the FP32 kernel); the presence
  *   decision is made in the intensity launch that follows either.
  */
 SPL_API spl_status spl_filter_step_detect(const spl_params* prm, const spl_hist* z, const float* h,
@@ -255,7 +261,8 @@ SPL_API spl_status spl_pi_propagate(const spl_params* prm, const float* pi_in, c
 
 /*
  * spl_filter_step_tc -- spl_filter_step (one outer iteration of Algorithm 1) with the data term on the tensor
- *   cores, for FP16 histograms (SPL_HIST_F16; integer counts up to 2048 are exact). Same arguments, outputs and
+ *   cores at any frame size, for FP16 histograms (SPL_HIST_F16; integer counts up to 2048 are exact) or uint16
+ *   histograms (the conversion, redo and accuracy rule of spl_filter_step's uint16 route). Same arguments, outputs and
  *   rules as spl_filter_step. C(d) (Eq. beta_div2) is formed as in spl_depth_cost_tc (FP16 operands, the taps
  *   h^beta scaled by 2^15 and split into high and low FP16 parts, FP32 accumulation: about 22 significant bits
  *   per tap) and consumed on chip: no per-candidate value is written to memory. The photon count K of each

@@ -117,11 +117,23 @@ EstimateArgs base_args(const spl_params* q, const spl_hist* z, const float* h) {
 namespace spl {
 namespace {
 
-// Launches one filter step: uint16 histograms through the tensor-core kernel when tc is set (its redo and intensity
-// launches follow), falling back to the FP32 kernel only for a shape the tensor-core kernel cannot hold (nothing is
-// launched then); every other format through the FP32 kernel.
+// Pixels from which the automatic entries take uint16 frames to the tensor cores: one 128-pixel block per SM. A
+// smaller frame leaves most SMs idle in the block-per-CTA tensor-core kernel, where the warp-per-pixel FP32 kernel
+// still spreads it (a 32x32 frame: 29 us against 59 us, measured).
+long long tc_min_pixels() {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 1LL << 62;
+    return 128LL * nsm;
+}
+
+// Launches one step of spl_filter_step, spl_filter_step_detect or spl_depth_estimate: uint16 frames of at least
+// tc_min_pixels() through the tensor-core kernel when tc is set (its redo and intensity launches follow), falling
+// back to the FP32 kernel only for a shape the tensor-core kernel cannot hold (nothing is launched then); every
+// other frame through the FP32 kernel.
 spl_status launch_step(const EstimateArgs& a, cudaStream_t s, bool tc, const char* what) {
-    if (tc && a.fmt == SPL_HIST_U16) {
+    if (tc && a.fmt == SPL_HIST_U16 && static_cast<long long>(a.H) * a.W >= tc_min_pixels()) {
         unsigned* status = tc_status_ptr();
         SPL_REQUIRE(status != nullptr, "no device status word (no CUDA device?)");
         const cudaError_t e = launch_filter_tc(a, status, s);
@@ -232,7 +244,7 @@ spl_status spl_depth_estimate(const spl_params* prm, const spl_hist* z, const fl
     a.refl = refl;
     a.bg = bg;
     a.present_now = present;
-    return cuda_status(launch_estimate(a, false, static_cast<cudaStream_t>(stream)), "spl_depth_estimate launch");
+    return launch_step(a, static_cast<cudaStream_t>(stream), true, "spl_depth_estimate launch");
 }
 
 spl_status spl_depth_estimate_msl(const spl_params* prm, int nbands, const spl_hist* z, const float* h,
@@ -354,7 +366,8 @@ spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, const fl
     spl_status st = check_params(prm, true);
     if (st != SPL_OK) return st;
     if ((st = check_hist(prm, z)) != SPL_OK) return st;
-    SPL_REQUIRE(z->fmt == SPL_HIST_F16, "spl_filter_step_tc takes FP16 histograms (SPL_HIST_F16)");
+    SPL_REQUIRE(z->fmt == SPL_HIST_F16 || z->fmt == SPL_HIST_U16,
+                "spl_filter_step_tc takes FP16 or uint16 histograms (SPL_HIST_F16, SPL_HIST_U16)");
     SPL_REQUIRE(h != nullptr, "h is NULL");
     SPL_REQUIRE(mu_in && var_in && mu_out && var_out, "mu_in, var_in, mu_out and var_out are required");
     SPL_REQUIRE(mu_out != mu_in && var_out != var_in && mu_out != var_in && var_out != mu_in,

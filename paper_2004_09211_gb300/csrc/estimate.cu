@@ -539,8 +539,9 @@ __global__ void __launch_bounds__(256) k_estimate(const EstimateArgs a) {
 // Pixels set aside by the tensor-core filter step on uint16 histograms
 // ------------------------------------------------------------------------------------------------------------
 
-// The tensor-core kernel converts uint16 counts to FP16 exactly only below 1024; a 128-pixel block holding a
-// larger count gets mu = NaN instead of its results. This kernel computes those pixels again with the steps of
+// The tensor-core kernel (uint16 frames of spl_filter_step, spl_filter_step_detect and spl_depth_estimate) converts
+// uint16 counts to FP16 exactly only below 1024; a 128-pixel block holding a larger count gets mu = NaN instead of
+// its results. This kernel computes those pixels again with the steps of
 // k_estimate (without its prefetching: the case is rare), one warp per pixel. A warp tests the mu of 32
 // consecutive pixels at once and takes the marked ones in turn; a CTA whose pixels hold no mark returns before
 // any set-up, so a frame with none costs one load per pixel.
@@ -615,9 +616,15 @@ __global__ void __launch_bounds__(256) k_estimate_redo(const EstimateArgs a) {
                 cmax = corr_dense<FMT>(gs, raw, cs, D, L, u0, lane);
             }
             Prior pr;
-            {
+            {  // as k_estimate: the filter step's stencil (Eq. predict), one Gaussian, or the flat prior
                 float w = 0.f, m = 0.f, v = 1.f;
-                if (lane < 9) {  // the filter step's prior (Eq. predict)
+                if (a.prior_mode == PRIOR_GAUSS) {
+                    if (lane == 0) {
+                        w = 1.f;
+                        m = nb.m;
+                        v = nb.v;
+                    }
+                } else if (a.prior_mode == PRIOR_STENCIL && lane < 9) {
                     w = a.nu[lane];
                     m = nb.info ? nb.m : a.flat_m;
                     v = (nb.info ? nb.v : a.flat_v) + a.sigma_rw2;

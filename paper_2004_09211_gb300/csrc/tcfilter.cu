@@ -23,9 +23,10 @@
 //             into running (weight, mean, second central moment) with a shared exponent reference, the chunk's
 //             own moments taken about its best candidate (the pairwise update of Chan, Golub and LeVeque), so
 //             no step subtracts large nearly equal numbers.
-//     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax; the photon count K goes to bg. A
-//             uint16 block holding a count of 1024 or more gets mu = NaN instead: FP16 would not carry its counts
-//             exactly, and the FP32 kernel computes those pixels again (k_estimate_redo, estimate.cu).
+//     output  mu = mean, var = second moment / weight (Eq. KL_div), argmax; the photon count K goes to bg. With
+//             uint16 input a block holding a count of 1024 or more (FP16 would not carry it exactly), and a pixel
+//             whose data term exceeds kTcMaxBits, get mu = NaN instead, and the FP32 kernel computes them again
+//             (k_estimate_redo, estimate.cu).
 // A second launch (intensity.cu) then runs the intensity MLE of Sec. II-E on the template at round-half-even(mu)
 // with that K and writes refl and bg.
 // All mbarrier waits are bounded (status bit 0 on time-out; the roles then stop, in-flight copies and MMAs are
@@ -61,17 +62,39 @@ constexpr unsigned kOnesBytes = 16 * kSlab * 2;  // 2 KB
 constexpr uint32_t kIdescTile = idesc_f16(kM, kN);
 constexpr uint32_t kIdescCnt = idesc_f16(kM, 16);
 constexpr float kPrune = px::kPrune2;            // log2 margin below the running maximum
+// uint16 input: largest data term lambda log2(e) max C (bits) a pixel keeps on the tensor cores. C here carries the
+// taps' 2^-23 relative residual and FP32 accumulation over at most 16 rounded steps, |dC| <= 2^-19.8 max C, so ell
+// stays within 1e-3 bits of its exact value below this; a brighter pixel is computed by the FP32 kernel.
+constexpr float kTcMaxBits = 1024.f;
 
 struct TcGeom {
     int a0, delta, kw, ntiles, nslab, mlead, S, npt, ring, nbs;
     float lam2s;  // lambda log2(e) 2^-15 (the accumulators hold C * 2^15)
 };
 
-// Eq. predict for one pixel, one thread: stencil entry k contributes N(mu_in, var_in + sigma_rw2) when the
-// neighbour is inside the frame, present and not faulty, else the weakly informative Gaussian; entries with
-// nu_k = 0 are unused. Entries with bitwise equal (mean, variance) are merged by adding their weights in stencil
-// order, then the used ones are packed to the front in stencil order.
+// The prior of one pixel, one thread. The filter step (PRIOR_STENCIL), Eq. predict: stencil entry k contributes
+// N(mu_in, var_in + sigma_rw2) when the neighbour is inside the frame, present and not faulty, else the weakly
+// informative Gaussian; entries with nu_k = 0 are unused. Entries with bitwise equal (mean, variance) are merged by
+// adding their weights in stencil order, then the used ones are packed to the front in stencil order. A single
+// frame: one Gaussian N(pmu[p], pvar[p]) (PRIOR_GAUSS), or the flat prior (PRIOR_UNIFORM) as one component with
+// k = 0, whose value 2^0 is the same at every depth (its recurrence ratios are 1).
 __device__ __forceinline__ void prior_thread(const EstimateArgs& a, long long p, Prior& pr, bool& faulty) {
+    if (a.prior_mode != PRIOR_STENCIL) {
+        const bool gauss = a.prior_mode == PRIOR_GAUSS;
+        const float v = gauss ? a.pvar[p] : 1.f;
+        pr.n = 1;
+        pr.ca[0] = gauss ? -0.5f * (px::kLog2TwoPi + lg2(v)) : 0.f;
+        pr.ck[0] = gauss ? px::kLog2e / (2.f * v) : 0.f;
+        pr.cm[0] = gauss ? a.pmu[p] : 0.f;
+        pr.minv = gauss ? v : INFINITY;
+#pragma unroll
+        for (int i = 1; i < px::kMaxComp; ++i) {
+            pr.ca[i] = -INFINITY;
+            pr.ck[i] = pr.cm[i] = 0.f;
+        }
+        faulty = a.faulty ? a.faulty[p] != 0 : false;
+        return;
+    }
     const int y = static_cast<int>(p / a.W), x = static_cast<int>(p - static_cast<long long>(y) * a.W);
     float w[9], m[9], v[9];
 #pragma unroll
@@ -182,6 +205,7 @@ struct Moments {
     float top;    // max(lower bound, largest ell evaluated), absolute log2 units
     float best;   // largest ell evaluated
     int bidx;     // its candidate index (smallest on ties)
+    float amax;   // largest raw accumulator seen on any tile
 };
 
 // Merges one chunk's sums (s0 = sum u, s1 = sum u x, s2 = sum u x^2 with x = candidate - ctr, weights u
@@ -375,6 +399,7 @@ __device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmi
 #pragma unroll
             for (int i = 0; i < 16; ++i) cm = fmaxf(cm, c[i]);
         }
+        st.amax = fmaxf(st.amax, cm);
         alive = valid && fmaf(l2s, cm, lpt) >= st.top - kPrune;
     }
     if (!__any_sync(0xffffffffu, alive)) return;
@@ -388,6 +413,7 @@ __device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmi
             float cq = c[0];
 #pragma unroll
             for (int i = 1; i < 16; ++i) cq = fmaxf(cq, c[i]);
+            st.amax = fmaxf(st.amax, cq);
             if (fmaf(l2s, cq, lpt) >= st.top - kPrune) {
                 bool done = false;
                 if (lin_ok)
@@ -637,6 +663,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             st.W = st.mu = st.M2 = 0.f;
             st.best = -INFINITY;
             st.bidx = 0;
+            st.amax = 0.f;
             const bool lin_ok = !(pr.minv < 1.5f);
             for (int t = 0; t < g.ntiles; ++t, ++tcount) {
                 const unsigned acc = tcount & 1u, use = tcount >> 1;
@@ -675,6 +702,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             __syncwarp();
             if (lane == 0) mbar_arrive(cnte0 + 8 * (blk & 1u));
             // outputs; the photon count goes to bg, where the intensity launch reads it
+            if (U16 && l2s * st.amax > kTcMaxBits) redo = 1;  // beyond the tensor cores' accuracy bound
             if (valid) {
                 if (redo) {
                     a.mu[p] = NAN;  // k_estimate_redo computes this pixel again

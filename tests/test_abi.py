@@ -130,19 +130,20 @@ def test_batch_argument_checks():
 
 
 def test_tensor_core_argument_checks():
-    """spl_depth_cost_tc / spl_filter_step_tc take FP16 histograms only and check the filter arguments like
-    spl_filter_step, all on the host."""
+    """spl_depth_cost_tc takes FP16 histograms only, spl_filter_step_tc FP16 or uint16 ones; both check the filter
+    arguments like spl_filter_step, all on the host."""
     lib = _abi.load()
     prm = make_params(4, 4, 64, 25, 12)
     hz_u16 = _abi.spl_hist(_abi.SPL_HIST_U16, 0x1000, 64)
     hz_f16 = _abi.spl_hist(_abi.SPL_HIST_F16, 0x1000, 64)
+    hz_f32 = _abi.spl_hist(_abi.SPL_HIST_F32, 0x1000, 64)
     st = lib.spl_depth_cost_tc(ct.byref(prm), ct.byref(hz_u16), 0x2000, 0x3000, None, None)
     assert st == _abi.SPL_EINVAL and "FP16" in lib.spl_last_error().decode()
     st = lib.spl_depth_cost_tc(ct.byref(prm), ct.byref(hz_f16), 0x2000, None, None, None)
     assert st == _abi.SPL_EINVAL and "nothing to compute" in lib.spl_last_error().decode()
-    st = lib.spl_filter_step_tc(ct.byref(prm), ct.byref(hz_u16), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
+    st = lib.spl_filter_step_tc(ct.byref(prm), ct.byref(hz_f32), 0x2000, 0x3000, 0x4000, None, None, None, 0x5000,
                                 0x6000, None, None, None, None)
-    assert st == _abi.SPL_EINVAL and "FP16" in lib.spl_last_error().decode()
+    assert st == _abi.SPL_EINVAL and "FP16 or uint16" in lib.spl_last_error().decode()
     st = lib.spl_filter_step_tc(ct.byref(prm), ct.byref(hz_f16), 0x2000, 0x3000, 0x4000, None, None, None, 0x3000,
                                 0x6000, None, None, None, None)
     assert st == _abi.SPL_EINVAL and "alias" in lib.spl_last_error().decode()

@@ -6,8 +6,9 @@ next frame's prior (Eq. predict), so FP32 rounding could accumulate along the se
 states are compared at the filter's tolerances (relative 1e-4; variance floor 1e-6 bins^2), and the largest
 relative difference over the whole sequence is printed (run with -s).
 
-Both arithmetic paths of the filter step run the chain: spl_filter_step (uint16 histograms: the data term on the
-tensor cores) and spl_filter_step_fp32 (the FP32 CUDA-core kernel), each against the same oracle chain.
+Both arithmetic paths of the filter step run the chain: spl_filter_step_tc on the uint16 histograms (the data term
+on the tensor cores, the route spl_filter_step takes for large frames) and spl_filter_step_fp32 (the FP32 CUDA-core
+kernel), each against the same oracle chain.
 
 Two regimes, 3000 frames each, 8 x 8 pixels, the 48-tap asymmetric IRF, beta = 0.5, sigma_RW^2 = 3, the cross
 weights with nu0 = 0.5:
@@ -67,7 +68,7 @@ def test_long_sequence_drift(orc, T, signal, sbr, seed):
     zd = synth.pitched(torch.from_numpy(z.reshape(N, P, T).astype(np.int32)).to(torch.uint16), pitch).to(DEV)
     hd = torch.from_numpy(h).to(DEV)
     chains = {}
-    for name, step in (("tensor-core route", spl.spl_filter_step), ("FP32 kernel", spl.spl_filter_step_fp32)):
+    for name, step in (("tensor-core route", spl.spl_filter_step_tc), ("FP32 kernel", spl.spl_filter_step_fp32)):
         mus = torch.empty(N + 1, P, device=DEV)
         vars_ = torch.empty(N + 1, P, device=DEV)
         spl.spl_state_init(prm, mus[0], vars_[0])

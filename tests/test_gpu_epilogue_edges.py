@@ -128,7 +128,7 @@ def test_recentred_sums(orc, beta):
     _compare(q, e, o)
 
 
-@pytest.mark.parametrize("entry", ["spl_filter_step", "spl_filter_step_fp32"])
+@pytest.mark.parametrize("entry", ["spl_filter_step_tc", "spl_filter_step_fp32"])
 @pytest.mark.parametrize("nu0,diag", [(0.5, 0.0), (0.4, 0.02)])
 def test_mixture_priors(orc, nu0, diag, entry):
     """One filter step from given states, on the tensor-core route and on the FP32 kernel: 3 x 3 stencils of up to

@@ -1,11 +1,14 @@
-"""The uint16 route of spl_filter_step: the data term on the tensor cores with the counts converted to FP16 on
-chip (exact below 1024), and 128-pixel blocks that hold a larger count computed again by the FP32 kernel.
+"""The uint16 route of the filter step: the data term on the tensor cores with the counts converted to FP16 on
+chip (exact below 1024); 128-pixel blocks that hold a larger count, and pixels whose data term exceeds the tensor
+cores' accuracy bound, computed again by the FP32 kernel. spl_filter_step_tc takes it at any frame size;
+spl_filter_step, spl_filter_step_detect and spl_depth_estimate from one 128-pixel block per SM upward.
 
-Checks: without such counts the route equals spl_filter_step_tc on FP16 copies of the same frames bit for bit
-(the conversion is exact and the kernel the same); a block holding a count of 1024 or more equals
-spl_filter_step_fp32 bit for bit (the FP32 kernel computed it), every other block stays on the tensor cores; a
-block whose largest count is 1023 stays on the tensor cores and still matches the oracle; everything matches the
-FP64 oracle at the filter's tolerances (tests/parity.py), including a ragged last block."""
+Checks: without such counts the uint16 route equals spl_filter_step_tc on FP16 copies of the same frames bit for
+bit (the conversion is exact and the kernel the same); a block holding a count of 1024 or more, and a pixel past
+the accuracy bound, equal spl_filter_step_fp32 bit for bit (the FP32 kernel computed them), every other block
+stays on the tensor cores; a block whose largest count is 1023 stays on the tensor cores and still matches the
+oracle; spl_filter_step picks the tensor cores for a large frame and the FP32 kernel for a small one; everything
+matches the FP64 oracle at the filter's tolerances (tests/parity.py), including a ragged last block."""
 import numpy as np
 import pytest
 import torch
@@ -43,7 +46,7 @@ def test_route_equals_the_fp16_kernel_bit_for_bit():
     h, peak, sc, zs = video_inputs(H, W, N, T, 0.02, seed=71)
     assert max(float(z.max()) for z in zs) < 1024
     prm = spl.make_params(H, W, T, len(h), peak, beta=0.4, sigma_rw2=3.0)
-    a = _steps(prm, h, zs, T, spl.spl_filter_step)
+    a = _steps(prm, h, zs, T, spl.spl_filter_step_tc)
     b = _steps(prm, h, zs, T, spl.spl_filter_step_tc, torch.float16)
     for n in range(N):
         for k in KEYS:
@@ -79,7 +82,7 @@ def test_blocks_with_large_counts_are_redone_in_fp32(orc):
     mu, var = spl.spl_state_init(prm)
     for n in range(N):
         zt = _gpu_hist(zs[n], T)
-        a = spl.spl_filter_step(prm, zt, hd, mu, var)
+        a = spl.spl_filter_step_tc(prm, zt, hd, mu, var)
         f = spl.spl_filter_step_fp32(prm, zt, hd, mu, var)
         e = orc.filter_step(q, h, zs[n], _np(mu).reshape(H, W).astype(np.float64),
                             _np(var).reshape(H, W).astype(np.float64), want_ell=True)
@@ -111,7 +114,7 @@ def test_route_on_a_single_pixel_and_long_histograms(orc):
     zs[1][0, 0, 5000:5048] += 30
     prm = spl.make_params(1, 1, T, len(hh), peak, beta=0.7, sigma_rw2=3.0)
     q = orc.params(T, len(hh), peak, beta=0.7, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
-    a = _steps(prm, hh, zs, T, spl.spl_filter_step)
+    a = _steps(prm, hh, zs, T, spl.spl_filter_step_tc)
     mu_o, var_o = orc.state_init(q, 1, 1)
     for n in range(2):  # each frame from the route's own previous state
         e = orc.filter_step(q, hh, zs[n], mu_o, var_o, want_ell=True)
@@ -119,4 +122,58 @@ def test_route_on_a_single_pixel_and_long_histograms(orc):
         check_close(a[n]["mu"], e["mu"], "mu")
         check_close(a[n]["var"], e["var"], "var", atol=1e-6)
         mu_o, var_o = a[n]["mu"].reshape(1, 1).astype(np.float64), a[n]["var"].reshape(1, 1).astype(np.float64)
+    _status_clear()
+
+
+def test_bright_pixels_leave_the_tensor_cores(orc):
+    """1000 photons in each of 79 consecutive bins at beta = 0.1: the data term lambda log2(e) C is about 8.7e5 bits,
+    far past the 1024 the tensor cores keep, so these pixels go to the FP32 kernel and equal it bit for bit (a
+    plateau of exactly equal C, which the FP32 kernel's identical operand order reproduces); the photon-starved
+    pixels beside them agree with the FP32 kernel within the tolerances. Everything matches the oracle."""
+    hh, peak = synth.asymmetric_irf(L=48)
+    H, W, T = 4, 8, 600
+    rng = np.random.default_rng(74)
+    z = rng.poisson(0.01, size=(H, W, T)).astype(np.float64)
+    bright = [(0, 1, 100), (1, 3, 250), (2, 6, 400), (3, 2, 130)]
+    for y, x, s0 in bright:
+        z[y, x, s0:s0 + 79] = 1000.0
+    beta = 0.1
+    prm = spl.make_params(H, W, T, len(hh), peak, beta=beta, sigma_rw2=3.0)
+    q = orc.params(T, len(hh), peak, beta=beta, sigma_rw2=3.0, nu=synth.cross_weights(0.5))
+    hd = torch.from_numpy(hh).to(DEV)
+    mu, var = spl.spl_state_init(prm)
+    zt = _gpu_hist(z, T)
+    a = spl.spl_filter_step_tc(prm, zt, hd, mu, var)
+    f = spl.spl_filter_step_fp32(prm, zt, hd, mu, var)
+    torch.cuda.synchronize()
+    ga = {k: _np(a[k]) for k in KEYS}
+    gf = {k: _np(f[k]) for k in KEYS}
+    for y, x, _ in bright:
+        p = y * W + x
+        for k in KEYS:
+            assert ga[k][p] == gf[k][p], f"pixel {p}: {k} is not the FP32 result"
+    check_close(ga["mu"], gf["mu"], "mu route vs FP32 kernel")
+    check_close(ga["var"], gf["var"], "var route vs FP32 kernel", atol=1e-6)
+    m0, v0 = orc.state_init(q, H, W)
+    e = orc.filter_step(q, hh, z, m0, v0, want_ell=True)
+    check_argmax(ga["argmax"], e["argmax"], e["ell"], q.dmin)
+    check_close(ga["mu"], e["mu"], "mu")
+    check_close(ga["var"], e["var"], "var", atol=1e-6)
+    _status_clear()
+
+
+def test_automatic_choice_by_frame_size():
+    """spl_filter_step on uint16 frames: from one 128-pixel block per SM upward it is the tensor-core route (equal
+    to spl_filter_step_tc bit for bit), below it the FP32 kernel (equal to spl_filter_step_fp32 bit for bit)."""
+    hh, peak = synth.asymmetric_irf(L=24)
+    T = 160
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    for H, W, entry in ((nsm, 128, spl.spl_filter_step_tc), (8, 16, spl.spl_filter_step_fp32)):
+        h, peak_, sc, zs = video_inputs(H, W, 2, T, 0.5, seed=75, L=24)
+        prm = spl.make_params(H, W, T, len(h), peak_, beta=0.5, sigma_rw2=3.0)
+        a = _steps(prm, h, zs, T, spl.spl_filter_step)
+        b = _steps(prm, h, zs, T, entry)
+        for n in range(2):
+            for k in KEYS:
+                assert np.array_equal(a[n][k], b[n][k]), f"{H}x{W} frame {n}: {k} differs from {entry.__name__}"
     _status_clear()
