@@ -55,27 +55,28 @@ TRAFFIC_CAPTURES = {
     # runs (nine captures of one launch each, mean) plus the intensity launch (mean of the same nine frames)
     # (ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum)
     "k_estimate": {"sources": ("estimate.cu", "pixel.cuh", "posterior.cuh", "intensity.cu"),
-                   "sha256": "5bae563cc5ba802d1c6630c86231778757af44605e34d5c7708197c4392920eb",
-                   "bytes_per_pixel": (201.16e6 + 15.52e6) / 65536,
+                   "sha256": "7c03e2392cea9239812429c9c1a41bc18e297fd094372fd196d619374661e66b",
+                   "bytes_per_pixel": (201.11e6 + 15.52e6) / 65536,
                    "inst_per_pixel": (368.24e6 + 14.85e6) / 65536},
     # one uint16 filter step of the video job (spl_filter_step): the tensor-core launch, the redo launch and the
     # intensity launch of frame 1 of each of the nine runs (mean)
     "k_filter_tc_u16": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh", "estimate.cu",
                                     "posterior.cuh"),
-                        "sha256": "2d0309315ca0a597401844aec69788500c655c436f5c3fa694ba5fdbc275c561",
-                        "bytes_per_pixel": 221.70e6 / 65536,
-                        "inst_per_pixel": 151.60e6 / 65536},
+                        "sha256": "448fc09f161a63788762c2d7d99b7abffe0c82e1adc21ec09877abfb1c073519",
+                        "bytes_per_pixel": 221.74e6 / 65536,
+                        "inst_per_pixel": 151.88e6 / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh"),
-                    "sha256": "822e47827c851ef9b23f136f85cc5ce229ada120d82354fe8333713ec4feffe6",
-                    "bytes_per_pixel": (537.633e6 + 3.613e6 + 17.199e6) / 65536,
+                    "sha256": "2dcc247c934b62b7c5c11d78501949a0af5a32748d0dd4dacc626c8ce27b6188",
+                    "bytes_per_pixel": (537.650e6 + 3.660e6 + 17.200e6) / 65536,
                     # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture
                     # of frame 2 of a 256 x 256 run of the mixed workload
-                    "inst_per_pixel": (348.01e6 + 14.004e6) / 65536},
-    # one launch of the photon-list kernel over all 64 sequences of the batched workload (7 050 240 pixels)
+                    "inst_per_pixel": (348.19e6 + 14.004e6) / 65536},
+    # the two launches (one per size class) of one frame of the photon-list kernel over all 64 sequences of the
+    # batched workload (7 050 240 pixels)
     "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh", "photons.cuh"),
-                "sha256": "f5824f43b6da8a5ca1affa3ab6ee1fddeaaaffe7532ae91505600800b054a963",
-                "bytes_per_pixel": (458.96e6 + 124.82e6) / 7050240,
-                "inst_per_pixel": 33720.18e6 / 7050240},
+                "sha256": "fd666076f64fd9d003440086d9d408245c1461c127b5b3ae82f67e04b7bacf7f",
+                "bytes_per_pixel": (160.68e6 + 32.66e6 + 295.12e6 + 71.50e6) / 7050240,
+                "inst_per_pixel": (17607.38e6 + 16141.73e6) / 7050240},
     # backward launches of the differentiable filter (128 x 128 frames, T = 1024): mean of three of the 20 launches
     # of one reverse sweep (they differ by 0.04 %)
     "k_diff_backward": {"sources": ("grad.cu", "pixel.cuh"),
@@ -666,6 +667,7 @@ def batched(args):
     init_states()
     spl.spl_batch_tune(plan, 0)
     info = spl.spl_batch_info(plan)
+    launches_per_frame = sum(1 for c in info["classes"] if c["units"] > 0)
     init_states()
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream(dev)
@@ -769,29 +771,31 @@ def batched(args):
              "max_rel_mu_vs_batched": rel,
              "note": "the same 64 sequences and photons as uint16 histograms through spl_filter_step_fp32 (one launch "
                      "pair per sequence and frame, 640 per step), histograms built outside the timed region"}
-    # roofline of k_batch: algorithmic bytes per launch (one frame of every sequence) = 4 B per photon (bin
-    # index) + 32 B per pixel (list offset, previous state, new state, argmax, refl, bg); its average launch time
-    # = the graph's time over its 10 frames (each frame's node pair is a 4-byte memset and the kernel)
+    # roofline of k_batch: algorithmic bytes per frame of every sequence = 4 B per photon (bin index) + 32 B per
+    # pixel (list offset, previous state, new state, argmax, refl, bg); its time = the graph's time over its 10
+    # frames (each frame's nodes are an 8-byte memset and one launch per size class)
     peaks = _peaks()
     P_all = units // BATCH_FRAMES
     launch_s = ms / BATCH_FRAMES / 1e3
     roofline = hbm_roofline(
         peaks, 4 * photons // BATCH_FRAMES + 32 * P_all, launch_s, capture_traffic("k_batch", P_all),
-        "k_batch (one frame of all 64 sequences)",
+        "k_batch (one frame of all 64 sequences: one launch per size class)",
         issue=issue_roofline(dev, peaks, capture_traffic("k_batch", P_all, "inst_per_pixel"), launch_s,
-                             "ncu smsp__inst_executed.sum of one launch of this workload"),
+                             "ncu smsp__inst_executed.sum of the launches of one frame of this workload"),
         note="latency-bound: up to 4049 candidates per pixel from at most 30 photons")
     line = {"metric": "pixel-frames/s", "value": units / (ms / 1e3), "unit": "pixel-frames/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched: 64 photon-list sequences x 10 frames, sides 32-512, T 512-4096",
                        "pixels": units // BATCH_FRAMES, "frames": BATCH_FRAMES, "photons_per_step": photons,
-                       "tile": info["tile"], "ctas": info["ctas"], "warps_per_cta": info["warps_per_cta"],
-                       "graph": "10 persistent launches captured in one CUDA graph"},
+                       "tile": info["tile"], "size_classes": info["classes"],
+                       "graph": f"{launches_per_frame * BATCH_FRAMES} persistent launches (one per size class and "
+                                "frame) captured in one CUDA graph"},
             "unbatched": {"value": units / (ms_unbatched / 1e3), "ms_per_step": ms_unbatched,
                           "note": "same sequences, one single-sequence plan per sequence, 640 launches"},
             "plain_fp32_histograms": plain, "depth_rmse_last_frame": rmse_batched,
-            "status_flags": flags, "gpu_launches": BATCH_FRAMES * args.steps, "clocks": clk.summary(),
+            "status_flags": flags, "gpu_launches": launches_per_frame * BATCH_FRAMES * args.steps,
+            "clocks": clk.summary(),
             "roofline": roofline}
     print(json.dumps(line), flush=True)
 

@@ -289,9 +289,13 @@ SPL_API spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, 
  *   spl_batch_create(prms, nseq, nslots, &b);              allocates device tables
  *   spl_batch_set(b, slot, frames) for each slot;          uploads pointers (synchronous, outside capture)
  *   spl_batch_tune(b, slot, stream);                       optional: times tile sizes on real data
- *   spl_batch_step(b, slot, stream) for frame after frame; one persistent launch each; capturable in a
- *                                                          CUDA graph (a memset and a kernel launch)
+ *   spl_batch_step(b, slot, stream) for frame after frame; one persistent launch per size class each;
+ *                                                          capturable in a CUDA graph (a memset and one or
+ *                                                          two kernel launches)
  *   spl_batch_status(b, &flags); spl_batch_destroy(b);
+ * The plan splits its sequences into two size classes when that raises the resident warps of the shorter ones:
+ * those with more than half the longest sequence's candidate count, and the rest, each class with shared-memory
+ * slices sized for its own longest sequence.
  * ------------------------------------------------------------------------------------------------------------ */
 
 /* Device pointers of one sequence for one frame (all [P] of that sequence unless stated). */
@@ -341,8 +345,15 @@ SPL_API spl_status spl_batch_step(spl_batch* b, int slot, void* stream);
  * of that slot are written several times with the same values). Synchronises the stream. */
 SPL_API spl_status spl_batch_tune(spl_batch* b, int slot, void* stream);
 
-/* Reports the plan's launch configuration (any pointer may be NULL). */
+/* Reports the plan's launch configuration (any pointer may be NULL): tile size, work units of both classes, and the
+ * CTAs and warps per CTA of the launch of the longer sequences' class. */
 SPL_API spl_status spl_batch_info(const spl_batch* b, int* tile, int* units, int* ctas, int* warps_per_cta);
+
+/* Reports size class cls (0 = the longer sequences; 0 <= cls < *nclass) of the plan: the class count (1 or 2), the
+ * class's work units, CTAs, warps per CTA and longest candidate grid (dmax - dmin + 1). Any output pointer may be
+ * NULL; SPL_EINVAL for a NULL plan or a class the plan does not have. */
+SPL_API spl_status spl_batch_class_info(const spl_batch* b, int cls, int* nclass, int* units, int* ctas,
+                                        int* warps_per_cta, int* max_candidates);
 
 /* Reads and clears the device-side condition flags (SPL_BATCH_*) accumulated since the last call.
  * Synchronous. */

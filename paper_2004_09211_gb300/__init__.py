@@ -373,9 +373,22 @@ def spl_batch_tune(handle, slot: int, stream=None) -> None:
 
 
 def spl_batch_info(handle) -> dict:
+    """The plan's tile size and unit count, the launch geometry of its first size class, and under "classes" every
+    class's units, CTAs, warps per CTA and longest candidate grid (spl_batch_class_info)."""
+    lib = _abi.load()
     v = [ct.c_int() for _ in range(4)]
-    _abi.check(_abi.load().spl_batch_info(handle, *[ct.byref(x) for x in v]))
-    return dict(tile=v[0].value, units=v[1].value, ctas=v[2].value, warps_per_cta=v[3].value)
+    _abi.check(lib.spl_batch_info(handle, *[ct.byref(x) for x in v]))
+    classes = []
+    nclass = 1
+    c = 0
+    while c < nclass:
+        w = [ct.c_int() for _ in range(5)]
+        _abi.check(lib.spl_batch_class_info(handle, c, *[ct.byref(x) for x in w]))
+        nclass = w[0].value
+        classes.append(dict(units=w[1].value, ctas=w[2].value, warps_per_cta=w[3].value,
+                            max_candidates=w[4].value))
+        c += 1
+    return dict(tile=v[0].value, units=v[1].value, ctas=v[2].value, warps_per_cta=v[3].value, classes=classes)
 
 
 def spl_batch_status(handle) -> int:

@@ -75,6 +75,7 @@ SIGNATURES = {
     "spl_batch_step": (ct.c_int, [_vp, ct.c_int, _vp]),
     "spl_batch_tune": (ct.c_int, [_vp, ct.c_int, _vp]),
     "spl_batch_info": (ct.c_int, [_vp] + [ct.POINTER(ct.c_int)] * 4),
+    "spl_batch_class_info": (ct.c_int, [_vp, ct.c_int] + [ct.POINTER(ct.c_int)] * 5),
     "spl_batch_status": (ct.c_int, [_vp, ct.POINTER(ct.c_uint32)]),
     "spl_diff_scratch_size": (ct.c_int, [_P, ct.POINTER(ct.c_size_t)]),
     "spl_diff_forward": (ct.c_int, [_P, ct.c_int, _Hh, _vp, ct.c_float, _vp, _vp, _vp, _vp, _vp, _vp, ct.c_size_t, _vp]),

@@ -1,5 +1,5 @@
 // Batched online filter over many independent sequences whose photon data are time-of-arrival lists (CSR),
-// in one persistent launch per frame.
+// in one persistent launch per frame and size class.
 //
 // Work units are (sequence, tile of consecutive pixels), ordered by decreasing estimated cost (pixels times
 // candidate depths) so the largest are taken first. Each warp repeatedly takes the next unit from a device
@@ -7,8 +7,10 @@
 // and processes the tile's pixels one at a time with the same per-pixel arithmetic as the histogram kernel
 // (pixel.cuh, posterior.cuh). The data term uses the photon-sum form of Eq. beta_div2:
 // C(d) = sum_k g[y_k - d + peak], formed lane = tap from the list in global memory (corr_photon_list, photons.cuh).
-// The queue head is reset by a memset on the launch stream before every step, so a step is a memset node and
-// a kernel node in a CUDA graph. The plan (unit list, descriptor tables, queue heads, status word) is
+// Sequences are split into two size classes when that raises the shorter ones' resident warps (their shared-memory
+// slices are sized for their own longest candidate grid); each class has its own launch and queue head. The queue
+// heads are reset by one memset on the launch stream before every step, so a step is a memset node and one or two
+// kernel nodes in a CUDA graph. The plan (unit list, descriptor tables, queue heads, status word) is
 // allocated once at creation; nothing is allocated per step.
 #include <math.h>
 #include <stdio.h>
@@ -223,12 +225,18 @@ struct spl_batch {
     std::vector<spl_params> prm;
     spl::DevSeq* d_seqs = nullptr;   // [nslots][nseq]
     spl::Unit* d_units = nullptr;    // [max units]
-    unsigned* d_head = nullptr;      // [nslots] work-queue heads
+    unsigned* d_head = nullptr;      // [nslots][2] work-queue heads, one per class
     unsigned* d_status = nullptr;    // condition flags
     int max_units = 0, nunits = 0, tile = 32;
-    int wpc = 8, ctas = 0;
-    size_t smem = 0;
-    spl::BSlice sl;
+    // Two classes of sequences by candidate count, each with its own per-warp slice and launch geometry: the
+    // sequences with at most split_D candidates would otherwise carry the slice sized for the longest grid and
+    // keep fewer warps resident. nclass = 1 when the split would not raise their resident warps.
+    int nclass = 1, split_D = 0;
+    int ubeg[2] = {0, 0}, ucnt[2] = {0, 0};  // each class's range of the unit list
+    int maxD[2] = {1, 1};                    // each class's longest candidate grid
+    int wpc[2] = {8, 8}, ctas[2] = {0, 0};
+    size_t smem[2] = {0, 0};
+    spl::BSlice sl[2];
     std::vector<int> slot_set;       // slot has been filled by spl_batch_set
 };
 
@@ -237,36 +245,73 @@ namespace {
 
 constexpr int kTiles[] = {8, 16, 32, 64, 128};
 
-std::vector<Unit> make_units(const std::vector<spl_params>& prm, int tile) {
+// The work units of the plan, class 0 (more than split_D candidates) first, then class 1, each in decreasing cost
+// order (candidates per pixel); cnt receives the two classes' unit counts.
+std::vector<Unit> make_units(const std::vector<spl_params>& prm, int tile, int split_D, int* cnt) {
     std::vector<Unit> u;
     std::vector<std::pair<long long, int>> order;  // (cost per pixel, seq)
     for (int s = 0; s < static_cast<int>(prm.size()); ++s)
         order.push_back({static_cast<long long>(prm[s].dmax - prm[s].dmin + 1), s});
     std::stable_sort(order.begin(), order.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    cnt[0] = cnt[1] = 0;
     for (const auto& o : order) {
         const int s = o.second;
         const int P = prm[s].H * prm[s].W;
-        for (int p0 = 0; p0 < P; p0 += tile) u.push_back(Unit{s, p0, std::min(P, p0 + tile), 0});
+        const int c = o.first > split_D ? 0 : 1;
+        for (int p0 = 0; p0 < P; p0 += tile) {
+            u.push_back(Unit{s, p0, std::min(P, p0 + tile), 0});
+            ++cnt[c];
+        }
     }
     return u;
 }
 
 cudaError_t upload_units(spl_batch* b, int tile) {
-    std::vector<Unit> u = make_units(b->prm, tile);
+    int cnt[2];
+    std::vector<Unit> u = make_units(b->prm, tile, b->nclass > 1 ? b->split_D : 0, cnt);
     if (static_cast<int>(u.size()) > b->max_units) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpy(b->d_units, u.data(), sizeof(Unit) * u.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     b->nunits = static_cast<int>(u.size());
+    b->ubeg[0] = 0;
+    b->ucnt[0] = cnt[0];
+    b->ubeg[1] = cnt[0];
+    b->ucnt[1] = cnt[1];
     b->tile = tile;
     return cudaSuccess;
 }
 
+// One step: the two queue heads of the slot cleared by one memset, then one persistent launch per class (a memset
+// node and one or two kernel nodes in a CUDA graph).
 cudaError_t launch_batch(spl_batch* b, int slot, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b->d_head + slot, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    k_batch<<<b->ctas, b->wpc * 32, b->smem, s>>>(b->d_seqs + static_cast<size_t>(slot) * b->nseq, b->d_units,
-                                                  b->nunits, b->d_head + slot, b->d_status, b->sl);
-    return cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(b->d_head + 2 * slot, 0, 2 * sizeof(unsigned), s);
+    for (int c = 0; c < b->nclass && e == cudaSuccess; ++c) {
+        if (b->ucnt[c] == 0) continue;
+        k_batch<<<b->ctas[c], b->wpc[c] * 32, b->smem[c], s>>>(b->d_seqs + static_cast<size_t>(slot) * b->nseq,
+                                                               b->d_units + b->ubeg[c], b->ucnt[c],
+                                                               b->d_head + 2 * slot + c, b->d_status, b->sl[c]);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// Warps per CTA that maximise resident warps for slice sl (one wave of resident CTAs); best = warps per SM.
+cudaError_t batch_geometry(const BSlice& sl, int nsm, int& wpc, int& ctas, size_t& smem, int& best) {
+    const size_t per_warp = sizeof(float) * static_cast<size_t>(sl.words);
+    best = 0;
+    for (int w = 8; w >= 1; --w) {
+        if (per_warp * w > 220 * 1024) continue;
+        int per_sm = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, w * 32, per_warp * w);
+        if (e != cudaSuccess) return e;
+        if (per_sm * w > best) {
+            best = per_sm * w;
+            wpc = w;
+            ctas = per_sm * nsm;
+            smem = per_warp * w;
+        }
+    }
+    return best == 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
 
 void free_plan(spl_batch* b) {
@@ -298,6 +343,7 @@ spl_status spl_batch_create(const spl_params* prms, int nseq, int nslots, spl_ba
     }
     int maxD = 1;
     long long max_units = 0;
+    std::vector<int> Ds;
     for (int s = 0; s < nseq; ++s) {
         spl_status st = check_params(&prms[s], true);
         if (st != SPL_OK) {
@@ -307,6 +353,7 @@ spl_status spl_batch_create(const spl_params* prms, int nseq, int nslots, spl_ba
             return st;
         }
         maxD = std::max(maxD, prms[s].dmax - prms[s].dmin + 1);
+        Ds.push_back(prms[s].dmax - prms[s].dmin + 1);
         max_units += (static_cast<long long>(prms[s].H) * prms[s].W + kTiles[0] - 1) / kTiles[0];
     }
     if (max_units > (1LL << 30)) {
@@ -319,34 +366,34 @@ spl_status spl_batch_create(const spl_params* prms, int nseq, int nslots, spl_ba
     b->prm.assign(prms, prms + nseq);
     b->slot_set.assign(nslots, 0);
     b->max_units = static_cast<int>(max_units);
-    b->sl = make_bslice(maxD);
+    // class 1: the sequences with at most half the longest grid's candidates, sliced for their own longest
+    b->split_D = maxD / 2;
+    int maxD1 = 0;
+    for (int d : Ds)
+        if (d <= b->split_D) maxD1 = std::max(maxD1, d);
+    b->maxD[0] = maxD;
+    b->maxD[1] = std::max(maxD1, 1);
+    b->sl[0] = make_bslice(b->maxD[0]);
+    b->sl[1] = make_bslice(b->maxD[1]);
+    b->nclass = maxD1 > 0 ? 2 : 1;
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_seqs, sizeof(DevSeq) * static_cast<size_t>(nseq) * nslots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_units, sizeof(Unit) * static_cast<size_t>(b->max_units));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_head, sizeof(unsigned) * nslots);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_head, 2 * sizeof(unsigned) * nslots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->d_seqs, 0, sizeof(DevSeq) * static_cast<size_t>(nseq) * nslots);
-    if (e == cudaSuccess) e = upload_units(b, 32);
-    // launch geometry: warps per CTA maximising resident warps, one wave of resident CTAs
+    // launch geometry per class: warps per CTA maximising resident warps, one wave of resident CTAs; the split is
+    // kept only where it raises the short sequences' resident warps
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    if (e == cudaSuccess) {
-        const size_t per_warp = sizeof(float) * static_cast<size_t>(b->sl.words);
-        int best = 0;
-        for (int w = 8; w >= 1 && e == cudaSuccess; --w) {
-            if (per_warp * w > 220 * 1024) continue;
-            int per_sm = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, w * 32, per_warp * w);
-            if (per_sm * w > best) {
-                best = per_sm * w;
-                b->wpc = w;
-                b->ctas = per_sm * b->nsm;
-                b->smem = per_warp * w;
-            }
-        }
-        if (e == cudaSuccess && best == 0) e = cudaErrorInvalidConfiguration;
+    int best0 = 0, best1 = 0;
+    if (e == cudaSuccess) e = batch_geometry(b->sl[0], b->nsm, b->wpc[0], b->ctas[0], b->smem[0], best0);
+    if (e == cudaSuccess && b->nclass == 2) {
+        e = batch_geometry(b->sl[1], b->nsm, b->wpc[1], b->ctas[1], b->smem[1], best1);
+        if (e == cudaSuccess && best1 <= best0) b->nclass = 1;
     }
+    if (e == cudaSuccess) e = upload_units(b, 32);
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;
         set_error("spl_batch_create: %s", cudaGetErrorString(e));
@@ -457,8 +504,26 @@ spl_status spl_batch_info(const spl_batch* b, int* tile, int* units, int* ctas, 
     }
     if (tile) *tile = b->tile;
     if (units) *units = b->nunits;
-    if (ctas) *ctas = b->ctas;
-    if (warps_per_cta) *warps_per_cta = b->wpc;
+    if (ctas) *ctas = b->ctas[0];
+    if (warps_per_cta) *warps_per_cta = b->wpc[0];
+    return SPL_OK;
+}
+
+spl_status spl_batch_class_info(const spl_batch* b, int cls, int* nclass, int* units, int* ctas, int* warps_per_cta,
+                                int* max_candidates) {
+    if (!b) {
+        set_error("plan is NULL");
+        return SPL_EINVAL;
+    }
+    if (cls < 0 || cls >= b->nclass) {
+        set_error("spl_batch_class_info: class %d of a plan with %d", cls, b->nclass);
+        return SPL_EINVAL;
+    }
+    if (nclass) *nclass = b->nclass;
+    if (units) *units = b->ucnt[cls];
+    if (ctas) *ctas = b->ctas[cls];
+    if (warps_per_cta) *warps_per_cta = b->wpc[cls];
+    if (max_candidates) *max_candidates = b->maxD[cls];
     return SPL_OK;
 }
 

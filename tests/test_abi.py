@@ -126,6 +126,7 @@ def test_batch_argument_checks():
     assert lib.spl_batch_set(None, 0, None) == _abi.SPL_EINVAL
     assert lib.spl_batch_tune(None, 0, None) == _abi.SPL_EINVAL
     assert lib.spl_batch_info(None, None, None, None, None) == _abi.SPL_EINVAL
+    assert lib.spl_batch_class_info(None, 0, None, None, None, None, None) == _abi.SPL_EINVAL
     assert lib.spl_batch_status(None, None) == _abi.SPL_EINVAL
 
 

@@ -140,6 +140,42 @@ def test_batch_matches_oracle(orc):
             mu, var = e["mu"], e["var"]
 
 
+def test_batch_size_classes(orc):
+    """Sequences whose candidate grids differ by more than a factor of two (T = 4096 against T = 512 and 1000):
+    the plan splits them into two size classes with a launch each; the classes partition the work units, the
+    second holds only grids of at most half the longest, and both match the oracle, eagerly and replayed from a
+    CUDA graph (bit for bit)."""
+    asy = synth.asymmetric_irf(L=48)
+    specs = [(4, 8, 4096, asy, 0.4, 3.0, synth.cross_weights(0.5), 3.0, 10.0),
+             (6, 6, 512, synth.gaussian_irf(3.0, 12), 0.7, 3.0, synth.cross_weights(0.5), 3.0, 10.0),
+             (1, 20, 1000, synth.gaussian_irf(2.0, 8), 0.2, 3.0, synth.cross_weights(0.6), 4.0, 5.0)]
+    seqs = _make_frames(specs, N=2, seed=12)
+    res, flags, info = _run(seqs, 2)
+    graph, _, _ = _run(seqs, 2, graph=True)
+    assert flags == 0
+    cls = info["classes"]
+    assert len(cls) == 2, info
+    grids = [q["T"] - q["L"] + 1 for q in seqs]
+    assert cls[0]["max_candidates"] >= max(grids) and 2 * cls[1]["max_candidates"] <= cls[0]["max_candidates"]
+    assert cls[0]["units"] > 0 and cls[1]["units"] > 0 and cls[0]["units"] + cls[1]["units"] == info["units"]
+    assert cls[1]["ctas"] * cls[1]["warps_per_cta"] > cls[0]["ctas"] * cls[0]["warps_per_cta"]
+    for i, q in enumerate(seqs):
+        oq = orc.params(q["T"], q["L"], q["peak"], beta=q["beta"], sigma_rw2=q["s2"], nu=q["nu"])
+        mu, var = orc.state_init(oq, q["H"], q["W"])
+        for n in range(2):
+            off, bins = q["frames"][n]
+            z = synth.csr_to_histograms(off, bins, q["T"]).astype(np.float64).reshape(q["H"], q["W"], q["T"])
+            e = orc.filter_step(oq, q["h"], z, mu, var, want_ell=True)
+            g = res[n][i]
+            check_argmax(g["argmax"], e["argmax"], e["ell"], oq.dmin, f"seq {i} frame {n} argmax")
+            check_close(g["mu_out"], e["mu"], f"seq {i} frame {n} mu")
+            check_close(g["var_out"], e["var"], f"seq {i} frame {n} var", atol=1e-6)
+            check_intensity(orc, oq, q["h"], z, g["mu_out"], e["mu"], g["refl"], g["bg"])
+            for k in ("mu_out", "var_out", "argmax", "refl", "bg"):
+                np.testing.assert_array_equal(graph[n][i][k], g[k])
+            mu, var = e["mu"], e["var"]
+
+
 def test_batch_graph_replay_and_tuning_reproduce_eager():
     seqs = _make_frames(_seq_specs(), N=3, seed=8)
     eager, _, _ = _run(seqs, 3)

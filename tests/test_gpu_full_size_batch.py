@@ -84,6 +84,7 @@ def test_full_size_batch_sampled(orc):
     seqs = _full_size_batch_inputs(N, DEV)
     res, flags, info = _run(seqs, N, tune=True)
     assert flags == 0 and info["units"] > 0
+    assert sum(c["units"] for c in info["classes"]) == info["units"]
     pick = np.random.default_rng(41)
     for i, q in enumerate(seqs):
         H, W = q["H"], q["W"]
