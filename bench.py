@@ -61,11 +61,11 @@ TRAFFIC_CAPTURES = {
     # one uint16 filter step of the video job (spl_filter_step): the tensor-core launch, the redo launch and the
     # intensity launch of frame 1 of each of the nine runs (mean)
     "k_filter_tc_u16": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh", "estimate.cu",
-                                    "posterior.cuh"),
+                                    "posterior.cuh", "f32x2.cuh"),
                         "sha256": "448fc09f161a63788762c2d7d99b7abffe0c82e1adc21ec09877abfb1c073519",
                         "bytes_per_pixel": 221.74e6 / 65536,
                         "inst_per_pixel": 151.88e6 / 65536},
-    "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh"),
+    "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh", "f32x2.cuh"),
                     "sha256": "2dcc247c934b62b7c5c11d78501949a0af5a32748d0dd4dacc626c8ce27b6188",
                     "bytes_per_pixel": (537.650e6 + 3.660e6 + 17.200e6) / 65536,
                     # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture

@@ -36,6 +36,7 @@
 
 #include <mutex>
 
+#include "f32x2.cuh"
 #include "pixel.cuh"
 #include "spl_internal.h"
 #include "tc_common.cuh"
@@ -379,6 +380,78 @@ __device__ __forceinline__ bool chunk_lin(const float* c, int c0, int D, int dmi
     return true;
 }
 
+// chunk_lin with the candidates taken in adjacent pairs (2j, 2j + 1), one packed f32x2 instruction per pair for
+// every add, multiply and FMA. Each component then follows two interleaved Gaussians on the even and the odd
+// candidates: values V = (v(2j), v(2j + 1)), started from exact exponentials at candidates 0 and 1, step ratios
+// v(i + 2) / v(i) = 2^(-k (4 (d_i - m) + 4)), and the ratio of those ratios 2^(-8 k) for both. Same contract and
+// the same data factor, bit for bit, as chunk_lin; the prior values and the moment sums differ from it by
+// rounding only (eight recurrence steps per value instead of fifteen, sums split into even and odd halves).
+template <int NC, bool FULL>
+__device__ __forceinline__ bool chunk_lin2(const float* c, int c0, int D, int dmin, float l2s, const Prior& pr,
+                                          float cq, float pref, Moments& s) {
+    using px::f2;
+    f2 V[NC], Q[NC], R[NC];
+    const float d0 = static_cast<float>(dmin + c0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const float e = d0 - pr.cm[k], ck = pr.ck[k], b = pr.ca[k] - pref;
+        const float e1 = e + 1.f;
+        V[k] = px::f2_make(ex2(b - ck * e * e), ex2(b - ck * e1 * e1));
+        Q[k] = px::f2_make(ex2(fminf(-ck * fmaf(4.f, e, 4.f), 100.f)), ex2(fminf(-ck * fmaf(4.f, e, 8.f), 100.f)));
+        const float r = ex2(-8.f * ck);
+        R[k] = px::f2_make(r, r);
+    }
+    const f2 ncq = px::f2_make(-cq, -cq), sl = px::f2_make(l2s, l2s);
+    f2 U[8];
+    f2 S0 = px::f2_make(0.f, 0.f), S1 = S0;
+    float um = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        f2 pv = V[0];
+        V[0] = px::f2_mul(V[0], Q[0]);
+        Q[0] = px::f2_mul(Q[0], R[0]);
+#pragma unroll
+        for (int k = 1; k < NC; ++k) {
+            pv = px::f2_add(pv, V[k]);
+            V[k] = px::f2_mul(V[k], Q[k]);
+            Q[k] = px::f2_mul(Q[k], R[k]);
+        }
+        const f2 t = px::f2_mul(px::f2_add(px::f2_make(c[2 * j], c[2 * j + 1]), ncq), sl);
+        f2 u = px::f2_mul(px::f2_make(ex2(px::f2_lo(t)), ex2(px::f2_hi(t))), pv);
+        if (!FULL)
+            u = px::f2_make(c0 + 2 * j < D ? px::f2_lo(u) : 0.f, c0 + 2 * j + 1 < D ? px::f2_hi(u) : 0.f);
+        U[j] = u;
+        um = fmaxf(um, fmaxf(px::f2_lo(u), px::f2_hi(u)));
+        S0 = px::f2_add(S0, u);
+        S1 = px::f2_fma(u, px::f2_make(static_cast<float>(2 * j), static_cast<float>(2 * j + 1)), S1);
+    }
+    if (!(um >= 0x1p-60f)) return false;
+    const float lm = fmaf(l2s, cq, pref) + lg2(um);
+    if (lm > s.best) {  // new best: its (smallest) index in the chunk
+        int ib = 0;
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+            ib = px::f2_hi(U[j]) == um ? 2 * j + 1 : ib;
+            ib = px::f2_lo(U[j]) == um ? 2 * j : ib;
+        }
+        s.best = lm;
+        s.bidx = c0 + ib;
+    }
+    s.top = fmaxf(s.top, lm);
+    if (!(lm >= s.top - kPrune)) return true;
+    const float s0 = px::f2_lo(S0) + px::f2_hi(S0);
+    const float m1 = (px::f2_lo(S1) + px::f2_hi(S1)) / s0;
+    const f2 nm = px::f2_make(-m1, -m1);
+    f2 S2 = px::f2_make(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const f2 x = px::f2_add(px::f2_make(static_cast<float>(2 * j), static_cast<float>(2 * j + 1)), nm);
+        S2 = px::f2_fma(px::f2_mul(U[j], x), x, S2);
+    }
+    merge_centred(s, l2s, cq, pref, s0, static_cast<float>(c0) + m1, px::f2_lo(S2) + px::f2_hi(S2));
+    return true;
+}
+
 // One candidate tile of one pixel (this lane). A tile whose prior bound alone reaches the pruning threshold is
 // kept without looking at the data (C >= 0); otherwise its largest accumulator decides. Kept tiles are evaluated
 // chunk by chunk with the tile's prior bound as the reference. The tensor-memory loads are warp-collective:
@@ -416,9 +489,14 @@ __device__ __forceinline__ void tile_work(uint32_t tacc, int c0t, int D, int dmi
             st.amax = fmaxf(st.amax, cq);
             if (fmaf(l2s, cq, lpt) >= st.top - kPrune) {
                 bool done = false;
-                if (lin_ok)
-                    done = cq0 + 16 <= D ? chunk_lin<NC, true>(c, cq0, D, dmin, l2s, pr, cq, lpt, st)
-                                         : chunk_lin<NC, false>(c, cq0, D, dmin, l2s, pr, cq, lpt, st);
+                if (lin_ok) {
+                    if (NC <= 5)  // packed pairs; the nine-component case keeps the scalar form (registers)
+                        done = cq0 + 16 <= D ? chunk_lin2<NC, true>(c, cq0, D, dmin, l2s, pr, cq, lpt, st)
+                                             : chunk_lin2<NC, false>(c, cq0, D, dmin, l2s, pr, cq, lpt, st);
+                    else
+                        done = cq0 + 16 <= D ? chunk_lin<NC, true>(c, cq0, D, dmin, l2s, pr, cq, lpt, st)
+                                             : chunk_lin<NC, false>(c, cq0, D, dmin, l2s, pr, cq, lpt, st);
+                }
                 if (!done) {
                     const float lpq = lpb_n<NC>(pr, static_cast<float>(dmin + cq0),
                                                 static_cast<float>(dmin + min(cq0 + 15, D - 1)));
