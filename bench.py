@@ -62,15 +62,15 @@ TRAFFIC_CAPTURES = {
     # intensity launch of frame 1 of each of the nine runs (mean)
     "k_filter_tc_u16": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh", "estimate.cu",
                                     "posterior.cuh", "f32x2.cuh"),
-                        "sha256": "448fc09f161a63788762c2d7d99b7abffe0c82e1adc21ec09877abfb1c073519",
-                        "bytes_per_pixel": 221.74e6 / 65536,
-                        "inst_per_pixel": 151.88e6 / 65536},
+                        "sha256": "0dcc41b054efb2b34239dff8e6cce5d9544c9e2306946b8dc718ba7323729a73",
+                        "bytes_per_pixel": (218.70e6 + 3.05e6) / 65536,
+                        "inst_per_pixel": 130.80e6 / 65536},
     "k_filter_tc": {"sources": ("tcfilter.cu", "tc_common.cuh", "intensity.cu", "pixel.cuh", "f32x2.cuh"),
-                    "sha256": "2dcc247c934b62b7c5c11d78501949a0af5a32748d0dd4dacc626c8ce27b6188",
-                    "bytes_per_pixel": (537.650e6 + 3.660e6 + 17.200e6) / 65536,
+                    "sha256": "3a0457eb824d56aecb181436c24d0cec9f94162f04733fdb7316bca9e72ce35e",
+                    "bytes_per_pixel": (537.628e6 + 3.699e6 + 17.200e6) / 65536,
                     # warp-instructions of one filter step (tensor-core launch + intensity launch), one capture
                     # of frame 2 of a 256 x 256 run of the mixed workload
-                    "inst_per_pixel": (348.19e6 + 14.004e6) / 65536},
+                    "inst_per_pixel": (290.46e6 + 14.004e6) / 65536},
     # the two launches (one per size class) of one frame of the photon-list kernel over all 64 sequences of the
     # batched workload (7 050 240 pixels)
     "k_batch": {"sources": ("batch.cu", "pixel.cuh", "posterior.cuh", "photons.cuh"),
@@ -406,9 +406,10 @@ def native(args):
     rmse, kept = job_rmse(spl, prms, hd, videos, sc, frames, dev, keep=(keep_run, CROP_FRAMES - 1))
     rmse32, _ = job_rmse(spl, prms, hd, videos, sc, frames, dev, step=spl.spl_filter_step_fp32)
 
-    e2e = None
+    e2e = e2e_hist = None
     if not args.no_e2e:
-        e2e = end_to_end(spl, prms, hd, videos, dev, stream, P)
+        e2e = end_to_end_toa(spl, prms, hd, videos, dev, stream, P)
+        e2e_hist = end_to_end(spl, prms, hd, videos, dev, stream, P)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -439,7 +440,8 @@ def native(args):
                        "sequences": len(SBRS), "betas": list(BETAS), "hist": "uint16",
                        "pixel_frames_per_step": units, "l2": "inputs larger than L2 (197 MB per frame), no flush",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "roofline": roofline, "e2e": e2e, "e2e_histograms": e2e_hist, "gpu_launches": launches,
+            "clocks": clk.summary(),
             "fp32_path": {"value": value32, "ms_per_step": ms32 / args.steps, "dtype": "f32",
                           "entry": "spl_filter_step_fp32", "roofline": roofline32,
                           "depth_rmse_last_frame": rmse32},
@@ -448,6 +450,149 @@ def native(args):
         print(json.dumps(line), flush=True)
     if dist:
         td.destroy_process_group()
+
+
+def toa_from_histograms(z, T):
+    """The photon lists of one frame whose histograms are z ([P, pitch] uint16 on the device): CSR offsets int32
+    [P + 1] and bins uint16, each bin repeated by its count, in bin order within a pixel."""
+    zi = z[:, :T].to(torch.int32)
+    offsets = torch.zeros(zi.shape[0] + 1, dtype=torch.int32, device=z.device)
+    offsets[1:] = torch.cumsum(zi.sum(1), 0)
+    nz = zi.nonzero()
+    bins = torch.repeat_interleave(nz[:, 1], zi[nz[:, 0], nz[:, 1]].to(torch.int64))
+    return offsets, bins.to(torch.int32).to(torch.uint16)
+
+
+def end_to_end_toa(spl, prms, hd, videos, dev, stream, P):
+    """Same job through the public API from photon time-of-arrival lists in pinned HOST memory (the ToAs of Sec.
+    II-A as CSR lists of uint16 bins, the same photons as the histograms of the device-resident job): inside the
+    timed region every frame's lists are copied host -> device (on each lane's copy stream, double-buffered), turned
+    into uint16 histograms on the device (spl_toa_histogram) and filtered (spl_filter_step), and every frame's
+    outputs (mu, var, argmax, refl, bg) are read back to pinned host buffers. The runs are issued round-robin on
+    JOB_STREAMS lanes like the device-resident job."""
+    host = []
+    maxn = 0
+    resident = []  # device lists of the first frames of every video, for the kernel roofline below
+    for v in videos:
+        hv = []
+        for n, z in enumerate(v):
+            off, bins = toa_from_histograms(z, T)
+            if n < 10:
+                resident.append((off, bins))
+            ho = torch.empty(off.shape, dtype=off.dtype, pin_memory=True)
+            ho.copy_(off)
+            hb = torch.empty(bins.shape, dtype=bins.dtype, pin_memory=True)
+            hb.copy_(bins)
+            hv.append((ho, hb))
+            maxn = max(maxn, bins.numel())
+        host.append(hv)
+    torch.cuda.synchronize(dev)
+    pitch = videos[0][0].shape[1]
+    frames = len(host[0])
+
+    class Lane:
+        def __init__(self):
+            self.stream = torch.cuda.Stream(dev)
+            self.copy = torch.cuda.Stream(dev)
+            self.off = [torch.empty(P + 1, dtype=torch.int32, device=dev) for _ in range(2)]
+            self.bins = [torch.empty(max(maxn, 1), dtype=torch.uint16, device=dev) for _ in range(2)]
+            self.z = torch.empty(P, pitch, dtype=torch.uint16, device=dev)
+            self.mu = [torch.empty(P, device=dev) for _ in range(2)]
+            self.var = [torch.empty(P, device=dev) for _ in range(2)]
+            self.outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                             bg=torch.empty(P, device=dev))
+            self.hout = {k: torch.empty(P, dtype=dt).pin_memory() for k, dt in
+                         (("mu", torch.float32), ("var", torch.float32), ("argmax", torch.int32),
+                          ("refl", torch.float32), ("bg", torch.float32))}
+            self.copied = [torch.cuda.Event() for _ in range(2)]
+            self.consumed = [torch.cuda.Event() for _ in range(2)]
+            self.i = 0
+
+    lanes = [Lane() for _ in range(JOB_STREAMS)]
+    h2d = d2h = 0
+
+    def put(ln, vi, n):  # the frame's lists into the lane's next buffer, on its copy stream
+        nonlocal h2d
+        s = ln.i & 1
+        ho, hb = host[vi][n]
+        with torch.cuda.stream(ln.copy):
+            ln.copy.wait_event(ln.consumed[s])
+            ln.off[s].copy_(ho, non_blocking=True)
+            if hb.numel():
+                ln.bins[s][:hb.numel()].copy_(hb, non_blocking=True)
+            ln.copied[s].record(ln.copy)
+        h2d += ho.numel() * 4 + hb.numel() * 2
+
+    def job():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        start = torch.cuda.Event()
+        start.record(stream)
+        for ln in lanes:
+            ln.stream.wait_event(start)
+            ln.copy.wait_event(start)
+            ln.i = 0
+        runs = [(vi, bi) for vi in range(len(host)) for bi in range(len(prms))]
+        for r, (vi, bi) in enumerate(runs):
+            ln = lanes[r % len(lanes)]
+            if r < len(lanes):  # a lane's first frame; the later runs' first frames are put by the run before
+                put(ln, vi, 0)
+            spl.spl_state_init(prms[bi], ln.mu[0], ln.var[0], stream=ln.stream)
+            for n in range(frames):
+                s = ln.i & 1
+                # the next frame of this lane (this run's next frame, or the first frame of its next run)
+                nxt = (vi, n + 1) if n + 1 < frames else (runs[r + len(lanes)][0], 0) \
+                    if r + len(lanes) < len(runs) else None
+                ln.stream.wait_event(ln.copied[s])
+                nb = host[vi][n][1].numel()
+                spl.spl_toa_histogram(prms[bi], ln.off[s], ln.bins[s][:nb], out=ln.z, stream=ln.stream)
+                src, dst = n & 1, (n + 1) & 1
+                o = spl.spl_filter_step(prms[bi], ln.z, hd, ln.mu[src], ln.var[src],
+                                        out=dict(mu=ln.mu[dst], var=ln.var[dst], **ln.outs), stream=ln.stream)
+                ln.consumed[s].record(ln.stream)
+                for k in ln.hout:
+                    with torch.cuda.stream(ln.stream):
+                        ln.hout[k].copy_(o[k], non_blocking=True)
+                    d2h += o[k].numel() * 4
+                ln.i += 1
+                if nxt is not None:
+                    put(ln, *nxt)
+        for ln in lanes:
+            done = torch.cuda.Event()
+            done.record(ln.stream)
+            stream.wait_event(done)
+        return len(runs) * frames
+
+    job()  # warm-up (also primes the events)
+    torch.cuda.synchronize(dev)
+    assert spl.spl_toa_status() == 0
+    t0 = time.perf_counter()
+    n = job()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+
+    # the histogram kernel alone on device-resident lists (the first 10 frames of each video, one after another on
+    # one stream; each launch writes a 197 MB cube, larger than L2): algorithmic bytes = the rows written
+    # (2 pitch per pixel) + the photons (2 B each) and offsets (4 B per pixel) read
+    zb = lanes[0].z
+    for off, bins in resident[:3]:
+        spl.spl_toa_histogram(prms[0], off, bins, out=zb, stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for off, bins in resident:
+        spl.spl_toa_histogram(prms[0], off, bins, out=zb, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    assert spl.spl_toa_status() == 0
+    launch_s = ev0.elapsed_time(ev1) / 1e3 / len(resident)
+    alg = sum(P * pitch * 2 + b.numel() * 2 + (P + 1) * 4 for _, b in resident) / len(resident)
+    kern = hbm_roofline(_peaks(), alg, launch_s, None,
+                        "k_toa_hist (spl_toa_histogram; mean over the first 10 frames of the three videos)")
+    return {"value": n * P / dt, "unit": "pixel-frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "toa_histogram_roofline": kern,
+            "note": "photon ToA lists (CSR, uint16 bins; the same photons as the histograms) in pinned host memory, "
+                    "copied each frame, histogrammed on the device (spl_toa_histogram) and filtered "
+                    "(spl_filter_step) on 3 lanes; outputs read back each frame"}
 
 
 def end_to_end(spl, prms, hd, videos, dev, stream, P):

@@ -275,6 +275,30 @@ SPL_API spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, 
                                       const uint8_t* present_now, float* mu_out, float* var_out, int32_t* argmax,
                                       float* refl, float* bg, void* stream);
 
+/*
+ * spl_toa_histogram -- the histograms of one frame from its photon time-of-arrival lists (Sec. II-A: the ToAs
+ *   y_{p,n} of pixel p, binned on the N_T = T bins of Eq. lik_ideal_poisson; z_p[t] = number of photons in bin t,
+ *   the histogram on which the histogram form of Eq. beta_div2 and Eq. lik_bg_poisson are written). The result
+ *   is a SPL_HIST_U16 cube for spl_filter_step, spl_depth_estimate and the other histogram calls; built on the
+ *   device, it lets a caller move a frame's photon lists to the GPU instead of its histograms.
+ *   offsets  : [P + 1] int32 (device); pixel p's photons are bins[offsets[p] .. offsets[p + 1]).
+ *   bins     : [nphotons] uint16 (device) bin indices, in any order within a pixel; may be NULL when nphotons = 0.
+ *   out      : [P][pitch] uint16 (device), 16-byte aligned, pitch >= T and a multiple of 8; every element of every
+ *              row is written (elements T..pitch-1 as 0).
+ *   Uses H, W, T of prm (T <= SPL_MAX_BINS). Counts are exact: the same histogram for every order of the
+ *   photons. Device-detected conditions, read and cleared by spl_toa_status:
+ *     SPL_TOA_BAD_BIN (1)     a photon with bin >= T was dropped;
+ *     SPL_TOA_SATURATED (2)   a bin held more than 65535 photons and was written as 65535;
+ *     SPL_TOA_BAD_OFFSETS (4) a pixel's offsets were not 0 <= offsets[p] <= offsets[p + 1] <= nphotons: its row is
+ *                             written as zeros and none of its photons is read.
+ */
+#define SPL_TOA_BAD_BIN 1
+#define SPL_TOA_SATURATED 2
+#define SPL_TOA_BAD_OFFSETS 4
+SPL_API spl_status spl_toa_histogram(const spl_params* prm, const int32_t* offsets, const uint16_t* bins,
+                                     int64_t nphotons, uint16_t* out, int64_t pitch, void* stream);
+SPL_API spl_status spl_toa_status(uint32_t* flags);
+
 /* ------------------------------------------------------------------------------------------------------------
  * Batched filtering of many independent sequences from photon time-of-arrival lists
  *

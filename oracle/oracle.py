@@ -133,6 +133,30 @@ def cost_toa(q: Params, h, bins) -> np.ndarray:
     return C
 
 
+def toa_histogram(T: int, offsets, bins):
+    """Histograms of one frame from its photon ToA lists in CSR form (pixel p's photons are
+    bins[offsets[p]:offsets[p + 1]]): z_p[t] = the number of its photons in bin t (Sec. II-A, the ToAs binned on the
+    N_T bins of Eq. lik_ideal_poisson; the histogram of the histogram form below Eq. beta_div2). Photons outside
+    [0, T) are dropped; a pixel whose offsets are not 0 <= b <= e <= len(bins) gets an empty row. Returns
+    (z [P][T] int64, flags) with flags bit 0 = a photon was dropped, bit 2 = some pixel's offsets were invalid."""
+    off = np.asarray(offsets, dtype=np.int64)
+    y = np.asarray(bins, dtype=np.int64)
+    P = off.size - 1
+    z = np.zeros((P, T), dtype=np.int64)
+    flags = 0
+    for p in range(P):
+        b, e = int(off[p]), int(off[p + 1])
+        if not (0 <= b <= e <= y.size):
+            flags |= 4
+            continue
+        yp = y[b:e]
+        keep = (yp >= 0) & (yp < T)
+        if not keep.all():
+            flags |= 1
+        z[p] = np.bincount(yp[keep], minlength=T)
+    return z, flags
+
+
 def posterior(ell, dmin: int):
     ell = _d(ell)
     a = np.zeros(1, np.int32)

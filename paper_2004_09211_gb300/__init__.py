@@ -261,6 +261,30 @@ def spl_filter_step(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: to
     return o
 
 
+def spl_toa_histogram(prm: spl_params, offsets: torch.Tensor, bins: torch.Tensor, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """uint16 histograms [P][pitch] of one frame from its CSR photon lists (offsets int32 [P + 1], bins uint16):
+    z_p[t] = the number of pixel p's photons in bin t. out (optional) sets the pitch (its last dimension);
+    by default pitch = T rounded up to a multiple of 8."""
+    P = _P(prm)
+    if out is None:
+        out = _empty((P, (prm.T + 7) // 8 * 8), torch.uint16, offsets)
+    pitch = out.shape[-1]
+    nph = bins.numel()
+    lib = _abi.load()
+    _abi.check(lib.spl_toa_histogram(
+        ct.byref(prm), _dev(offsets, "offsets", torch.int32, P + 1),
+        _dev(bins, "bins", torch.uint16) if nph > 0 else None, nph,
+        _dev(out, "out", torch.uint16, P * pitch), pitch, _stream(stream)))
+    return out
+
+
+def spl_toa_status() -> int:
+    f = ct.c_uint32()
+    _abi.check(_abi.load().spl_toa_status(ct.byref(f)))
+    return int(f.value)
+
+
 def spl_filter_step_detect(prm: spl_params, z: torch.Tensor, h: torch.Tensor, mu_in: torch.Tensor,
                            var_in: torch.Tensor, present_in=None, faulty=None, pi0=None, out: dict | None = None,
                            stream=None) -> dict:

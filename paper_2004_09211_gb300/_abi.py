@@ -45,6 +45,9 @@ SPL_BATCH_BAD_BIN = 1
 SPL_BATCH_TOO_MANY = 2
 SPL_BATCH_DESC_MISMATCH = 4
 SPL_MAX_PHOTONS = 1024
+SPL_TOA_BAD_BIN = 1
+SPL_TOA_SATURATED = 2
+SPL_TOA_BAD_OFFSETS = 4
 
 
 # name -> (restype, argtypes); mirrors include/spl.h
@@ -81,6 +84,8 @@ SIGNATURES = {
     "spl_diff_forward": (ct.c_int, [_P, ct.c_int, _Hh, _vp, ct.c_float, _vp, _vp, _vp, _vp, _vp, _vp, ct.c_size_t, _vp]),
     "spl_diff_backward": (ct.c_int, [_P, ct.c_int, _Hh, _vp, ct.c_float, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ct.c_size_t,
                                      _vp]),
+    "spl_toa_histogram": (ct.c_int, [_P, _vp, _vp, ct.c_int64, _vp, ct.c_int64, _vp]),
+    "spl_toa_status": (ct.c_int, [ct.POINTER(ct.c_uint32)]),
     "spl_batch_step_noalloc": (ct.c_int, [ct.POINTER(spl_seq_desc), _vp, ct.c_int, ct.c_int, _vp, _vp]),
 }
 

@@ -417,4 +417,38 @@ spl_status spl_pi_propagate(const spl_params* prm, const float* pi_in, const uin
                        "spl_pi_propagate launch");
 }
 
+spl_status spl_toa_histogram(const spl_params* prm, const int32_t* offsets, const uint16_t* bins, int64_t nphotons,
+                             uint16_t* out, int64_t pitch, void* stream) {
+    g_err[0] = 0;
+    SPL_REQUIRE(prm != nullptr, "prm is NULL");
+    SPL_REQUIRE(prm->H >= 1 && prm->W >= 1, "H and W must be >= 1 (got %d x %d)", prm->H, prm->W);
+    SPL_REQUIRE(static_cast<long long>(prm->H) * prm->W <= (1LL << 31) - 1, "H*W exceeds 2^31-1");
+    SPL_REQUIRE(prm->T >= 1, "T must be >= 1 (got %d)", prm->T);
+    if (prm->T > SPL_MAX_BINS) {
+        set_error("T (%d) above %d is not supported by the library", prm->T, SPL_MAX_BINS);
+        return SPL_EUNSUPPORTED;
+    }
+    SPL_REQUIRE(offsets != nullptr, "offsets is NULL");
+    SPL_REQUIRE(nphotons >= 0 && nphotons <= (1LL << 31) - 1, "nphotons (%lld) must be in [0, 2^31-1]",
+                static_cast<long long>(nphotons));
+    SPL_REQUIRE(bins != nullptr || nphotons == 0, "bins is NULL with nphotons > 0");
+    SPL_REQUIRE(out != nullptr, "out is NULL");
+    SPL_REQUIRE(aligned16(out), "out must be 16-byte aligned");
+    SPL_REQUIRE(pitch >= prm->T && pitch % 8 == 0, "pitch (%lld) must be >= T (%d) and a multiple of 8",
+                static_cast<long long>(pitch), prm->T);
+    return cuda_status(launch_toa_hist(offsets, bins, nphotons, prm->T, pitch,
+                                       static_cast<long long>(prm->H) * prm->W, out,
+                                       static_cast<cudaStream_t>(stream)),
+                       "spl_toa_histogram launch");
+}
+
+spl_status spl_toa_status(uint32_t* flags) {
+    g_err[0] = 0;
+    SPL_REQUIRE(flags != nullptr, "flags is NULL");
+    unsigned v = 0;
+    spl_status st = cuda_status(toa_status_read(&v), "spl_toa_status");
+    if (st == SPL_OK) *flags = v;
+    return st;
+}
+
 }  // extern "C"

@@ -102,5 +102,9 @@ cudaError_t launch_filter_tc(const EstimateArgs& a, unsigned* status, cudaStream
 cudaError_t launch_estimate_redo(const EstimateArgs& a, cudaStream_t s);
 unsigned* tc_status_ptr();
 cudaError_t tc_status_read(unsigned* out);
+// uint16 histograms [P][pitch] from CSR photon lists (toa.cu); its condition flags are read by toa_status_read.
+cudaError_t launch_toa_hist(const int32_t* offsets, const uint16_t* bins, long long nph, int T, long long pitch,
+                            long long P, uint16_t* out, cudaStream_t s);
+cudaError_t toa_status_read(unsigned* out);
 
 }  // namespace spl

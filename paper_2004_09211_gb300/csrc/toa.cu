@@ -1,0 +1,108 @@
+// Histograms from photon time-of-arrival lists: z_p[t] = the number of pixel p's photons detected in bin t, the
+// histogram on which the histogram form of Eq. beta_div2 (C(d) = z^T s_d^beta) and Eq. lik_bg_poisson are
+// written (Sec. II-A: y_{p,n} is the set of a pixel's ToA, binned on the N_T bins of Eq. lik_ideal_poisson).
+//
+// One warp per pixel, its counters (32-bit, T rounded up to 8 of them) in the warp's slice of shared memory: the
+// lanes add the pixel's photons with shared-memory atomics (any order gives the same counts), then write the row
+// as uint16 with one coalesced 16-byte store per 8 elements (zeros past the counters), zeroing the slice in the
+// same pass for the warp's next pixel. DRAM traffic per pixel: the row written once (2 * pitch bytes) plus its
+// photons read once (2 bytes each) and its two offsets.
+//
+// Device-detected conditions (bits of the status word read by spl_toa_status):
+//   bit 0  a photon with a bin >= T was dropped;
+//   bit 1  a bin held more than 65535 photons and was written as 65535;
+//   bit 2  a pixel's offsets were not 0 <= offsets[p] <= offsets[p + 1] <= nphotons: its row is written as zeros
+//          and none of its photons is read.
+#include <stdint.h>
+
+#include "spl_internal.h"
+
+namespace spl {
+
+__device__ unsigned g_toa_status;
+
+namespace {
+
+constexpr int kMaxWarps = 8;
+
+__global__ void __launch_bounds__(kMaxWarps * 32) k_toa_hist(const int32_t* __restrict__ offsets,
+                                                             const uint16_t* __restrict__ bins, long long nph, int T,
+                                                             long long pitch, long long P, uint16_t* __restrict__ out) {
+    extern __shared__ uint4 s_cnt4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const int tw = (T + 7) & ~7;  // counters per warp
+    unsigned* cnt = reinterpret_cast<unsigned*>(s_cnt4) + warp * tw;
+    uint4* c4 = reinterpret_cast<uint4*>(cnt);
+    const int nc8 = tw >> 3;                                // 16-byte stores from counters
+    const long long n8 = pitch >> 3;                        // 16-byte stores per row
+    for (int i = lane; i < 2 * nc8; i += 32) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    unsigned flags = 0;
+    const long long stride = static_cast<long long>(gridDim.x) * wpc;
+    for (long long p = static_cast<long long>(blockIdx.x) * wpc + warp; p < P; p += stride) {
+        const long long b = offsets[p], e = offsets[p + 1];
+        if (b >= 0 && b <= e && e <= nph) {
+            for (long long k = b + lane; k < e; k += 32) {
+                const unsigned t = bins[k];
+                if (t < static_cast<unsigned>(T)) atomicAdd(&cnt[t], 1u);
+                else flags |= 1u;
+            }
+        } else {
+            flags |= 4u;
+        }
+        __syncwarp();
+        uint4* o = reinterpret_cast<uint4*>(out + p * pitch);
+        for (long long i = nc8 + lane; i < n8; i += 32) o[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = lane; i < nc8; i += 32) {
+            const uint4 a = c4[2 * i], q = c4[2 * i + 1];
+            c4[2 * i] = make_uint4(0u, 0u, 0u, 0u);
+            c4[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
+            const unsigned v[8] = {a.x, a.y, a.z, a.w, q.x, q.y, q.z, q.w};
+            unsigned w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned lo = v[2 * j], hi = v[2 * j + 1];
+                flags |= (lo | hi) > 0xffffu ? 2u : 0u;
+                w[j] = min(lo, 0xffffu) | (min(hi, 0xffffu) << 16);
+            }
+            o[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        __syncwarp();
+    }
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if (lane == 0 && flags) atomicOr(&g_toa_status, flags);
+}
+
+}  // namespace
+
+cudaError_t toa_status_read(unsigned* out) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_toa_status, sizeof(unsigned));
+    if (e != cudaSuccess) return e;
+    const unsigned zero = 0;
+    return cudaMemcpyToSymbol(g_toa_status, &zero, sizeof(unsigned));
+}
+
+// Warps per CTA: as many as fit in 96 KB of shared memory ((T + 7) & ~7 32-bit counters each), at most 8; a
+// persistent grid of the resident CTAs on every SM, or fewer when the frame has fewer pixels.
+cudaError_t launch_toa_hist(const int32_t* offsets, const uint16_t* bins, long long nph, int T, long long pitch,
+                            long long P, uint16_t* out, cudaStream_t s) {
+    const long long slice = 4LL * ((T + 7) & ~7);
+    int wpc = static_cast<int>((96 * 1024) / slice);
+    wpc = wpc < 1 ? 1 : (wpc > kMaxWarps ? kMaxWarps : wpc);
+    const size_t smem = static_cast<size_t>(slice) * wpc;
+    cudaError_t e = cudaFuncSetAttribute(k_toa_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_toa_hist, wpc * 32, smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long need = (P + wpc - 1) / wpc, full = static_cast<long long>(nsm) * per_sm;
+    const int grid = static_cast<int>(need < full ? need : full);
+    k_toa_hist<<<grid, wpc * 32, smem, s>>>(offsets, bins, nph, T, pitch, P, out);
+    return cudaGetLastError();
+}
+
+}  // namespace spl

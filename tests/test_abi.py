@@ -232,3 +232,26 @@ def test_throughput_probe_size_query():
     nb, opt = ct.c_int(0), ct.c_longlong(0)
     assert lib.spl_probe_throughput(7, 4, 16, None, None, ct.byref(nb), ct.byref(opt), None) == _abi.SPL_EINVAL
     assert lib.spl_probe_throughput(0, 0, 16, None, None, ct.byref(nb), ct.byref(opt), None) == _abi.SPL_EINVAL
+
+
+@pytest.mark.parametrize("args, needle", [
+    (dict(offsets=None), "offsets"),
+    (dict(bins=None), "bins is NULL"),
+    (dict(nph=-1), "nphotons"),
+    (dict(out=None), "out is NULL"),
+    (dict(out=0x3008), "16-byte aligned"),
+    (dict(pitch=60), "pitch"),
+    (dict(pitch=68), "pitch"),
+    (dict(T=9000, pitch=9000), "not supported"),
+])
+def test_toa_histogram_argument_checks(args, needle):
+    """spl_toa_histogram checks its arguments on the host (nothing is launched): offsets and out are required,
+    bins unless there are no photons, out 16-byte aligned, pitch >= T and a multiple of 8, T <= SPL_MAX_BINS."""
+    lib = _abi.load()
+    kw = dict(offsets=0x1000, bins=0x2000, nph=10, out=0x3000, pitch=64, T=64)
+    kw.update(args)
+    prm = make_params(4, 4, kw["T"], 1, 0)
+    st = lib.spl_toa_histogram(ct.byref(prm), kw["offsets"], kw["bins"], kw["nph"], kw["out"], kw["pitch"], None)
+    assert st in (_abi.SPL_EINVAL, _abi.SPL_EUNSUPPORTED)
+    assert needle in lib.spl_last_error().decode()
+    assert lib.spl_toa_status(None) == _abi.SPL_EINVAL

@@ -52,6 +52,47 @@ def test_photon_list_form_equals_histogram_form(orc):
         np.testing.assert_allclose(orc.cost_toa(q, h, y), orc.cost(q, h, z[None])[0], rtol=1e-13)
 
 
+def test_toa_histogram_hand_example(orc):
+    """A worked example counted by hand: three pixels with 3, 0 and 2 photons on T = 4 bins."""
+    z, flags = orc.toa_histogram(4, [0, 3, 3, 5], [2, 0, 2, 1, 1])
+    assert flags == 0
+    np.testing.assert_array_equal(z, [[1, 0, 2, 0], [0, 0, 0, 0], [0, 2, 0, 0]])
+
+
+def test_toa_histogram_carries_the_photon_sum_form(orc):
+    """Each row of toa_histogram is the histogram of the histogram form of Eq. beta_div2: C(d) on it equals the
+    photon-sum form on the pixel's list in any order, and the row sums to the pixel's photon count K."""
+    h, peak = synth.asymmetric_irf(L=11)
+    T = 50
+    rng = _rng(21)
+    counts = rng.integers(0, 30, size=12)
+    counts[[0, 5]] = 0
+    off = np.concatenate([[0], np.cumsum(counts)])
+    y = rng.integers(0, T, size=int(off[-1]))
+    z, flags = orc.toa_histogram(T, off, y)
+    assert flags == 0 and z.shape == (12, T)
+    q = orc.params(T, len(h), peak, beta=0.5)
+    for p in range(12):
+        yp = y[off[p]:off[p + 1]]
+        assert z[p].sum() == counts[p]
+        if counts[p] == 0:
+            assert not z[p].any()
+            continue
+        np.testing.assert_allclose(orc.cost(q, h, z[p][None].astype(np.float64))[0],
+                                   orc.cost_toa(q, h, rng.permutation(yp).astype(np.int32)), rtol=1e-13)
+
+
+def test_toa_histogram_input_errors(orc):
+    """Photons outside [0, T) are dropped (flag 1); a pixel with decreasing or out-of-range offsets gets an empty
+    row (flag 4) and the other pixels keep theirs."""
+    z, flags = orc.toa_histogram(4, [0, 2, 4], [1, 4, 3, 3])
+    assert flags == 1
+    np.testing.assert_array_equal(z, [[0, 1, 0, 0], [0, 0, 0, 2]])
+    z, flags = orc.toa_histogram(4, [0, 2, 1, 3, 9], [1, 1, 2])
+    assert flags == 4
+    np.testing.assert_array_equal(z, [[0, 2, 0, 0], [0, 0, 0, 0], [0, 1, 1, 0], [0, 0, 0, 0]])
+
+
 def test_zero_taps_contribute_nothing(orc):
     """0^beta = 0: an IRF with holes gives C(d) = (1/m)^beta * (photons on the non-zero taps), a windowed
     count computed with numpy.correlate against the tap mask."""
