@@ -39,10 +39,29 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_toa_hist(const int32_t* __re
     __syncwarp();
     unsigned flags = 0;
     const long long stride = static_cast<long long>(gridDim.x) * wpc;
-    for (long long p = static_cast<long long>(blockIdx.x) * wpc + warp; p < P; p += stride) {
-        const long long b = offsets[p], e = offsets[p + 1];
+    // The next pixel's offsets and first 32 photons are loaded while the current one is counted and written, so
+    // the two dependent loads (offsets, then bins) of a pixel overlap the previous pixel's work.
+    long long p = static_cast<long long>(blockIdx.x) * wpc + warp;
+    long long b = 0, e = 0;
+    unsigned t0 = 0xffffffffu;  // this lane's first photon of the pixel (none: above every bin)
+    if (p < P) {
+        b = offsets[p];
+        e = offsets[p + 1];
+        if (b >= 0 && b <= e && e <= nph && b + lane < e) t0 = bins[b + lane];
+    }
+    for (; p < P; p += stride) {
+        const long long pn = p + stride;
+        long long bn = 0, en = 0;
+        if (pn < P) {
+            bn = offsets[pn];
+            en = offsets[pn + 1];
+        }
         if (b >= 0 && b <= e && e <= nph) {
-            for (long long k = b + lane; k < e; k += 32) {
+            if (b + lane < e) {
+                if (t0 < static_cast<unsigned>(T)) atomicAdd(&cnt[t0], 1u);
+                else flags |= 1u;
+            }
+            for (long long k = b + 32 + lane; k < e; k += 32) {
                 const unsigned t = bins[k];
                 if (t < static_cast<unsigned>(T)) atomicAdd(&cnt[t], 1u);
                 else flags |= 1u;
@@ -51,6 +70,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_toa_hist(const int32_t* __re
             flags |= 4u;
         }
         __syncwarp();
+        // the next pixel's first photons, issued before this pixel's row is written
+        const unsigned t0n =
+            (pn < P && bn >= 0 && bn <= en && en <= nph && bn + lane < en) ? bins[bn + lane] : 0xffffffffu;
         uint4* o = reinterpret_cast<uint4*>(out + p * pitch);
         for (long long i = nc8 + lane; i < n8; i += 32) o[i] = make_uint4(0u, 0u, 0u, 0u);
         for (int i = lane; i < nc8; i += 32) {
@@ -68,6 +90,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_toa_hist(const int32_t* __re
             o[i] = make_uint4(w[0], w[1], w[2], w[3]);
         }
         __syncwarp();
+        b = bn;
+        e = en;
+        t0 = t0n;
     }
     flags = __reduce_or_sync(0xffffffffu, flags);
     if (lane == 0 && flags) atomicOr(&g_toa_status, flags);
