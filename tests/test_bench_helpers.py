@@ -45,3 +45,22 @@ def test_changed_source_voids_the_capture(tmp_path, monkeypatch):
         fh.write("\n// edited\n")
     assert bench.capture_traffic(name, 1000) is None
     assert bench.capture_traffic(name, 1000, "inst_per_pixel") is None
+
+
+def test_photon_lists_of_a_frame_give_back_its_histograms(orc):
+    """The end-to-end leg moves each frame as photon lists built from its histograms (each bin repeated by its
+    count): the oracle's histogram of those lists is the frame again, pixel by pixel, including empty pixels."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(4)
+    P, T, pitch = 37, 61, 64
+    z = rng.poisson(0.4, size=(P, T))
+    z[[0, 9, 36]] = 0
+    z[5, 7] = 300
+    zt = torch.zeros((P, pitch), dtype=torch.int32)
+    zt[:, :T] = torch.from_numpy(z)
+    off, bins = bench.toa_from_histograms(zt.to(torch.uint16), T)
+    assert off.dtype == torch.int32 and bins.dtype == torch.uint16 and int(off[-1]) == z.sum()
+    got, flags = orc.toa_histogram(T, off.numpy(), bins.to(torch.int32).numpy())
+    assert flags == 0
+    np.testing.assert_array_equal(got, z)
