@@ -291,6 +291,9 @@ SPL_API spl_status spl_filter_step_tc(const spl_params* prm, const spl_hist* z, 
  *     SPL_TOA_SATURATED (2)   a bin held more than 65535 photons and was written as 65535;
  *     SPL_TOA_BAD_OFFSETS (4) a pixel's offsets were not 0 <= offsets[p] <= offsets[p + 1] <= nphotons: its row is
  *                             written as zeros and none of its photons is read.
+ *   Host checks (nothing launched on failure): prm, offsets and out non-NULL, bins non-NULL unless nphotons = 0,
+ *   0 <= nphotons < 2^31, out 16-byte aligned, pitch >= T and a multiple of 8 -> SPL_EINVAL; T > SPL_MAX_BINS ->
+ *   SPL_EUNSUPPORTED.
  */
 #define SPL_TOA_BAD_BIN 1
 #define SPL_TOA_SATURATED 2
