@@ -4,7 +4,7 @@
 //
 // One warp per pixel, its counters (32-bit, T rounded up to 8 of them) in the warp's slice of shared memory: the
 // lanes add the pixel's photons with shared-memory atomics (any order gives the same counts), then write the row
-// as uint16 with one coalesced 16-byte store per 8 elements (zeros past the counters), zeroing the slice in the
+// as uint16 with one coalesced 8-byte store per 4 elements (zeros past the counters), zeroing the slice in the
 // same pass for the warp's next pixel. DRAM traffic per pixel: the row written once (2 * pitch bytes) plus its
 // photons read once (2 bytes each) and its two offsets.
 //
@@ -33,9 +33,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_toa_hist(const int32_t* __re
     const int tw = (T + 7) & ~7;  // counters per warp
     unsigned* cnt = reinterpret_cast<unsigned*>(s_cnt4) + warp * tw;
     uint4* c4 = reinterpret_cast<uint4*>(cnt);
-    const int nc8 = tw >> 3;                                // 16-byte stores from counters
-    const long long n8 = pitch >> 3;                        // 16-byte stores per row
-    for (int i = lane; i < 2 * nc8; i += 32) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+    const int nc4 = tw >> 2;             // groups of four counters (one 8-byte store each)
+    const long long n4 = pitch >> 2;     // 8-byte stores per row
+    for (int i = lane; i < nc4; i += 32) c4[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
     unsigned flags = 0;
     const long long stride = static_cast<long long>(gridDim.x) * wpc;
@@ -73,21 +73,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_toa_hist(const int32_t* __re
         // the next pixel's first photons, issued before this pixel's row is written
         const unsigned t0n =
             (pn < P && bn >= 0 && bn <= en && en <= nph && bn + lane < en) ? bins[bn + lane] : 0xffffffffu;
-        uint4* o = reinterpret_cast<uint4*>(out + p * pitch);
-        for (long long i = nc8 + lane; i < n8; i += 32) o[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = lane; i < nc8; i += 32) {
-            const uint4 a = c4[2 * i], q = c4[2 * i + 1];
-            c4[2 * i] = make_uint4(0u, 0u, 0u, 0u);
-            c4[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
-            const unsigned v[8] = {a.x, a.y, a.z, a.w, q.x, q.y, q.z, q.w};
-            unsigned w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const unsigned lo = v[2 * j], hi = v[2 * j + 1];
-                flags |= (lo | hi) > 0xffffu ? 2u : 0u;
-                w[j] = min(lo, 0xffffu) | (min(hi, 0xffffu) << 16);
-            }
-            o[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        // four counters per lane at unit stride (conflict-free 16-byte shared loads and stores), written as four
+        // uint16 with one 8-byte store per lane (coalesced: 256 bytes per warp instruction)
+        uint2* o = reinterpret_cast<uint2*>(out + p * pitch);
+        for (long long i = nc4 + lane; i < n4; i += 32) o[i] = make_uint2(0u, 0u);
+#pragma unroll 4
+        for (int i = lane; i < nc4; i += 32) {
+            const uint4 a = c4[i];
+            c4[i] = make_uint4(0u, 0u, 0u, 0u);
+            flags |= (a.x | a.y | a.z | a.w) > 0xffffu ? 2u : 0u;
+            o[i] = make_uint2(min(a.x, 0xffffu) | (min(a.y, 0xffffu) << 16),
+                              min(a.z, 0xffffu) | (min(a.w, 0xffffu) << 16));
         }
         __syncwarp();
         b = bn;
