@@ -111,7 +111,7 @@ def hbm_roofline(peaks, alg_bytes, launch_s, traffic, kernel, **extra):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s", **extra}
 
 
-# Measured on GB300 (bench.py --workload alu_peaks, profiles/alu_peaks_gb300.md): FP32 FMA instructions issue at
+# Measured on GB300 (bench.py --workload alu_peaks, with spl_probe_throughput): FP32 FMA instructions issue at
 # 124.5 lanes per clock per SM (3.89 warp-instructions per clock per SM, one per scheduler), packed f32x2 FMAs at
 # 127.0 operations (no gain: the FMA pipe takes two cycles per packed instruction) and ex2.approx at 31.9.
 MEASURED_WARP_ISSUE_PER_CLK_SM = 124.5 / 32
