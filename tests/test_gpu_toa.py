@@ -107,3 +107,32 @@ def test_filter_step_on_device_histograms():
     assert spl.spl_tc_status() == 0
     for k in ("mu", "var", "argmax", "refl", "bg"):
         assert torch.equal(a[k], b[k]), k
+
+
+def test_full_size_frame_matches_the_oracle(orc):
+    """The video workload's frame size and densest lists (256 x 256 pixels, T = 1500, SBR 0.01: about 300 photons
+    per pixel, 20 M in the frame), each pixel's photons in random order, in the launch configuration of the
+    benchmark's end-to-end leg: every element equal to the oracle's histogram."""
+    H, W, T, L = 256, 256, 1500, 48
+    h, peak = synth.asymmetric_irf(L=L)
+    depth = synth.smooth_depth_map(H, W, peak + 30, T - L + peak - 30, 11).round()
+    g = torch.Generator().manual_seed(11)
+    mean = synth.expected_counts(torch.from_numpy(depth), torch.full((H, W), 3.0, dtype=torch.float64),
+                                 3.0 / (0.01 * T), torch.from_numpy(h), peak, T)
+    z = torch.poisson(mean, generator=g).to(torch.int64).reshape(H * W, T)
+    cnt = z.sum(1)
+    off = np.concatenate([[0], np.cumsum(cnt.numpy())]).astype(np.int32)
+    nz = z.nonzero()
+    reps = z[nz[:, 0], nz[:, 1]]
+    bins = torch.repeat_interleave(nz[:, 1], reps)
+    pix = torch.repeat_interleave(nz[:, 0], reps).to(torch.float64)
+    key = pix + torch.rand(pix.numel(), generator=torch.Generator().manual_seed(12), dtype=torch.float64)
+    bins = bins[torch.argsort(key)].numpy().astype(np.uint16)  # each pixel's photons in random order
+    assert bins.size > 15_000_000
+    prm = spl.make_params(H, W, T, L, peak)
+    got, flags = _run(prm, off, bins, synth.pad_pitch(T))
+    zo, oflags = orc.toa_histogram(T, off, bins)
+    assert flags == 0 and oflags == 0
+    np.testing.assert_array_equal(got[:, :T], zo)
+    np.testing.assert_array_equal(zo, z.numpy())
+    assert not got[:, T:].any()
