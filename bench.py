@@ -1105,31 +1105,52 @@ def detect(args):
                for _ in BETAS] for _ in SBRS]
     outs = dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
                 bg=torch.empty(P, device=dev))
-    pi_buf = [torch.empty(P, device=dev) for _ in range(2)]
-    pres_buf = [torch.empty(P, dtype=torch.uint8, device=dev) for _ in range(2)]
-    pi0_buf = torch.empty(P, device=dev)
     stream = torch.cuda.current_stream(dev)
     units = len(SBRS) * len(BETAS) * frames * P
 
-    def run(vi, bi):
-        """One (SBR, beta) run over all frames; returns the last frame's decisions."""
+    def lane_buffers():
+        return dict(pi=[torch.empty(P, device=dev) for _ in range(2)],
+                    pres=[torch.empty(P, dtype=torch.uint8, device=dev) for _ in range(2)],
+                    pi0=torch.empty(P, device=dev),
+                    outs=dict(argmax=torch.empty(P, dtype=torch.int32, device=dev), refl=torch.empty(P, device=dev),
+                              bg=torch.empty(P, device=dev)))
+
+    # the nine runs are independent sequences: issued round-robin on JOB_STREAMS streams, each with its own
+    # buffers, as in the headline job
+    lanes = [(torch.cuda.Stream(dev), lane_buffers()) for _ in range(JOB_STREAMS)]
+    plain_lanes = [(st, lb["outs"]) for st, lb in lanes]
+
+    def run(vi, bi, st=None, lb=None):
+        """One (SBR, beta) run over all frames on stream st with lane buffers lb; returns the last frame's
+        decisions."""
+        st = st if st is not None else stream
+        lb = lb if lb is not None else lanes[0][1]
         prm = prms[bi]
         mu, var = states[vi][bi]
-        spl.spl_state_init(prm, mu[0], var[0], stream=stream)
+        spl.spl_state_init(prm, mu[0], var[0], stream=st)
         pi0 = pres = None
         for n, z in enumerate(videos[vi]):
             src, dst = n & 1, (n + 1) & 1
             o = spl.spl_filter_step_detect(prm, z, hd, mu[src], var[src], present_in=pres, pi0=pi0,
-                                           out=dict(mu=mu[dst], var=var[dst], pi=pi_buf[n & 1],
-                                                    present=pres_buf[n & 1], **outs), stream=stream)
-            pi0 = spl.spl_pi_propagate(prm, o["pi"], pi_out=pi0_buf, stream=stream)
+                                           out=dict(mu=mu[dst], var=var[dst], pi=lb["pi"][n & 1],
+                                                    present=lb["pres"][n & 1], **lb["outs"]), stream=st)
+            pi0 = spl.spl_pi_propagate(prm, o["pi"], pi_out=lb["pi0"], stream=st)
             pres = o["present"]
         return pres
 
     def job():
-        for vi in range(len(SBRS)):
-            for bi in range(len(BETAS)):
-                run(vi, bi)
+        start = torch.cuda.Event()
+        start.record(stream)
+        for st, _ in lanes:
+            st.wait_event(start)
+        runs = [(vi, bi) for vi in range(len(SBRS)) for bi in range(len(BETAS))]
+        for r, (vi, bi) in enumerate(runs):
+            st, lb = lanes[r % len(lanes)]
+            run(vi, bi, st, lb)
+        for st, _ in lanes:
+            done = torch.cuda.Event()
+            done.record(st)
+            stream.wait_event(done)
 
     def timed(fn):
         for _ in range(args.warmup):
@@ -1158,7 +1179,7 @@ def detect(args):
             mu, var = states[vi][bi]
             o = spl.spl_filter_step_detect(prm, zbg, hd, mu[frames & 1], var[frames & 1], stream=stream)
             p_fa[f"SBR {sbr} beta {BETAS[bi]}"] = float(o["present"].float().mean())
-    ms_plain = timed(lambda: run_job(spl, prms, hd, videos, states, outs, stream))
+    ms_plain = timed(lambda: run_job(spl, prms, hd, videos, states, outs, stream, lanes=plain_lanes))
     # roofline of one detect step (tensor-core depth launch + redo scan + detecting intensity launch + pi
     # propagation): uint16 row (2 T) + previous state (8 B) + present_in (1 B) + pi0 (4 B) + outputs mu, var, argmax,
     # refl, bg, pi, present (25 B) + the propagation's pi read and pi0 write (8 B) per pixel; time per step = job
