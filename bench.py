@@ -1029,8 +1029,8 @@ def diff(args):
 
 def video_tc(args):
     """The video job (the headline workload) through spl_filter_step_tc on FP16 copies of its uint16 frames (the
-    counts are small integers, exact in FP16), timed like the headline, beside spl_filter_step_fp32 on the original
-    frames. Also reported: the depth RMSE of both paths against the ground truth at every run's last frame."""
+    counts are small integers, exact in FP16), timed like the headline (the runs on JOB_STREAMS streams), beside
+    spl_filter_step_fp32 on the original frames. Also reported: the depth RMSE of both paths against the ground truth at every run's last frame."""
     import paper_2004_09211_gb300 as spl
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -1046,15 +1046,20 @@ def video_tc(args):
                 bg=torch.empty(P, device=dev))
     stream = torch.cuda.current_stream(dev)
     units = len(SBRS) * len(BETAS) * frames * P
+    # the runs on JOB_STREAMS streams, as in the headline job (two tensor-core CTAs fill an SM's shared memory, so a
+    # CTA of another launch never waits there for tensor memory)
+    lanes = [(torch.cuda.Stream(dev), dict(argmax=torch.empty(P, dtype=torch.int32, device=dev),
+                                           refl=torch.empty(P, device=dev), bg=torch.empty(P, device=dev)))
+             for _ in range(JOB_STREAMS)]
 
     def timed(step, vids):
         for _ in range(args.warmup):
-            run_job(spl, prms, hd, vids, states, outs, stream, step=step)
+            run_job(spl, prms, hd, vids, states, outs, stream, step=step, lanes=lanes)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            run_job(spl, prms, hd, vids, states, outs, stream, step=step)
+            run_job(spl, prms, hd, vids, states, outs, stream, step=step, lanes=lanes)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / args.steps, job_rmse(spl, prms, hd, vids, sc, frames, dev, step=step)[0]
