@@ -255,3 +255,14 @@ def test_toa_histogram_argument_checks(args, needle):
     assert st in (_abi.SPL_EINVAL, _abi.SPL_EUNSUPPORTED)
     assert needle in lib.spl_last_error().decode()
     assert lib.spl_toa_status(None) == _abi.SPL_EINVAL
+
+
+def test_toa_histogram_binding_refuses_host_tensors():
+    """The binding passes device pointers only: host tensors are refused before anything reaches the library."""
+    import torch
+    import paper_2004_09211_gb300 as spl
+    prm = make_params(2, 2, 64, 1, 0)
+    off = torch.zeros(5, dtype=torch.int32)
+    bins = torch.zeros(0, dtype=torch.uint16)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        spl.spl_toa_histogram(prm, off, bins, out=torch.zeros((4, 64), dtype=torch.int32).to(torch.uint16))
